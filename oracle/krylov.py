@@ -1,0 +1,180 @@
+"""Krylov solvers started from the subspace guess (Algorithm 1, step 4).
+
+The paper runs GMRES (Saad and Schultz) for general matrices and names CG
+(Hestenes and Stiefel) for symmetric positive definite ones (Section 1); both
+stop on the residual relative to ||b||, the reading under which the paper's
+"initial residual already below the tolerance, hence 0 iterations" (Sections
+4 and 5) is possible.  Conventions shared with the GPU side:
+
+* an iteration is one product with A inside the loop (one Arnoldi step for
+  GMRES, one search direction for CG);
+* CG: when the recursive residual passes the test, the true residual b - A x
+  is recomputed; if it fails, CG restarts from it (the count continues);
+  p^T A p <= 0 is a breakdown;
+* GMRES(m): CGS2 Arnoldi (two classical Gram-Schmidt passes, h = h1 + h2),
+  Givens rotations with r = hypot(a, b), inner stop when |g_{j+1}| <= tol ||b||,
+  happy breakdown when h_{j+1,j} <= 1e-14 ||h_{:,j}||, and the true residual
+  recomputed at every restart;
+* mixed refinement: r = b - A64 x in FP64; the correction d solves
+  A32 d = r / ||r|| by the same solver run entirely in float32, to a relative
+  residual max(inner_tol, theta * tol ||b|| / ||r||); x += ||r|| d in FP64.
+
+Status codes: 0 converged, 1 not converged within max_iters, -4 breakdown.
+
+Parity: pinned by dense LU on small systems, finite termination of full
+GMRES, CG's k-step termination on k distinct eigenvalues, the Arnoldi
+relation and the orthogonality of the Krylov basis.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse
+
+CONVERGED = 0
+NOT_CONVERGED = 1
+BREAKDOWN = -4
+
+
+def csr(rowptr, colind, values, n: int) -> scipy.sparse.csr_matrix:
+    """The CSR triple as a scipy matrix (scipy's product is the SpMV primitive)."""
+    return scipy.sparse.csr_matrix((values, colind, rowptr), shape=(n, n))
+
+
+def cg(A, b, x, tol: float, max_iters: int):
+    """Conjugate gradients from x.  Returns (x, iterations, relres, status)."""
+    dt = b.dtype
+    x = x.astype(dt, copy=True)
+    bnorm = math.sqrt(float(np.dot(b, b)))
+    target = tol * bnorm
+    r = b - A @ x
+    rr = np.dot(r, r)
+    it = 0
+    if math.sqrt(float(rr)) <= target:
+        return x, 0, math.sqrt(float(rr)) / bnorm, CONVERGED
+    p = r.copy()
+    while True:
+        if it >= max_iters:
+            return x, it, math.sqrt(float(np.dot(r, r))) / bnorm, NOT_CONVERGED
+        q = A @ p
+        pq = np.dot(p, q)
+        if not pq > 0:
+            return x, it, math.sqrt(float(rr)) / bnorm, BREAKDOWN
+        alpha = rr / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        rr_new = np.dot(r, r)
+        it += 1
+        if math.sqrt(float(rr_new)) <= target:
+            r = b - A @ x
+            rr = np.dot(r, r)
+            if math.sqrt(float(rr)) <= target:
+                return x, it, math.sqrt(float(rr)) / bnorm, CONVERGED
+            p = r.copy()
+            continue
+        beta = rr_new / rr
+        rr = rr_new
+        p = r + beta * p
+
+
+def gmres(A, b, x, tol: float, restart: int, max_iters: int, record=None):
+    """Restarted GMRES with CGS2 Arnoldi from x.  Returns (x, iters, relres, status).
+
+    ``record`` (optional list) receives (V, Hbar) of every cycle, for tests of
+    the Arnoldi relation.
+    """
+    dt = b.dtype
+    x = x.astype(dt, copy=True)
+    n = b.shape[0]
+    bnorm = math.sqrt(float(np.dot(b, b)))
+    target = tol * bnorm
+    it = 0
+    while True:
+        r = b - A @ x
+        beta = math.sqrt(float(np.dot(r, r)))
+        if beta <= target:
+            return x, it, beta / bnorm, CONVERGED
+        if it >= max_iters:
+            return x, it, beta / bnorm, NOT_CONVERGED
+        V = np.zeros((n, restart + 1), dtype=dt)
+        H = np.zeros((restart + 1, restart))          # Hessenberg, FP64 always
+        Hbar = np.zeros((restart + 1, restart))
+        cs = np.zeros(restart)
+        sn = np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        V[:, 0] = r / dt.type(beta)
+        k = 0
+        for j in range(restart):
+            w = A @ V[:, j]
+            h1 = V[:, :j + 1].T @ w
+            w = w - V[:, :j + 1] @ h1
+            h2 = V[:, :j + 1].T @ w
+            w = w - V[:, :j + 1] @ h2
+            h = h1.astype(np.float64) + h2.astype(np.float64)
+            hn = math.sqrt(float(np.dot(w, w)))
+            H[:j + 1, j] = h
+            H[j + 1, j] = hn
+            Hbar[:j + 2, j] = H[:j + 2, j]
+            for i in range(j):                        # previous rotations
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            a_, b_ = H[j, j], H[j + 1, j]
+            rr = math.hypot(a_, b_)
+            if rr == 0.0:
+                cs[j], sn[j] = 1.0, 0.0
+            else:
+                cs[j], sn[j] = a_ / rr, b_ / rr
+            H[j, j] = rr
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            it += 1
+            k = j + 1
+            if hn > 0.0:
+                V[:, j + 1] = w / dt.type(hn)
+            happy = hn <= 1e-14 * math.sqrt(float(np.dot(h, h)) + hn * hn)
+            if happy or abs(g[j + 1]) <= target or it >= max_iters:
+                break
+        if any(H[i, i] == 0.0 for i in range(k)):
+            return x, it, beta / bnorm, BREAKDOWN
+        yk = np.zeros(k)
+        for i in range(k - 1, -1, -1):                # back substitution
+            yk[i] = (g[i] - np.dot(H[i, i + 1:k], yk[i + 1:k])) / H[i, i]
+        if record is not None:
+            record.append((V[:, :k + 1].copy(), Hbar[:k + 1, :k].copy()))
+        x = x + V[:, :k] @ yk.astype(dt)
+
+
+def mixed_refine(A64, A32, b, x, tol: float, inner: str, restart: int,
+                 max_iters: int, inner_tol: float = 1e-2, theta: float = 0.5,
+                 max_refinements: int = 100):
+    """FP32-inner / FP64-outer iterative refinement.  Returns
+    (x, inner_iterations, refinements, relres, status)."""
+    x = x.astype(np.float64, copy=True)
+    bnorm = math.sqrt(float(np.dot(b, b)))
+    target = tol * bnorm
+    total = 0
+    refinements = 0
+    while True:
+        r = b - A64 @ x
+        rn = math.sqrt(float(np.dot(r, r)))
+        if rn <= target:
+            return x, total, refinements, rn / bnorm, CONVERGED
+        if refinements >= max_refinements or total >= max_iters:
+            return x, total, refinements, rn / bnorm, NOT_CONVERGED
+        rhs32 = (r / rn).astype(np.float32)
+        itol = max(inner_tol, theta * target / rn)
+        d0 = np.zeros_like(rhs32)
+        budget = max_iters - total
+        if inner == "cg":
+            d, it, _, st = cg(A32, rhs32, d0, itol, budget)
+        else:
+            d, it, _, st = gmres(A32, rhs32, d0, itol, restart, budget)
+        total += it
+        refinements += 1
+        if st == BREAKDOWN:
+            return x, total, refinements, rn / bnorm, BREAKDOWN
+        x = x + rn * d.astype(np.float64)
