@@ -1,0 +1,173 @@
+/*
+ * seqaccel — subspace-accelerated solution of a sequence of sparse linear
+ * systems A(t_i) x(t_i) = b(t_i), i = 0, 1, 2, ... on one GPU (sm_103a).
+ *
+ * Method (Guido, Kressner, Ricci, arXiv 2309.02156):
+ *   Section 1, eq. (1)   the systems arrive one at a time;
+ *   Section 2            history X = [x(t_{i-M}) | ... | x(t_{i-1})], shifted
+ *                        by one column per system;
+ *   Algorithm 1          guess = argmin over span(X) of ||A(t_i) s - b(t_i)||_2,
+ *                        then the Krylov solver starts from it.
+ * Here the reduced least-squares problem of Algorithm 1, step 3 is sketched
+ * with a sparse-sign matrix S (s x n, zeta nonzeros of +-1/sqrt(zeta) per
+ * column, generated from SplitMix64 counters):
+ *   W = S [A X | b],  y = argmin ||W[:, :m] y - W[:, m]||_2 (pivoted Householder
+ *   QR, rank truncation), x0 = X y;
+ * then CG (SPD) or restarted GMRES with CGS2 Arnoldi (Section 1, Algorithm 1
+ * step 4) runs from x0 to ||b - A x|| <= tol ||b||.
+ *
+ * Conventions for every entry point
+ *   - Pointers named *_dev are DEVICE pointers owned by the caller and only
+ *     borrowed for the duration of the call; pointers named *_host are host
+ *     pointers.  Vectors are dense, contiguous, length n.
+ *   - All work is ordered on the CUDA stream given to seq_create.  Calls that
+ *     return a seq_info synchronise that stream before returning.
+ *   - Matrices are CSR with int32 row pointers (n+1) and column indices (nnz);
+ *     column indices outside [0, n) are skipped by the kernels and reported as
+ *     SEQ_EINVAL.
+ *   - Return values are seq_status codes; no exception or abort crosses the
+ *     boundary.  seq_last_error() describes the last failure of a context.
+ *   - A context is not thread safe; distinct contexts are independent.
+ */
+#ifndef SEQACCEL_H
+#define SEQACCEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct seq_ctx seq_ctx;
+
+typedef enum {
+    SEQ_OK = 0,               /* converged / done                              */
+    SEQ_NOT_CONVERGED = 1,    /* iteration cap reached; x holds the last iterate */
+    SEQ_FALLBACK_USED = 2,    /* learned guess rejected, sketched LS used        */
+    SEQ_EINVAL = -1,          /* bad argument or malformed CSR                   */
+    SEQ_ENOMEM = -2,          /* device or pinned allocation failed              */
+    SEQ_ECUDA = -3,           /* a CUDA runtime call failed                      */
+    SEQ_EBREAKDOWN = -4,      /* CG p^T A p <= 0, or a singular Hessenberg       */
+    SEQ_ENONFINITE = -5,      /* NaN or Inf met in a residual norm               */
+    SEQ_ETIMEOUT = -6         /* a bounded device-side wait expired              */
+} seq_status;
+
+typedef enum {
+    SEQ_F64 = 0,      /* FP64 everywhere                                                */
+    SEQ_MIXED = 1     /* FP32 values, history, sketch and inner Krylov; FP64 QR,
+                         refinement residual b - A x and convergence test             */
+} seq_precision;
+
+typedef enum {
+    SEQ_GUESS_ZERO = 0,     /* x0 = 0                                                  */
+    SEQ_GUESS_PREV = 1,     /* x0 = x(t_{i-1}), the paper's baseline (Sections 4-5)    */
+    SEQ_GUESS_SKETCH = 2,   /* x0 = X y, y from the sketched least squares (Alg. 1)    */
+    SEQ_GUESS_LEARNED = 3   /* y predicted by the coefficient MLP, sketched LS fallback */
+} seq_guess_mode;
+
+typedef enum { SEQ_CG = 0, SEQ_GMRES = 1 } seq_krylov;
+
+typedef struct {
+    int32_t n;                 /* rows = columns                                  */
+    int32_t nnz;               /* stored entries                                  */
+    const int32_t* rowptr;     /* device, n+1, rowptr[0] = 0, non-decreasing      */
+    const int32_t* colind;     /* device, nnz                                     */
+    const double* values;      /* device, nnz, FP64                               */
+    const float* values_f32;   /* device, nnz, FP32 copy used by SEQ_MIXED inner
+                                  solves; NULL: the library rounds `values`        */
+} seq_csr;
+
+typedef struct {
+    int32_t n;            /* unknowns per system                                   */
+    int32_t M;            /* history length, 1..31                                 */
+    int32_t s;            /* sketch rows, M+1..128                                  */
+    int32_t zeta;         /* nonzeros per sketch column, 1..min(s, 16)             */
+    uint64_t seed;        /* sketch seed (S is fixed for the life of the context)  */
+    int32_t precision;    /* seq_precision                                         */
+    int32_t guess;        /* seq_guess_mode                                        */
+    int32_t krylov;       /* seq_krylov                                            */
+    int32_t restart;      /* GMRES restart length, 1..64                           */
+    int32_t max_iters;    /* Krylov iteration cap per solve (inner iterations in
+                             SEQ_MIXED)                                            */
+    double inner_tol;     /* SEQ_MIXED: floor of the inner relative tolerance;
+                             0 selects 1e-2                                        */
+    double rank_tol;      /* QR truncation tau; 0 selects 1e-12 (SEQ_F64) or 1e-5
+                             (SEQ_MIXED)                                           */
+} seq_config;
+
+typedef struct {
+    int32_t iters;          /* Krylov iterations (inner iterations summed in SEQ_MIXED) */
+    int32_t refinements;    /* FP64 refinement steps (SEQ_MIXED)                       */
+    int32_t history_cols;   /* history columns the guess used                          */
+    int32_t rank;           /* columns kept by the pivoted QR                           */
+    double guess_relres;    /* ||b - A x0|| / ||b|| of the starting vector              */
+    double sketch_resid;    /* ||W1 y - wb||_2 (sketched residual)                      */
+    double final_relres;    /* true ||b - A x|| / ||b|| at exit (seq_solve)             */
+    int32_t status;         /* seq_status of the call                                   */
+    int32_t launches;       /* kernels this call launched (graph nodes included)        */
+} seq_info;
+
+/* Create a context for one sequence (Section 2: one history X per sequence).
+ * Allocates the history ring (n x M), the sketch (2 bytes x zeta x n), the
+ * Krylov workspace (GMRES: n x (restart+1) basis) and small device state.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: SEQ_EINVAL (cfg out of range), SEQ_ENOMEM, SEQ_ECUDA.  *out is NULL
+ * on failure. */
+int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out);
+
+/* Free everything the context owns.  NULL is accepted. */
+int seq_destroy(seq_ctx* ctx);
+
+/* Append x(t_i) to the history and drop the oldest column once M are held
+ * (Section 2.1, the history update "removing its first column and appending a
+ * new last column").  x_dev: device, n FP64 values (rounded to FP32 in
+ * SEQ_MIXED).  Stream-ordered; does not synchronise. */
+int seq_push_solution(seq_ctx* ctx, const double* x_dev);
+
+/* Number of history columns currently held (0..M). */
+int seq_history_size(const seq_ctx* ctx);
+
+/* Initial guess for A x = b (Algorithm 1, steps 1-3, with the sketched reduced
+ * problem; or the guess mode chosen in the config).  Writes x0_dev (device, n
+ * FP64).  With an empty history x0 = 0; with m < M columns the m available
+ * ones are used.  Fills info (guess_relres, sketch_resid, rank, history_cols).
+ * Synchronises the stream.  Errors: SEQ_EINVAL, SEQ_ECUDA. */
+int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev,
+              double* x0_dev, seq_info* info);
+
+/* Krylov solve from x_dev (Algorithm 1, step 4): on entry x_dev holds the
+ * starting vector, on exit the iterate with ||b - A x|| <= tol ||b|| (status
+ * SEQ_OK) or the last iterate (SEQ_NOT_CONVERGED after max_iters iterations).
+ * CG or GMRES(restart) with CGS2 per the config; SEQ_MIXED runs FP32 inner
+ * solves inside FP64 iterative refinement.  Does not push x.  Synchronises. */
+int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol,
+              double* x_dev, seq_info* info);
+
+/* Description of the last error of ctx ("" if none).  Valid until the next
+ * call on ctx. */
+const char* seq_last_error(const seq_ctx* ctx);
+
+/* The sketched block and coefficients of the last seq_guess, in logical
+ * history order (oldest column first): W_host (s x (m+1), row-major, b last)
+ * and y_host (m), where m = info.history_cols of that call.  Either pointer
+ * may be NULL.  Diagnostic; synchronises. */
+int seq_last_sketch(seq_ctx* ctx, double* W_host, double* y_host);
+
+/* Materialise the sparse-sign sketch used by every context with the same
+ * (n, s, zeta, seed): for column j, rows_dev[j*zeta + k] and signs_dev[j*zeta + k]
+ * (+1/-1) in acceptance order (see the oracle's definition: candidates are
+ * SplitMix64 outputs 256 j + c + 1, row = ((h >> 32) s) >> 32, sign = bit 0,
+ * duplicates skipped).  Device pointers; stream-ordered; synchronises. */
+int seq_sketch_columns(int32_t n, int32_t s, int32_t zeta, uint64_t seed,
+                       int32_t* rows_dev, int8_t* signs_dev, void* cuda_stream);
+
+/* Measure this device's FP64 fused multiply-add throughput (TFLOP/s, counting
+ * 2 flops per FMA) with a register-only kernel of about 50 ms.  Used as the
+ * arithmetic roof of the FP64 kernels.  Synchronises. */
+int seq_probe_fp64_peak(void* cuda_stream, double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEQACCEL_H */

@@ -1,0 +1,221 @@
+"""ctypes binding of libseqaccel: structs mirroring include/seqaccel.h and thin
+wrappers with the same names.  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional
+
+import torch
+
+from . import build as _build
+
+STATUS = {0: "SEQ_OK", 1: "SEQ_NOT_CONVERGED", 2: "SEQ_FALLBACK_USED", -1: "SEQ_EINVAL",
+          -2: "SEQ_ENOMEM", -3: "SEQ_ECUDA", -4: "SEQ_EBREAKDOWN", -5: "SEQ_ENONFINITE",
+          -6: "SEQ_ETIMEOUT"}
+PRECISION = {"f64": 0, "mixed": 1}
+GUESS = {"zero": 0, "prev": 1, "sketch": 2, "learned": 3}
+KRYLOV = {"cg": 0, "gmres": 1}
+
+
+class SeqError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32),
+                ("rowptr", ctypes.c_void_p), ("colind", ctypes.c_void_p),
+                ("values", ctypes.c_void_p), ("values_f32", ctypes.c_void_p)]
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("M", ctypes.c_int32), ("s", ctypes.c_int32),
+                ("zeta", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("precision", ctypes.c_int32), ("guess", ctypes.c_int32),
+                ("krylov", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("max_iters", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("rank_tol", ctypes.c_double)]
+
+
+class SeqInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("refinements", ctypes.c_int32),
+                ("history_cols", ctypes.c_int32), ("rank", ctypes.c_int32),
+                ("guess_relres", ctypes.c_double), ("sketch_resid", ctypes.c_double),
+                ("final_relres", ctypes.c_double), ("status", ctypes.c_int32),
+                ("launches", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_LIB = None
+
+_SIGS = {
+    "seq_create": (ctypes.c_int, [ctypes.POINTER(_Config), ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_void_p)]),
+    "seq_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "seq_push_solution": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "seq_history_size": (ctypes.c_int, [ctypes.c_void_p]),
+    "seq_guess": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Csr), ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.POINTER(SeqInfo)]),
+    "seq_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Csr), ctypes.c_void_p,
+                                 ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(SeqInfo)]),
+    "seq_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "seq_last_sketch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "seq_sketch_columns": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
+    "seq_probe_fp64_peak": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True) -> ctypes.CDLL:
+    """Load libseqaccel.so (building it first when sources are newer)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build() if build_if_needed else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libseqaccel.so is not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t: Optional[torch.Tensor], dtype: torch.dtype, n: Optional[int] = None) -> int:
+    if t is None:
+        return 0
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous CUDA tensor of {dtype}, got {t.dtype} on {t.device}")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"tensor has {t.numel()} elements, need {n}")
+    return t.data_ptr()
+
+
+@dataclasses.dataclass
+class CSR:
+    """A device CSR matrix: int32 rowptr (n+1), int32 colind (nnz), float64 values
+    and an optional float32 copy for mixed precision."""
+    rowptr: torch.Tensor
+    colind: torch.Tensor
+    values: torch.Tensor
+    values_f32: Optional[torch.Tensor] = None
+
+    @property
+    def n(self) -> int:
+        return self.rowptr.numel() - 1
+
+    @property
+    def nnz(self) -> int:
+        return self.colind.numel()
+
+    def _c(self) -> _Csr:
+        return _Csr(self.n, self.nnz, _ptr(self.rowptr, torch.int32, self.n + 1),
+                    _ptr(self.colind, torch.int32, self.nnz),
+                    _ptr(self.values, torch.float64, self.nnz),
+                    _ptr(self.values_f32, torch.float32, self.nnz))
+
+
+class Sequence:
+    """One sequence of systems A(t_i) x = b(t_i) sharing a history of M solutions
+    (seq_create / seq_push_solution / seq_guess / seq_solve)."""
+
+    def __init__(self, n: int, M: int, s: int, zeta: int = 8, seed: int = 0x5EEDBA5E,
+                 precision: str = "f64", guess: str = "sketch", krylov: str = "gmres",
+                 restart: int = 30, max_iters: int = 30000, inner_tol: float = 0.0,
+                 rank_tol: float = 0.0):
+        self._lib = load()
+        cfg = _Config(n, M, s, zeta, seed, PRECISION[precision], GUESS[guess], KRYLOV[krylov],
+                      restart, max_iters, inner_tol, rank_tol)
+        h = ctypes.c_void_p()
+        rc = self._lib.seq_create(ctypes.byref(cfg), ctypes.c_void_p(_stream()), ctypes.byref(h))
+        if rc != 0:
+            raise SeqError(rc, "seq_create failed")
+        self._h = h
+        self.n, self.M, self.s = n, M, s
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.seq_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int, info: Optional[SeqInfo] = None, allow=(0, 1)) -> None:
+        if rc not in allow:
+            msg = self._lib.seq_last_error(self._h)
+            raise SeqError(rc, msg.decode() if msg else "")
+
+    def history_size(self) -> int:
+        return self._lib.seq_history_size(self._h)
+
+    def push(self, x: torch.Tensor) -> None:
+        self._check(self._lib.seq_push_solution(self._h, _ptr(x, torch.float64, self.n)))
+
+    def guess(self, A: CSR, b: torch.Tensor, x0: torch.Tensor) -> dict:
+        info = SeqInfo()
+        rc = self._lib.seq_guess(self._h, ctypes.byref(A._c()), _ptr(b, torch.float64, self.n),
+                                 _ptr(x0, torch.float64, self.n), ctypes.byref(info))
+        self._check(rc, info)
+        return info.as_dict()
+
+    def solve(self, A: CSR, b: torch.Tensor, tol: float, x: torch.Tensor,
+              allow=(0, 1)) -> dict:
+        info = SeqInfo()
+        rc = self._lib.seq_solve(self._h, ctypes.byref(A._c()), _ptr(b, torch.float64, self.n),
+                                 ctypes.c_double(tol), _ptr(x, torch.float64, self.n),
+                                 ctypes.byref(info))
+        self._check(rc, info, allow)
+        d = info.as_dict()
+        d["rc"] = rc
+        return d
+
+    def last_sketch(self):
+        """(W, y) of the last guess as float64 CPU tensors, oldest history column first."""
+        m = None
+        import numpy as np
+        W = np.zeros(self.s * (self.M + 1))
+        y = np.zeros(self.M)
+        rc = self._lib.seq_last_sketch(self._h, W.ctypes.data, y.ctypes.data)
+        self._check(rc)
+        return W, y
+
+
+def sketch_columns(n: int, s: int, zeta: int, seed: int):
+    """(rows int32 [n, zeta], signs int8 [n, zeta]) of the sparse-sign sketch, on the device."""
+    lib = load()
+    rows = torch.empty((n, zeta), dtype=torch.int32, device="cuda")
+    signs = torch.empty((n, zeta), dtype=torch.int8, device="cuda")
+    rc = lib.seq_sketch_columns(n, s, zeta, seed, rows.data_ptr(), signs.data_ptr(),
+                                ctypes.c_void_p(_stream()))
+    if rc != 0:
+        raise SeqError(rc, "seq_sketch_columns failed")
+    return rows, signs
+
+
+def probe_fp64_peak() -> float:
+    """Measured FP64 FMA throughput of the current device in TFLOP/s."""
+    lib = load()
+    out = ctypes.c_double()
+    rc = lib.seq_probe_fp64_peak(ctypes.c_void_p(_stream()), ctypes.byref(out))
+    if rc != 0:
+        raise SeqError(rc, "seq_probe_fp64_peak failed")
+    return out.value

@@ -1,0 +1,552 @@
+// C-ABI of libseqaccel (declared in include/seqaccel.h): context management
+// and the host orchestration of the guess (Algorithm 1, steps 1-3) and the
+// Krylov solve (step 4).  Device memory is allocated once per context; every
+// call is ordered on the context's stream and synchronises only where a
+// seq_info is returned (once per GMRES restart cycle inside seq_solve).
+#include <math.h>
+#include <stddef.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/seqaccel.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace sa;
+
+struct seq_ctx {
+    seq_config cfg;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;      // private stream used only for graph capture
+    int dev = 0;
+    bool mixed = false;
+    int ldx = 0;
+    void* X = nullptr;               // history ring, n x ldx (double or float)
+    int pushes = 0;
+    uint16_t* sk = nullptr;          // packed sketch, n x zeta
+    void* sk_partial = nullptr;
+    int sk_nblk = 0;
+    double* W = nullptr;             // s*(M+1) + 1
+    LsqOut* lsq = nullptr;
+    LsqOut* lsq_host = nullptr;      // pinned
+    int nblk = 0;
+    double* kpartial = nullptr;      // nblk * 64 doubles
+    size_t ldv = 0;
+    void* V = nullptr;               // (restart+1) x ldv basis (GMRES)
+    void* w = nullptr;
+    void* r = nullptr;               // CG vectors
+    void* p = nullptr;
+    void* q = nullptr;
+    float* val32 = nullptr;          // rounded matrix values (mixed, when not supplied)
+    int val32_cap = 0;
+    float* rhs32 = nullptr;
+    float* d = nullptr;
+    DevArgs* d_args = nullptr;       // outer (FP64) system
+    DevArgs* h_args = nullptr;       // pinned staging
+    DevArgs* d_args_in = nullptr;    // inner (FP32) system
+    DevArgs* h_args_in = nullptr;
+    KState* ks = nullptr;            // outer / FP64 solve state
+    KState* ks_in = nullptr;         // inner solve state
+    KState* h_ks = nullptr;          // pinned mirror of the state tail
+    cudaGraphExec_t cycle = nullptr;
+    int cycle_launches = 0;
+    int launches = 0;
+    std::string err;
+};
+
+namespace {
+
+const size_t kTailOff = offsetof(KState, beta);
+const size_t kTailLen = offsetof(KState, counter) - offsetof(KState, beta);
+
+int fail(seq_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(ctx, SEQ_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+int check_csr(seq_ctx* ctx, const seq_csr* A) {
+    if (!A) return fail(ctx, SEQ_EINVAL, "A is NULL");
+    if (A->n != ctx->cfg.n) return fail(ctx, SEQ_EINVAL, "A->n differs from the context's n");
+    if (A->nnz < 0) return fail(ctx, SEQ_EINVAL, "A->nnz < 0");
+    if (!A->rowptr || (A->nnz > 0 && (!A->colind || !A->values)))
+        return fail(ctx, SEQ_EINVAL, "A has a NULL array");
+    return SEQ_OK;
+}
+
+// Copy the state tail (beta .. bad_index) of a device KState into h_ks.
+int read_tail(seq_ctx* ctx, const KState* ks) {
+    CK(cudaMemcpyAsync(reinterpret_cast<char*>(ctx->h_ks) + kTailOff,
+                       reinterpret_cast<const char*>(ks) + kTailOff, kTailLen,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SEQ_OK;
+}
+
+int set_args(seq_ctx* ctx, const seq_csr* A, const double* b, double* x, double tol,
+             int max_iters) {
+    DevArgs* h = ctx->h_args;
+    memset(h, 0, sizeof(DevArgs));
+    h->rowptr = A->rowptr;
+    h->colind = A->colind;
+    h->val64 = A->values;
+    h->val32 = A->values_f32 ? A->values_f32 : ctx->val32;
+    h->b = b;
+    h->x = x;
+    h->d = ctx->d;
+    h->rhs32 = ctx->rhs32;
+    h->n = A->n;
+    h->nnz = A->nnz;
+    h->max_iters = max_iters;
+    h->tol = tol;
+    CK(cudaMemcpyAsync(ctx->d_args, h, sizeof(DevArgs), cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->mixed) {
+        memcpy(ctx->h_args_in, h, sizeof(DevArgs));
+        CK(cudaMemcpyAsync(ctx->d_args_in, ctx->h_args_in, sizeof(DevArgs),
+                           cudaMemcpyHostToDevice, ctx->stream));
+    }
+    return SEQ_OK;
+}
+
+int ensure_val32(seq_ctx* ctx, const seq_csr* A) {
+    if (!ctx->mixed || A->values_f32) return SEQ_OK;
+    if (A->nnz > ctx->val32_cap) {
+        if (ctx->val32) cudaFree(ctx->val32);
+        ctx->val32 = nullptr;
+        ctx->val32_cap = 0;
+        if (cudaMalloc(&ctx->val32, sizeof(float) * (size_t)(A->nnz > 0 ? A->nnz : 1)) != cudaSuccess)
+            return fail(ctx, SEQ_ENOMEM, "cannot allocate the FP32 copy of A");
+        ctx->val32_cap = A->nnz;
+    }
+    launch_round_f32(A->values, ctx->val32, A->nnz, ctx->stream);
+    ctx->launches += 1;
+    return SEQ_OK;
+}
+
+int capture_cycle(seq_ctx* ctx) {
+    if (ctx->cycle) return SEQ_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    const int R = ctx->cfg.restart;
+    if (!ctx->mixed)
+        launch_gmres_cycle_f64(ctx->d_args, ctx->ks, (double*)ctx->V, ctx->ldv, (double*)ctx->w,
+                               ctx->kpartial, ctx->nblk, R, ctx->cap, &ctx->cycle_launches);
+    else
+        launch_gmres_cycle_f32(ctx->d_args_in, ctx->ks_in, (float*)ctx->V, ctx->ldv,
+                               (float*)ctx->w, (float*)ctx->kpartial, ctx->nblk, R, ctx->cap,
+                               &ctx->cycle_launches);
+    CK(cudaStreamEndCapture(ctx->cap, &g));
+    cudaError_t e = cudaGraphInstantiate(&ctx->cycle, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ctx->cycle = nullptr;
+        return fail(ctx, SEQ_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    return SEQ_OK;
+}
+
+// One restarted GMRES solve on the system bound to (args, ks); `f32` selects
+// the FP32 inner kernels.  Returns a seq_status; h_ks holds the final tail.
+int run_gmres(seq_ctx* ctx, bool f32) {
+    KState* ks = f32 ? ctx->ks_in : ctx->ks;
+    if (!f32)
+        launch_gmres_start_f64(ctx->d_args, ks, (double*)ctx->V, ctx->ldv, ctx->kpartial,
+                               ctx->nblk, 1, ctx->stream);
+    else
+        launch_gmres_start_f32(ctx->d_args_in, ks, (float*)ctx->V, ctx->ldv,
+                               (float*)ctx->kpartial, ctx->nblk, 1, ctx->stream);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    int rc = read_tail(ctx, ks);
+    if (rc) return rc;
+    rc = capture_cycle(ctx);
+    if (rc) return rc;
+    // The iteration cap bounds the number of cycles: each unfinished cycle
+    // performs at least one Arnoldi step.
+    const long max_cycles = (long)ctx->cfg.max_iters + 2;
+    long cycles = 0;
+    while (!ctx->h_ks->finished) {
+        if (++cycles > max_cycles) return fail(ctx, SEQ_ETIMEOUT, "GMRES cycle bound exceeded");
+        CK(cudaGraphLaunch(ctx->cycle, ctx->stream));
+        ctx->launches += ctx->cycle_launches;
+        rc = read_tail(ctx, ks);
+        if (rc) return rc;
+    }
+    return SEQ_OK;
+}
+
+void fill_info(seq_info* info, const KState* t) {
+    if (!info) return;
+    info->guess_relres = t->first_relres;
+    info->final_relres = t->bnorm > 0 ? t->beta / t->bnorm : t->beta;
+    info->iters = t->iters;
+    info->status = t->status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
+    if (!out) return SEQ_EINVAL;
+    *out = nullptr;
+    if (!cfg) return SEQ_EINVAL;
+    const seq_config& c = *cfg;
+    if (c.n <= 0 || c.M < 1 || c.M > kMaxM || c.s < c.M + 1 || c.s > kMaxS || c.zeta < 1 ||
+        c.zeta > c.s || c.zeta > kMaxZeta || c.restart < 1 || c.restart > kMaxRestart ||
+        c.max_iters < 0 || (c.precision != SEQ_F64 && c.precision != SEQ_MIXED) ||
+        c.guess < SEQ_GUESS_ZERO || c.guess > SEQ_GUESS_LEARNED ||
+        (c.krylov != SEQ_CG && c.krylov != SEQ_GMRES))
+        return SEQ_EINVAL;
+    seq_ctx* ctx = new seq_ctx();
+    ctx->cfg = c;
+    if (ctx->cfg.inner_tol <= 0) ctx->cfg.inner_tol = 1e-2;
+    if (ctx->cfg.rank_tol <= 0) ctx->cfg.rank_tol = c.precision == SEQ_MIXED ? 1e-5 : 1e-12;
+    ctx->mixed = c.precision == SEQ_MIXED;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    const int n = c.n, M = c.M, s = c.s;
+    const size_t el = ctx->mixed ? sizeof(float) : sizeof(double);
+    ctx->ldx = ctx->mixed ? round_up(M, 8) : round_up(M, 4);
+    bool ok = cudaGetDevice(&ctx->dev) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaMalloc(&ctx->X, el * (size_t)n * ctx->ldx) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(ctx->X, 0, el * (size_t)n * ctx->ldx, ctx->stream) == cudaSuccess;
+    ok = ok && cudaMalloc(&ctx->sk, sizeof(uint16_t) * (size_t)n * c.zeta) == cudaSuccess;
+    ctx->sk_nblk = sketch_grid(n);
+    ok = ok && cudaMalloc(&ctx->sk_partial, el * (size_t)ctx->sk_nblk * (s * (M + 1) + 1)) == cudaSuccess;
+    ok = ok && cudaMalloc(&ctx->W, sizeof(double) * (s * (M + 1) + 1)) == cudaSuccess;
+    ok = ok && cudaMalloc(&ctx->lsq, sizeof(LsqOut)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&ctx->lsq_host, sizeof(LsqOut)) == cudaSuccess;
+    ctx->nblk = stream_grid(n);
+    ok = ok && cudaMalloc(&ctx->kpartial, sizeof(double) * (size_t)ctx->nblk * 64) == cudaSuccess;
+    ctx->ldv = (size_t)round_up(n, 64);
+    if (c.krylov == SEQ_GMRES) {
+        ok = ok && cudaMalloc(&ctx->V, el * ctx->ldv * (c.restart + 1)) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->w, el * ctx->ldv) == cudaSuccess;
+    } else {
+        ok = ok && cudaMalloc(&ctx->r, el * (size_t)n) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->p, el * (size_t)n) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->q, el * (size_t)n) == cudaSuccess;
+    }
+    if (ctx->mixed) {
+        ok = ok && cudaMalloc(&ctx->rhs32, sizeof(float) * (size_t)n) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->d, sizeof(float) * (size_t)n) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc(&ctx->d_args, sizeof(DevArgs)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&ctx->h_args, sizeof(DevArgs)) == cudaSuccess;
+    ok = ok && cudaMalloc(&ctx->d_args_in, sizeof(DevArgs)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&ctx->h_args_in, sizeof(DevArgs)) == cudaSuccess;
+    ok = ok && cudaMalloc(&ctx->ks, sizeof(KState)) == cudaSuccess;
+    ok = ok && cudaMalloc(&ctx->ks_in, sizeof(KState)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&ctx->h_ks, sizeof(KState)) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(ctx->ks, 0, sizeof(KState), ctx->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(ctx->ks_in, 0, sizeof(KState), ctx->stream) == cudaSuccess;
+    if (ok) {
+        launch_sketch_columns(n, s, c.zeta, c.seed, ctx->sk, nullptr, nullptr, ctx->stream);
+        ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(ctx->stream) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        seq_destroy(ctx);
+        return SEQ_ENOMEM;
+    }
+    *out = ctx;
+    return SEQ_OK;
+}
+
+int seq_destroy(seq_ctx* ctx) {
+    if (!ctx) return SEQ_OK;
+    if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+    if (ctx->cycle) cudaGraphExecDestroy(ctx->cycle);
+    void* dev_ptrs[] = {ctx->X, ctx->sk, ctx->sk_partial, ctx->W, ctx->lsq, ctx->kpartial,
+                        ctx->V, ctx->w, ctx->r, ctx->p, ctx->q, ctx->val32, ctx->rhs32, ctx->d,
+                        ctx->d_args, ctx->d_args_in, ctx->ks, ctx->ks_in};
+    for (void* p : dev_ptrs)
+        if (p) cudaFree(p);
+    void* host_ptrs[] = {ctx->lsq_host, ctx->h_args, ctx->h_args_in, ctx->h_ks};
+    for (void* p : host_ptrs)
+        if (p) cudaFreeHost(p);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    delete ctx;
+    return SEQ_OK;
+}
+
+int seq_push_solution(seq_ctx* ctx, const double* x_dev) {
+    if (!ctx || !x_dev) return fail(ctx, SEQ_EINVAL, "NULL argument");
+    const int slot = ctx->pushes % ctx->cfg.M;
+    if (ctx->mixed)
+        launch_push_f32(x_dev, ctx->cfg.n, (float*)ctx->X, ctx->ldx, slot, ctx->stream);
+    else
+        launch_push_f64(x_dev, ctx->cfg.n, (double*)ctx->X, ctx->ldx, slot, ctx->stream);
+    CK(cudaGetLastError());
+    ctx->pushes += 1;
+    ctx->launches = 1;
+    return SEQ_OK;
+}
+
+int seq_history_size(const seq_ctx* ctx) {
+    if (!ctx) return 0;
+    return ctx->pushes < ctx->cfg.M ? ctx->pushes : ctx->cfg.M;
+}
+
+int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_dev, seq_info* info) {
+    if (!ctx) return SEQ_EINVAL;
+    ctx->err.clear();
+    ctx->launches = 0;
+    int rc = check_csr(ctx, A);
+    if (rc) return rc;
+    if (!b_dev || !x0_dev) return fail(ctx, SEQ_EINVAL, "NULL vector");
+    const seq_config& c = ctx->cfg;
+    const int n = c.n, M = c.M;
+    const int m = seq_history_size(ctx);
+    int mode = c.guess;
+    if (mode == SEQ_GUESS_LEARNED) mode = SEQ_GUESS_SKETCH;
+    if (m == 0 && mode != SEQ_GUESS_ZERO) mode = SEQ_GUESS_ZERO;
+    CK(cudaMemsetAsync(ctx->ks, 0, sizeof(KState), ctx->stream));
+    int rank = 0;
+    double rho = 0.0;
+    if (mode == SEQ_GUESS_ZERO) {
+        CK(cudaMemsetAsync(x0_dev, 0, sizeof(double) * (size_t)n, ctx->stream));
+    } else if (mode == SEQ_GUESS_PREV) {
+        const int slot = (ctx->pushes - 1) % M;
+        if (ctx->mixed)
+            launch_copy_slot_f32((const float*)ctx->X, ctx->ldx, n, slot, x0_dev, ctx->stream);
+        else
+            launch_copy_slot_f64((const double*)ctx->X, ctx->ldx, n, slot, x0_dev, ctx->stream);
+        ctx->launches += 1;
+    } else {
+        int* bad = &ctx->ks->bad_index;
+        if (ctx->mixed) {
+            rc = ensure_val32(ctx, A);
+            if (rc) return rc;
+            const float* v32 = A->values_f32 ? A->values_f32 : ctx->val32;
+            launch_sketch_f32(A->rowptr, A->colind, v32, (const float*)ctx->X, ctx->ldx, b_dev,
+                              ctx->sk, n, A->nnz, M, c.s, c.zeta, (float*)ctx->sk_partial,
+                              ctx->sk_nblk, ctx->W, bad, ctx->stream);
+        } else {
+            launch_sketch_f64(A->rowptr, A->colind, A->values, (const double*)ctx->X, ctx->ldx,
+                              b_dev, ctx->sk, n, A->nnz, M, c.s, c.zeta, (double*)ctx->sk_partial,
+                              ctx->sk_nblk, ctx->W, bad, ctx->stream);
+        }
+        const int oldest = (ctx->pushes - m) % M;
+        launch_lsq(ctx->W, c.s, M, m, oldest, c.rank_tol, ctx->lsq, ctx->stream);
+        if (ctx->mixed)
+            launch_expand_f32((const float*)ctx->X, ctx->ldx, n, M, ctx->lsq, x0_dev, ctx->stream);
+        else
+            launch_expand_f64((const double*)ctx->X, ctx->ldx, n, M, ctx->lsq, x0_dev, ctx->stream);
+        ctx->launches += 4;
+        CK(cudaMemcpyAsync(ctx->lsq_host, ctx->lsq, offsetof(LsqOut, W_logical),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(&ctx->lsq_host->rho, &ctx->lsq->rho,
+                           sizeof(LsqOut) - offsetof(LsqOut, rho), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    }
+    rc = set_args(ctx, A, b_dev, x0_dev, 1.0, 0);
+    if (rc) return rc;
+    launch_residual_norm(ctx->d_args, ctx->ks, ctx->kpartial, ctx->nblk, nullptr, ctx->stream);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    rc = read_tail(ctx, ctx->ks);
+    if (rc) return rc;
+    if (mode == SEQ_GUESS_SKETCH) {
+        rank = ctx->lsq_host->rank;
+        rho = ctx->lsq_host->rho;
+    }
+    if (info) {
+        memset(info, 0, sizeof(seq_info));
+        info->history_cols = mode == SEQ_GUESS_ZERO ? 0 : (mode == SEQ_GUESS_PREV ? 1 : m);
+        info->rank = rank;
+        info->sketch_resid = rho;
+        info->guess_relres = ctx->h_ks->first_relres;
+        info->final_relres = ctx->h_ks->first_relres;
+        info->launches = ctx->launches;
+    }
+    ctx->lsq_host->m = (mode == SEQ_GUESS_SKETCH) ? m : 0;
+    if (ctx->h_ks->bad_index) {
+        if (info) info->status = SEQ_EINVAL;
+        return fail(ctx, SEQ_EINVAL, "CSR column index outside [0, n)");
+    }
+    if (!isfinite(ctx->h_ks->first_relres)) {
+        if (info) info->status = SEQ_ENONFINITE;
+        return fail(ctx, SEQ_ENONFINITE, "non-finite residual of the guess");
+    }
+    return SEQ_OK;
+}
+
+int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, double* x_dev,
+              seq_info* info) {
+    if (!ctx) return SEQ_EINVAL;
+    ctx->err.clear();
+    ctx->launches = 0;
+    int rc = check_csr(ctx, A);
+    if (rc) return rc;
+    if (!b_dev || !x_dev) return fail(ctx, SEQ_EINVAL, "NULL vector");
+    if (!(tol > 0.0)) return fail(ctx, SEQ_EINVAL, "tol must be > 0");
+    const seq_config& c = ctx->cfg;
+    if (info) memset(info, 0, sizeof(seq_info));
+    CK(cudaMemsetAsync(ctx->ks, 0, sizeof(KState), ctx->stream));
+    CK(cudaMemsetAsync(ctx->ks_in, 0, sizeof(KState), ctx->stream));
+    rc = ensure_val32(ctx, A);
+    if (rc) return rc;
+    rc = set_args(ctx, A, b_dev, x_dev, tol, c.max_iters);
+    if (rc) return rc;
+    int status = SEQ_OK;
+    if (!ctx->mixed) {
+        if (c.krylov == SEQ_GMRES) {
+            rc = run_gmres(ctx, false);
+            if (rc) return rc;
+        } else {
+            launch_cg_block_f64(ctx->d_args, ctx->ks, (double*)ctx->r, (double*)ctx->p,
+                                (double*)ctx->q, ctx->stream);
+            ctx->launches += 1;
+            CK(cudaGetLastError());
+            rc = read_tail(ctx, ctx->ks);
+            if (rc) return rc;
+        }
+        fill_info(info, ctx->h_ks);
+        status = ctx->h_ks->status;
+    } else {
+        // FP64 iterative refinement around FP32 inner solves.
+        const double theta = 0.5;
+        int total = 0, refinements = 0;
+        launch_refine_residual(ctx->d_args, ctx->ks, ctx->rhs32, ctx->kpartial, ctx->nblk,
+                               ctx->stream);
+        ctx->launches += 1;
+        CK(cudaGetLastError());
+        rc = read_tail(ctx, ctx->ks);
+        if (rc) return rc;
+        const double bnorm = ctx->h_ks->bnorm, target = ctx->h_ks->target;
+        const double first = ctx->h_ks->beta / bnorm;
+        double beta = ctx->h_ks->beta;
+        int bad = ctx->h_ks->bad_index;
+        status = SEQ_OK;
+        const int max_ref = 100;
+        while (beta > target) {
+            if (!isfinite(beta)) {
+                status = SEQ_ENONFINITE;
+                break;
+            }
+            if (total >= c.max_iters || refinements >= max_ref) {
+                status = SEQ_NOT_CONVERGED;
+                break;
+            }
+            DevArgs* hi = ctx->h_args_in;
+            hi->tol = fmax(c.inner_tol, theta * target / beta);
+            hi->max_iters = c.max_iters - total;
+            CK(cudaMemcpyAsync(ctx->d_args_in, hi, sizeof(DevArgs), cudaMemcpyHostToDevice,
+                               ctx->stream));
+            if (c.krylov == SEQ_GMRES) {
+                rc = run_gmres(ctx, true);
+                if (rc) return rc;
+            } else {
+                launch_cg_block_f32(ctx->d_args_in, ctx->ks_in, (float*)ctx->r, (float*)ctx->p,
+                                    (float*)ctx->q, ctx->stream);
+                ctx->launches += 1;
+                CK(cudaGetLastError());
+                rc = read_tail(ctx, ctx->ks_in);
+                if (rc) return rc;
+            }
+            bad |= ctx->h_ks->bad_index;
+            total += ctx->h_ks->iters;
+            refinements += 1;
+            const int ist = ctx->h_ks->status;
+            if (ist == SEQ_EBREAKDOWN || ist == SEQ_ENONFINITE) {
+                status = ist;
+                break;
+            }
+            launch_refine_update(ctx->d_args, nullptr, 0.0, nullptr, ctx->stream);
+            launch_refine_residual(ctx->d_args, ctx->ks, ctx->rhs32, ctx->kpartial, ctx->nblk,
+                                   ctx->stream);
+            ctx->launches += 2;
+            CK(cudaGetLastError());
+            rc = read_tail(ctx, ctx->ks);
+            if (rc) return rc;
+            beta = ctx->h_ks->beta;
+            bad |= ctx->h_ks->bad_index;
+        }
+        if (info) {
+            info->iters = total;
+            info->refinements = refinements;
+            info->guess_relres = first;
+            info->final_relres = beta / bnorm;
+            info->status = status;
+        }
+        if (bad) status = SEQ_EINVAL;
+    }
+    if (info) info->launches = ctx->launches;
+    if (ctx->h_ks->bad_index) {
+        if (info) info->status = SEQ_EINVAL;
+        return fail(ctx, SEQ_EINVAL, "CSR column index outside [0, n)");
+    }
+    if (status == SEQ_NOT_CONVERGED) ctx->err = "iteration cap reached";
+    return status;
+}
+
+const char* seq_last_error(const seq_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+int seq_last_sketch(seq_ctx* ctx, double* W_host, double* y_host) {
+    if (!ctx) return SEQ_EINVAL;
+    const int m = ctx->lsq_host->m;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (W_host && m > 0)
+        CK(cudaMemcpy(W_host, ctx->lsq->W_logical, sizeof(double) * ctx->cfg.s * (m + 1),
+                      cudaMemcpyDeviceToHost));
+    if (y_host && m > 0)
+        CK(cudaMemcpy(y_host, ctx->lsq->y_logical, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    return SEQ_OK;
+}
+
+int seq_sketch_columns(int32_t n, int32_t s, int32_t zeta, uint64_t seed, int32_t* rows_dev,
+                       int8_t* signs_dev, void* cuda_stream) {
+    if (n <= 0 || s < 1 || s > 32767 || zeta < 1 || zeta > s || zeta > kMaxZeta || !rows_dev ||
+        !signs_dev)
+        return SEQ_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    launch_sketch_columns(n, s, zeta, seed, nullptr, rows_dev, signs_dev, st);
+    if (cudaGetLastError() != cudaSuccess) return SEQ_ECUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? SEQ_OK : SEQ_ECUDA;
+}
+
+int seq_probe_fp64_peak(void* cuda_stream, double* tflops) {
+    if (!tflops) return SEQ_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SEQ_ECUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * 8, threads = 256, iters = 1 << 13;
+    double* out = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * blocks * threads) != cudaSuccess) return SEQ_ENOMEM;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, st);
+        launch_fp64_probe(out, blocks, threads, iters, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess) return SEQ_ECUDA;
+    // 8 independent FMA chains per thread, 2 flops each.
+    *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+    return SEQ_OK;
+}
+
+}  // extern "C"

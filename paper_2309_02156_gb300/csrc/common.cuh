@@ -1,0 +1,192 @@
+// Device helpers shared by the seqaccel kernels (sm_103a).
+//
+// Reductions are deterministic: every partial sum has a fixed owner and is
+// combined in a fixed order (warp butterfly, then warps in index order, then
+// blocks in index order by the last block to finish), so results do not
+// depend on scheduling and repeat bit for bit from run to run.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sa {
+
+constexpr int kWarp = 32;
+constexpr int kMaxBasis = 65;     // GMRES restart <= 64 -> at most 65 basis vectors
+constexpr int kMaxRestart = 64;
+constexpr int kMaxM = 31;         // history length (M + 1 <= 32 lanes in the sketch kernel)
+constexpr int kMaxS = 128;        // sketch rows
+constexpr int kMaxZeta = 16;
+constexpr int kStreamBlock = 256; // threads per block of the streaming kernels
+
+// Device-side copy of the per-call arguments.  The CUDA graphs of a context
+// take a pointer to this struct, so one captured graph serves every call.
+struct DevArgs {
+    const int* rowptr;
+    const int* colind;
+    const double* val64;
+    const float* val32;
+    const double* b;
+    double* x;          // FP64 iterate (GMRES/CG on the FP64 system, or the
+                        // refinement iterate in mixed precision)
+    void* d;            // inner correction vector (mixed precision, FP32)
+    const float* rhs32; // inner right-hand side (mixed precision)
+    int n;
+    int nnz;
+    int max_iters;
+    int pad0;
+    double tol;         // relative tolerance of this solve
+};
+
+// State of one restarted GMRES / CG solve, kept on the device.
+struct KState {
+    double sigma[kMaxBasis];        // stored basis column k = v_k / sigma_k
+    double h1[kMaxBasis];           // first CGS pass coefficients
+    double h2[kMaxBasis];           // second CGS pass coefficients
+    double c1[kMaxBasis];           // sigma_k * h1_k (applied to stored columns)
+    double c2[kMaxBasis];           // sigma_k * h2_k
+    double H[kMaxBasis * kMaxRestart];  // rotated Hessenberg, column-major (ld kMaxBasis)
+    double cs[kMaxRestart];
+    double sn[kMaxRestart];
+    double g[kMaxBasis];
+    double cy[kMaxBasis];           // sigma_k * y_k for the basis update
+    double beta;                    // ||r|| at the last cycle start
+    double bnorm;                   // ||b||
+    double target;                  // tol * ||b||
+    double first_relres;            // relative residual of the starting vector
+    int cycle_over;                 // 1: Arnoldi steps of this cycle are finished
+    int finished;                   // 1: the solve is over (see status)
+    int jdone;                      // Arnoldi steps in the current cycle
+    int iters;                      // iterations of this solve
+    int status;                     // seq_status
+    int bad_index;                  // a CSR column index fell outside [0, n)
+    unsigned counter[8];            // last-block counters, one per kernel kind
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum K per-thread values over the block; on return red[k] (shared, >= K
+// entries) holds the block total of value k.  blockDim.x is a multiple of 32.
+template <typename T, int K>
+__device__ __forceinline__ void block_sum(T (&v)[K], int nk, T* red, T* scratch /* nwarps*K */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (k < nk) {
+            T s = warp_sum(v[k]);
+            if (lane == 0) scratch[warp * K + k] = s;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        T s = scratch[k];
+        for (int w = 1; w < nw; ++w) s += scratch[w * K + k];
+        red[k] = s;
+    }
+    __syncthreads();
+}
+
+// Returns true (in every thread) in the block that arrives last.  Each block
+// must have written its partials (by any of its threads) before calling.
+__device__ __forceinline__ bool last_block_arrive(unsigned* counter) {
+    __shared__ int am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(counter, 1u);
+        am_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (am_last) __threadfence();
+    return am_last != 0;
+}
+
+// Sum partial[blk * stride + k] over blocks 0..nblk-1 in index order, for
+// k < nk, by the threads of one block (one k per thread, four interleaved
+// accumulators combined in a fixed order).  Reads bypass L1.
+template <typename T>
+__device__ __forceinline__ T sum_over_blocks(const T* partial, int nblk, int stride, int k) {
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    int b = 0;
+    for (; b + 3 < nblk; b += 4) {
+        a0 += __ldcg(partial + (size_t)(b + 0) * stride + k);
+        a1 += __ldcg(partial + (size_t)(b + 1) * stride + k);
+        a2 += __ldcg(partial + (size_t)(b + 2) * stride + k);
+        a3 += __ldcg(partial + (size_t)(b + 3) * stride + k);
+    }
+    for (; b < nblk; ++b) a0 += __ldcg(partial + (size_t)b * stride + k);
+    return (a0 + a1) + (a2 + a3);
+}
+
+// SplitMix64 output finaliser (Steele, Lea, Flood 2014; variant-13 mixer).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Rows [lo, hi) owned by block `blk` when n rows are split into `nblk`
+// contiguous chunks whose length is a multiple of 32.
+__device__ __forceinline__ void block_rows(int n, int nblk, int blk, int& lo, int& hi) {
+    int chunk = (n + nblk - 1) / nblk;
+    chunk = (chunk + 31) & ~31;
+    lo = min(n, blk * chunk);
+    hi = min(n, lo + chunk);
+}
+
+// (A x)[row] for the 32 consecutive rows r0 .. r0+31 of one warp, lane l
+// returning row r0 + l (0 past the end).  The warp walks the tile's nonzeros
+// in 32-entry chunks with coalesced loads of colind/values, stages the
+// products in shared memory and each lane sums the entries of its own row in
+// CSR order.  Column indices outside [0, n) contribute 0 and raise *bad.
+template <typename Acc, typename VT, typename XT>
+__device__ __forceinline__ Acc warp_tile_spmv(const int* __restrict__ rowptr,
+                                              const int* __restrict__ colind,
+                                              const VT* __restrict__ val,
+                                              const XT* __restrict__ x, int n, int nnz,
+                                              int r0, Acc* sprod, int* bad) {
+    const int lane = threadIdx.x & 31;
+    const int row = r0 + lane;
+    int rs = 0, re = 0;
+    if (row < n) {
+        rs = __ldg(rowptr + row);
+        re = __ldg(rowptr + row + 1);
+        rs = max(0, min(rs, nnz));
+        re = max(rs, min(re, nnz));
+    }
+    const int last = min(31, n - 1 - r0);
+    const int e0 = __shfl_sync(0xffffffffu, rs, 0);
+    const int e1 = __shfl_sync(0xffffffffu, re, last);
+    Acc acc = 0;
+    int flag = 0;
+    for (int base = e0; base < e1; base += 32) {
+        const int e = base + lane;
+        Acc prod = 0;
+        if (e < e1) {
+            const int c = __ldg(colind + e);
+            if ((unsigned)c < (unsigned)n) {
+                prod = (Acc)__ldg(val + e) * (Acc)x[c];
+            } else {
+                flag = 1;
+            }
+        }
+        sprod[lane] = prod;
+        __syncwarp();
+        const int lo = max(rs, base), hi = min(re, base + 32);
+        for (int k = lo; k < hi; ++k) acc += sprod[k - base];
+        __syncwarp();
+    }
+    if (flag) atomicOr(bad, 1);
+    return acc;
+}
+
+}  // namespace sa

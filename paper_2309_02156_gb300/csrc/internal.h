@@ -1,0 +1,75 @@
+// Host-side launchers of the seqaccel kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace sa {
+
+// sketch.cu
+int sketch_grid(int n);
+void launch_sketch_columns(int n, int s, int zeta, uint64_t seed, uint16_t* packed,
+                           int32_t* rows, int8_t* signs, cudaStream_t st);
+void launch_sketch_f64(const int* rowptr, const int* colind, const double* val, const double* X,
+                       int ldx, const double* b, const uint16_t* sk, int n, int nnz, int M, int s,
+                       int zeta, double* partial, int nblk, double* W, int* bad, cudaStream_t st);
+void launch_sketch_f32(const int* rowptr, const int* colind, const float* val, const float* X,
+                       int ldx, const double* b, const uint16_t* sk, int n, int nnz, int M, int s,
+                       int zeta, float* partial, int nblk, double* W, int* bad, cudaStream_t st);
+
+// lsq.cu
+struct LsqOut {
+    double y_logical[kMaxM];
+    double y_phys[kMaxM];
+    double W_logical[kMaxS * (kMaxM + 1)];   // s x (m+1), row-major, b last
+    double rho;
+    int rank;
+    int m;
+};
+void launch_lsq(const double* W, int s, int M, int m, int oldest_slot, double tau, LsqOut* out,
+                cudaStream_t st);
+void launch_expand_f64(const double* X, int ldx, int n, int M, const LsqOut* lo, double* x0,
+                       cudaStream_t st);
+void launch_expand_f32(const float* X, int ldx, int n, int M, const LsqOut* lo, double* x0,
+                       cudaStream_t st);
+void launch_copy_slot_f64(const double* X, int ldx, int n, int slot, double* x0, cudaStream_t st);
+void launch_copy_slot_f32(const float* X, int ldx, int n, int slot, double* x0, cudaStream_t st);
+void launch_push_f64(const double* x, int n, double* X, int ldx, int slot, cudaStream_t st);
+void launch_push_f32(const double* x, int n, float* X, int ldx, int slot, cudaStream_t st);
+
+// krylov.cu
+int stream_grid(int n);
+// ||b - A x|| and ||b|| of FP64 vectors; results in st->beta, st->bnorm and
+// st->first_relres = beta / bnorm.
+void launch_residual_norm(const DevArgs* a, KState* ks, double* partial, int nblk,
+                          const double* x_override, cudaStream_t st);
+// Restarted GMRES(R) with CGS2 on the FP64 system: the start kernel and one
+// full cycle (R Arnoldi steps, basis update, residual of the updated iterate).
+void launch_gmres_start_f64(const DevArgs* a, KState* ks, double* V, size_t ldv, double* partial,
+                            int nblk, int first, cudaStream_t st);
+void launch_gmres_cycle_f64(const DevArgs* a, KState* ks, double* V, size_t ldv, double* w,
+                            double* partial, int nblk, int R, cudaStream_t st, int* launches);
+// Same on the FP32 inner system A32 d = rhs32 (mixed precision).
+void launch_gmres_start_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, float* partial,
+                            int nblk, int first, cudaStream_t st);
+void launch_gmres_cycle_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, float* w,
+                            float* partial, int nblk, int R, cudaStream_t st, int* launches);
+// Mixed precision outer step: x += scale * d (FP64 += FP32), then the FP64
+// residual r = b - A64 x, its norm, and rhs32 = r / ||r||.
+void launch_refine_residual(const DevArgs* a, KState* ks, float* rhs32, double* partial, int nblk,
+                            cudaStream_t st);
+void launch_refine_update(const DevArgs* a, const KState* inner, double scale_from_outer_beta,
+                          KState* outer, cudaStream_t st);
+// Single-block CG (T = double: FP64 system; the kernel loops on the device).
+void launch_cg_block_f64(const DevArgs* a, KState* ks, double* r, double* p, double* q,
+                         cudaStream_t st);
+void launch_cg_block_f32(const DevArgs* a, KState* ks, float* r, float* p, float* q,
+                         cudaStream_t st);
+void launch_round_f32(const double* src, float* dst, int n, cudaStream_t st);
+
+// probe.cu
+void launch_fp64_probe(double* out, int blocks, int threads, int iters, cudaStream_t st);
+
+}  // namespace sa

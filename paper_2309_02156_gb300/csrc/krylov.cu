@@ -1,0 +1,641 @@
+// Krylov solvers started from the subspace guess (Algorithm 1, step 4; the
+// paper uses GMRES for general matrices and names CG for SPD ones, Section 1).
+//
+// Restarted GMRES(R) with CGS2 Arnoldi.  One Arnoldi step j is three
+// streaming kernels over the n rows, each ending with a deterministic
+// last-block reduction:
+//   K5  w = A v_j (warp-tile CSR SpMV)        and h1 = V_j^T w     (dots fused)
+//   K7a w -= V_j h1                            and h2 = V_j^T w     (fused: V read once)
+//   K7b w -= V_j h2, v_{j+1} = w (unnormalised) and ||w||^2; the last block
+//       then forms the Hessenberg column h1 + h2, applies the Givens
+//       rotations, updates the residual estimate and decides whether the
+//       cycle ends (K8 folded in).
+// Basis columns are stored unnormalised with sigma_k = 1/||.|| kept on the
+// device, so no extra pass rescales them.  A cycle (R steps, the basis update
+// x += V y and the true residual of the new iterate) is captured once as a
+// CUDA graph; kernels after the end of a cycle return at once.
+//
+// The same templates run the FP32 inner solve of mixed precision (system
+// A32 d = rhs32 from d = 0, FP32 vectors and FP32 dot accumulation; the
+// Hessenberg and rotations stay FP64).
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sa {
+
+enum { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_BREAKDOWN = -4, ST_NONFINITE = -5 };
+enum { CNT_START = 0, CNT_DOT = 1, CNT_PASS2 = 2, CNT_PASS3 = 3, CNT_RES = 4, CNT_REFINE = 5 };
+
+struct SysF64 {
+    using T = double;
+    using V = double;
+    __device__ static const double* val(const DevArgs* a) { return a->val64; }
+    __device__ static const double* rhs(const DevArgs* a) { return a->b; }
+    __device__ static double* x(const DevArgs* a) { return a->x; }
+};
+struct SysF32 {
+    using T = float;
+    using V = float;
+    __device__ static const float* val(const DevArgs* a) { return a->val32; }
+    __device__ static const float* rhs(const DevArgs* a) { return a->rhs32; }
+    __device__ static float* x(const DevArgs* a) { return reinterpret_cast<float*>(a->d); }
+};
+
+int stream_grid(int n) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int want = sms * 2;
+    const int need = (n + kStreamBlock - 1) / kStreamBlock;
+    return need < want ? (need > 0 ? need : 1) : want;
+}
+
+// ---------------------------------------------------------------------------
+// ||b - A x|| and ||b|| (FP64); x_override replaces a->x when not NULL.
+__global__ void __launch_bounds__(kStreamBlock)
+residual_norm_kernel(const DevArgs* __restrict__ a, KState* ks, double* partial,
+                     const double* x_override) {
+    __shared__ double sprod[kStreamBlock];
+    __shared__ double scratch[(kStreamBlock / 32) * 2];
+    __shared__ double red[2];
+    const int n = a->n, nnz = a->nnz;
+    const double* x = x_override ? x_override : a->x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int lo, hi;
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    double acc[2] = {0.0, 0.0};
+    for (int r0 = lo + warp * 32; r0 < hi; r0 += nw * 32) {
+        const double ax = warp_tile_spmv<double>(a->rowptr, a->colind, a->val64, x, n, nnz, r0,
+                                                 sprod + warp * 32, &ks->bad_index);
+        const int row = r0 + lane;
+        if (row < n) {
+            const double bi = a->b[row];
+            const double r = bi - ax;
+            acc[0] += r * r;
+            acc[1] += bi * bi;
+        }
+    }
+    block_sum<double, 2>(acc, 2, red, scratch);
+    if (threadIdx.x < 2) partial[blockIdx.x * 2 + threadIdx.x] = red[threadIdx.x];
+    if (last_block_arrive(&ks->counter[CNT_RES])) {
+        if (threadIdx.x == 0) {
+            const double rr = sum_over_blocks(partial, gridDim.x, 2, 0);
+            const double bb = sum_over_blocks(partial, gridDim.x, 2, 1);
+            ks->beta = sqrt(rr);
+            ks->bnorm = sqrt(bb);
+            ks->first_relres = sqrt(rr) / sqrt(bb);
+            ks->counter[CNT_RES] = 0;
+        }
+    }
+}
+
+void launch_residual_norm(const DevArgs* a, KState* ks, double* partial, int nblk,
+                          const double* x_override, cudaStream_t st) {
+    residual_norm_kernel<<<nblk, kStreamBlock, 0, st>>>(a, ks, partial, x_override);
+}
+
+// ---------------------------------------------------------------------------
+// Cycle start: r = rhs - A x written to basis column 0, beta = ||r||.  With
+// first != 0 the solve is initialised (||rhs||, target, iteration count; the
+// FP32 inner solve also zeroes d, so r = rhs).
+template <class Sys>
+__global__ void __launch_bounds__(kStreamBlock)
+gmres_start_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* V,
+                   typename Sys::T* partial, int first) {
+    using T = typename Sys::T;
+    if (!first && ks->finished) return;
+    __shared__ T sprod[kStreamBlock];
+    __shared__ T scratch[(kStreamBlock / 32) * 2];
+    __shared__ T red[2];
+    const int n = a->n, nnz = a->nnz;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T* x = Sys::x(a);
+    const T* rhs = Sys::rhs(a);
+    const bool zero_x = first && (sizeof(T) == 4);
+    int lo, hi;
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    T acc[2] = {0, 0};
+    for (int r0 = lo + warp * 32; r0 < hi; r0 += nw * 32) {
+        T ax = 0;
+        if (!zero_x)
+            ax = warp_tile_spmv<T>(a->rowptr, a->colind, Sys::val(a), x, n, nnz, r0,
+                                   sprod + warp * 32, &ks->bad_index);
+        const int row = r0 + lane;
+        if (row < n) {
+            const T bi = rhs[row];
+            const T r = bi - ax;
+            V[row] = r;
+            if (zero_x) x[row] = 0;
+            acc[0] += r * r;
+            acc[1] += bi * bi;
+        }
+    }
+    block_sum<T, 2>(acc, 2, red, scratch);
+    if (threadIdx.x < 2) partial[blockIdx.x * 2 + threadIdx.x] = red[threadIdx.x];
+    if (last_block_arrive(&ks->counter[CNT_START])) {
+        if (threadIdx.x == 0) {
+            const double rr = (double)sum_over_blocks(partial, gridDim.x, 2, 0);
+            const double beta = sqrt(rr);
+            if (first) {
+                const double bb = (double)sum_over_blocks(partial, gridDim.x, 2, 1);
+                ks->bnorm = sqrt(bb);
+                ks->target = a->tol * ks->bnorm;
+                ks->iters = 0;
+                ks->status = ST_OK;
+                ks->first_relres = beta / ks->bnorm;
+            }
+            ks->beta = beta;
+            ks->g[0] = beta;
+            ks->sigma[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+            ks->jdone = 0;
+            ks->cycle_over = 0;
+            ks->finished = 0;
+            if (!isfinite(beta)) {
+                ks->status = ST_NONFINITE;
+                ks->finished = 1;
+            } else if (beta <= ks->target) {
+                ks->status = ST_OK;
+                ks->finished = 1;
+            } else if (ks->iters >= a->max_iters) {
+                ks->status = ST_NOT_CONVERGED;
+                ks->finished = 1;
+            }
+            if (ks->finished) ks->cycle_over = 1;
+            ks->counter[CNT_START] = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5: w = sigma_j A vstored_j, h1 = sigma_k (V_stored^T w)_k for k <= j.
+template <class Sys, int KMAX>
+__global__ void __launch_bounds__(kStreamBlock)
+arnoldi_dot_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* V, size_t ldv,
+                   typename Sys::T* w, typename Sys::T* partial, int j) {
+    using T = typename Sys::T;
+    if (ks->cycle_over) return;
+    __shared__ T sprod[kStreamBlock];
+    __shared__ T scratch[(kStreamBlock / 32) * KMAX];
+    __shared__ T red[KMAX];
+    const int n = a->n, nnz = a->nnz, nk = j + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const T sig = (T)ks->sigma[j];
+    const T* vj = V + (size_t)j * ldv;
+    int lo, hi;
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    T part[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) part[k] = 0;
+    for (int r0 = lo + warp * 32; r0 < hi; r0 += nw * 32) {
+        const T ax = warp_tile_spmv<T>(a->rowptr, a->colind, Sys::val(a), vj, n, nnz, r0,
+                                       sprod + warp * 32, &ks->bad_index);
+        const int row = r0 + lane;
+        if (row < n) {
+            const T y = ax * sig;
+            w[row] = y;
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < nk) part[k] += V[(size_t)k * ldv + row] * y;
+        }
+    }
+    block_sum<T, KMAX>(part, nk, red, scratch);
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) partial[(size_t)blockIdx.x * KMAX + k] = red[k];
+    if (last_block_arrive(&ks->counter[CNT_DOT])) {
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+            const double hk = ks->sigma[k] * (double)sum_over_blocks(partial, gridDim.x, KMAX, k);
+            ks->h1[k] = hk;
+            ks->c1[k] = ks->sigma[k] * hk;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) ks->counter[CNT_DOT] = 0;
+    }
+}
+
+// K7a: w -= V_stored c1; h2 = sigma_k (V_stored^T w)_k.
+template <class Sys, int KMAX>
+__global__ void __launch_bounds__(kStreamBlock)
+arnoldi_pass2_kernel(const DevArgs* __restrict__ a, KState* ks, const typename Sys::T* V,
+                     size_t ldv, typename Sys::T* w, typename Sys::T* partial, int j) {
+    using T = typename Sys::T;
+    if (ks->cycle_over) return;
+    __shared__ T cf[KMAX];
+    __shared__ T scratch[(kStreamBlock / 32) * KMAX];
+    __shared__ T red[KMAX];
+    const int n = a->n, nk = j + 1;
+    for (int k = threadIdx.x; k < KMAX; k += blockDim.x) cf[k] = k < nk ? (T)ks->c1[k] : (T)0;
+    __syncthreads();
+    int lo, hi;
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    T part[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) part[k] = 0;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        T vv[KMAX];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) vv[k] = k < nk ? V[(size_t)k * ldv + i] : (T)0;
+        T r = w[i];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < nk) r -= vv[k] * cf[k];
+        w[i] = r;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < nk) part[k] += vv[k] * r;
+    }
+    block_sum<T, KMAX>(part, nk, red, scratch);
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) partial[(size_t)blockIdx.x * KMAX + k] = red[k];
+    if (last_block_arrive(&ks->counter[CNT_PASS2])) {
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+            const double hk = ks->sigma[k] * (double)sum_over_blocks(partial, gridDim.x, KMAX, k);
+            ks->h2[k] = hk;
+            ks->c2[k] = ks->sigma[k] * hk;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) ks->counter[CNT_PASS2] = 0;
+    }
+}
+
+// Thread 0 of the last block of K7b: Hessenberg column, Givens, stopping test.
+__device__ void arnoldi_finish(KState* ks, const DevArgs* a, int j, int R, double hn2) {
+    const double hn = sqrt(hn2);
+    const int nk = j + 1;
+    double* Hc = ks->H + (size_t)j * kMaxBasis;
+    double hh = 0.0;
+    for (int i = 0; i < nk; ++i) {
+        const double h = ks->h1[i] + ks->h2[i];
+        Hc[i] = h;
+        hh += h * h;
+    }
+    Hc[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = ks->cs[i] * Hc[i] + ks->sn[i] * Hc[i + 1];
+        Hc[i + 1] = -ks->sn[i] * Hc[i] + ks->cs[i] * Hc[i + 1];
+        Hc[i] = t;
+    }
+    const double av = Hc[j], bv = Hc[j + 1];
+    const double rr = hypot(av, bv);
+    double c = 1.0, s = 0.0;
+    if (rr != 0.0) {
+        c = av / rr;
+        s = bv / rr;
+    }
+    ks->cs[j] = c;
+    ks->sn[j] = s;
+    Hc[j] = rr;
+    Hc[j + 1] = 0.0;
+    ks->g[j + 1] = -s * ks->g[j];
+    ks->g[j] = c * ks->g[j];
+    ks->iters += 1;
+    ks->sigma[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+    const bool nonfinite = !isfinite(hn) || !isfinite(ks->g[j + 1]);
+    const bool happy = hn <= 1e-14 * sqrt(hh + hn * hn);
+    const bool conv = fabs(ks->g[j + 1]) <= ks->target;
+    if (nonfinite || happy || conv || ks->iters >= a->max_iters || j == R - 1) {
+        const int k = j + 1;
+        ks->cycle_over = 1;
+        ks->jdone = k;
+        for (int i = 0; i < kMaxBasis; ++i) ks->cy[i] = 0.0;
+        if (nonfinite) {
+            ks->status = ST_NONFINITE;
+            ks->finished = 1;
+            return;
+        }
+        for (int i = 0; i < k; ++i)
+            if (ks->H[(size_t)i * kMaxBasis + i] == 0.0) {
+                ks->status = ST_BREAKDOWN;
+                ks->finished = 1;
+                return;
+            }
+        double y[kMaxBasis];
+        for (int i = k - 1; i >= 0; --i) {
+            double acc = 0.0;
+            for (int l = i + 1; l < k; ++l) acc += ks->H[(size_t)l * kMaxBasis + i] * y[l];
+            y[i] = (ks->g[i] - acc) / ks->H[(size_t)i * kMaxBasis + i];
+        }
+        for (int i = 0; i < k; ++i) ks->cy[i] = ks->sigma[i] * y[i];
+    }
+}
+
+// K7b: w -= V_stored c2, stored as basis column j+1; ||w||^2; then K8.
+template <class Sys, int KMAX>
+__global__ void __launch_bounds__(kStreamBlock)
+arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* V, size_t ldv,
+                     const typename Sys::T* w, typename Sys::T* partial, int j, int R) {
+    using T = typename Sys::T;
+    if (ks->cycle_over) return;
+    __shared__ T cf[KMAX];
+    __shared__ T scratch[kStreamBlock / 32];
+    __shared__ T red[1];
+    const int n = a->n, nk = j + 1;
+    for (int k = threadIdx.x; k < KMAX; k += blockDim.x) cf[k] = k < nk ? (T)ks->c2[k] : (T)0;
+    __syncthreads();
+    T* vout = V + (size_t)(j + 1) * ldv;
+    int lo, hi;
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    T part[1] = {0};
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        T r = w[i];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < nk) r -= V[(size_t)k * ldv + i] * cf[k];
+        vout[i] = r;
+        part[0] += r * r;
+    }
+    block_sum<T, 1>(part, 1, red, scratch);
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+    if (last_block_arrive(&ks->counter[CNT_PASS3])) {
+        if (threadIdx.x == 0) {
+            const double hn2 = (double)sum_over_blocks(partial, gridDim.x, 1, 0);
+            arnoldi_finish(ks, a, j, R, hn2);
+            ks->counter[CNT_PASS3] = 0;
+        }
+    }
+}
+
+// x += V_stored cy (the GMRES correction of the finished cycle).
+template <class Sys>
+__global__ void __launch_bounds__(kStreamBlock)
+gmres_update_kernel(const DevArgs* __restrict__ a, const KState* ks, const typename Sys::T* V,
+                    size_t ldv) {
+    using T = typename Sys::T;
+    if (ks->status != ST_OK && ks->status != ST_NOT_CONVERGED) return;
+    if (ks->finished) return;
+    __shared__ double cy[kMaxBasis];
+    __shared__ int kk;
+    if (threadIdx.x == 0) kk = ks->jdone;
+    for (int k = threadIdx.x; k < kMaxBasis; k += blockDim.x) cy[k] = ks->cy[k];
+    __syncthreads();
+    const int k = kk, n = a->n;
+    T* x = Sys::x(a);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        T acc = 0;
+        for (int l = 0; l < k; ++l) acc += V[(size_t)l * ldv + i] * (T)cy[l];
+        x[i] += acc;
+    }
+}
+
+template <class Sys>
+static void launch_start(const DevArgs* a, KState* ks, typename Sys::T* V, typename Sys::T* partial,
+                         int nblk, int first, cudaStream_t st) {
+    gmres_start_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, partial, first);
+}
+
+template <class Sys, int KMAX>
+static void launch_step(const DevArgs* a, KState* ks, typename Sys::T* V, size_t ldv,
+                        typename Sys::T* w, typename Sys::T* partial, int nblk, int j, int R,
+                        cudaStream_t st) {
+    arnoldi_dot_kernel<Sys, KMAX><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j);
+    arnoldi_pass2_kernel<Sys, KMAX><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j);
+    arnoldi_pass3_kernel<Sys, KMAX><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j, R);
+}
+
+template <class Sys>
+static void launch_cycle(const DevArgs* a, KState* ks, typename Sys::T* V, size_t ldv,
+                         typename Sys::T* w, typename Sys::T* partial, int nblk, int R,
+                         cudaStream_t st, int* launches) {
+    for (int j = 0; j < R; ++j) {
+        const int nk = j + 1;
+        if (nk <= 8)
+            launch_step<Sys, 8>(a, ks, V, ldv, w, partial, nblk, j, R, st);
+        else if (nk <= 16)
+            launch_step<Sys, 16>(a, ks, V, ldv, w, partial, nblk, j, R, st);
+        else if (nk <= 32)
+            launch_step<Sys, 32>(a, ks, V, ldv, w, partial, nblk, j, R, st);
+        else
+            launch_step<Sys, 64>(a, ks, V, ldv, w, partial, nblk, j, R, st);
+    }
+    gmres_update_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv);
+    gmres_start_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, partial, 0);
+    if (launches) *launches = 3 * R + 2;
+}
+
+void launch_gmres_start_f64(const DevArgs* a, KState* ks, double* V, size_t, double* partial,
+                            int nblk, int first, cudaStream_t st) {
+    launch_start<SysF64>(a, ks, V, partial, nblk, first, st);
+}
+void launch_gmres_cycle_f64(const DevArgs* a, KState* ks, double* V, size_t ldv, double* w,
+                            double* partial, int nblk, int R, cudaStream_t st, int* launches) {
+    launch_cycle<SysF64>(a, ks, V, ldv, w, partial, nblk, R, st, launches);
+}
+void launch_gmres_start_f32(const DevArgs* a, KState* ks, float* V, size_t, float* partial,
+                            int nblk, int first, cudaStream_t st) {
+    launch_start<SysF32>(a, ks, V, partial, nblk, first, st);
+}
+void launch_gmres_cycle_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, float* w,
+                            float* partial, int nblk, int R, cudaStream_t st, int* launches) {
+    launch_cycle<SysF32>(a, ks, V, ldv, w, partial, nblk, R, st, launches);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision: r = b - A64 x in FP64, beta = ||r||, rhs32 = (float) r.
+__global__ void __launch_bounds__(kStreamBlock)
+refine_residual_kernel(const DevArgs* __restrict__ a, KState* ks, float* rhs32, double* partial) {
+    __shared__ double sprod[kStreamBlock];
+    __shared__ double scratch[(kStreamBlock / 32) * 2];
+    __shared__ double red[2];
+    const int n = a->n, nnz = a->nnz;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int lo, hi;
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    double acc[2] = {0.0, 0.0};
+    for (int r0 = lo + warp * 32; r0 < hi; r0 += nw * 32) {
+        const double ax = warp_tile_spmv<double>(a->rowptr, a->colind, a->val64, a->x, n, nnz, r0,
+                                                 sprod + warp * 32, &ks->bad_index);
+        const int row = r0 + lane;
+        if (row < n) {
+            const double bi = a->b[row];
+            const double r = bi - ax;
+            rhs32[row] = (float)r;
+            acc[0] += r * r;
+            acc[1] += bi * bi;
+        }
+    }
+    block_sum<double, 2>(acc, 2, red, scratch);
+    if (threadIdx.x < 2) partial[blockIdx.x * 2 + threadIdx.x] = red[threadIdx.x];
+    if (last_block_arrive(&ks->counter[CNT_REFINE])) {
+        if (threadIdx.x == 0) {
+            const double rr = sum_over_blocks(partial, gridDim.x, 2, 0);
+            const double bb = sum_over_blocks(partial, gridDim.x, 2, 1);
+            ks->beta = sqrt(rr);
+            ks->bnorm = sqrt(bb);
+            ks->target = a->tol * ks->bnorm;
+            ks->counter[CNT_REFINE] = 0;
+        }
+    }
+}
+
+void launch_refine_residual(const DevArgs* a, KState* ks, float* rhs32, double* partial, int nblk,
+                            cudaStream_t st) {
+    refine_residual_kernel<<<nblk, kStreamBlock, 0, st>>>(a, ks, rhs32, partial);
+}
+
+// x += d (FP64 += FP32 correction of the inner solve).
+__global__ void refine_update_kernel(const DevArgs* __restrict__ a) {
+    const int n = a->n;
+    const float* d = reinterpret_cast<const float*>(a->d);
+    double* x = a->x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] += (double)d[i];
+}
+
+void launch_refine_update(const DevArgs* a, const KState*, double, KState*, cudaStream_t st) {
+    refine_update_kernel<<<152 * 8, 256, 0, st>>>(a);
+}
+
+__global__ void round_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+void launch_round_f32(const double* src, float* dst, int n, cudaStream_t st) {
+    int b = (n + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    if (b < 1) b = 1;
+    round_f32_kernel<<<b, 256, 0, st>>>(src, dst, n);
+}
+
+// ---------------------------------------------------------------------------
+// CG in one thread block: the whole iteration runs on the device with block
+// barriers only (no launches, no host round trips).  Meant for small and
+// medium systems; the batched form runs one such solve per sequence.
+template <class Sys>
+__device__ __forceinline__ typename Sys::T csr_row(const DevArgs* a, const typename Sys::T* x,
+                                                   int i, int n, int nnz, int& bad) {
+    using T = typename Sys::T;
+    const T* val = Sys::val(a);
+    int rs = max(0, min(a->rowptr[i], nnz));
+    int re = max(rs, min(a->rowptr[i + 1], nnz));
+    T acc = 0;
+    for (int e = rs; e < re; ++e) {
+        const int c = a->colind[e];
+        if ((unsigned)c < (unsigned)n)
+            acc += val[e] * x[c];
+        else
+            bad = 1;
+    }
+    return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_total(T v, T* sred) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sred[warp] = v;
+    __syncthreads();
+    T t = 0;
+    for (int w = 0; w < nw; ++w) t += sred[w];
+    return t;
+}
+
+template <class Sys>
+__global__ void __launch_bounds__(1024)
+cg_block_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* r, typename Sys::T* p,
+                typename Sys::T* q) {
+    using T = typename Sys::T;
+    __shared__ T sred[32];
+    const int n = a->n, nnz = a->nnz, tid = threadIdx.x, bd = blockDim.x;
+    T* x = Sys::x(a);
+    const T* b = Sys::rhs(a);
+    int bad = 0;
+    const bool zero_x = sizeof(T) == 4;      // the FP32 inner solve starts from d = 0
+    if (zero_x)
+        for (int i = tid; i < n; i += bd) x[i] = 0;
+    __syncthreads();
+    T rr_l = 0, bb_l = 0;
+    for (int i = tid; i < n; i += bd) {
+        const T ri = b[i] - (zero_x ? (T)0 : csr_row<Sys>(a, x, i, n, nnz, bad));
+        r[i] = ri;
+        p[i] = ri;
+        rr_l += ri * ri;
+        bb_l += b[i] * b[i];
+    }
+    T rr = block_total(rr_l, sred);
+    const T bb = block_total(bb_l, sred);
+    const double bnorm = sqrt((double)bb);
+    const double target = a->tol * bnorm;
+    const double first = sqrt((double)rr) / bnorm;
+    int it = 0, status = ST_OK;
+    if (sqrt((double)rr) > target) {
+        for (;;) {
+            if (it >= a->max_iters) {
+                status = ST_NOT_CONVERGED;
+                break;
+            }
+            __syncthreads();
+            T pq_l = 0;
+            for (int i = tid; i < n; i += bd) {
+                const T qi = csr_row<Sys>(a, p, i, n, nnz, bad);
+                q[i] = qi;
+                pq_l += p[i] * qi;
+            }
+            const T pq = block_total(pq_l, sred);
+            if (!(pq > 0)) {
+                status = isfinite((double)pq) ? ST_BREAKDOWN : ST_NONFINITE;
+                break;
+            }
+            const T alpha = rr / pq;
+            T rn_l = 0;
+            for (int i = tid; i < n; i += bd) {
+                x[i] += alpha * p[i];
+                const T ri = r[i] - alpha * q[i];
+                r[i] = ri;
+                rn_l += ri * ri;
+            }
+            const T rr_new = block_total(rn_l, sred);
+            ++it;
+            if (!isfinite((double)rr_new)) {
+                status = ST_NONFINITE;
+                break;
+            }
+            if (sqrt((double)rr_new) <= target) {
+                __syncthreads();
+                T t_l = 0;
+                for (int i = tid; i < n; i += bd) {
+                    const T ri = b[i] - csr_row<Sys>(a, x, i, n, nnz, bad);
+                    r[i] = ri;
+                    t_l += ri * ri;
+                }
+                rr = block_total(t_l, sred);
+                if (sqrt((double)rr) <= target) break;
+                for (int i = tid; i < n; i += bd) p[i] = r[i];
+                continue;
+            }
+            const T beta = rr_new / rr;
+            rr = rr_new;
+            for (int i = tid; i < n; i += bd) p[i] = r[i] + beta * p[i];
+        }
+    }
+    if (bad) atomicOr(&ks->bad_index, 1);
+    __syncthreads();
+    // Final true residual (reported, and used by the refinement loop).
+    T f_l = 0;
+    for (int i = tid; i < n; i += bd) {
+        const T ri = b[i] - csr_row<Sys>(a, x, i, n, nnz, bad);
+        f_l += ri * ri;
+    }
+    const T ff = block_total(f_l, sred);
+    if (tid == 0) {
+        ks->iters = it;
+        ks->status = status;
+        ks->bnorm = bnorm;
+        ks->target = target;
+        ks->first_relres = first;
+        ks->beta = sqrt((double)ff);
+        ks->finished = 1;
+        ks->cycle_over = 1;
+    }
+}
+
+void launch_cg_block_f64(const DevArgs* a, KState* ks, double* r, double* p, double* q,
+                         cudaStream_t st) {
+    cg_block_kernel<SysF64><<<1, 1024, 0, st>>>(a, ks, r, p, q);
+}
+void launch_cg_block_f32(const DevArgs* a, KState* ks, float* r, float* p, float* q,
+                         cudaStream_t st) {
+    cg_block_kernel<SysF32><<<1, 1024, 0, st>>>(a, ks, r, p, q);
+}
+
+}  // namespace sa

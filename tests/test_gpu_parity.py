@@ -1,0 +1,289 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Tolerances, derived from the arithmetic (u = 2^-53):
+* sketch S: bit-exact (integer work).
+* W = S [A X | b]: entries are sums of ~n zeta / s signed FP64 terms, each
+  term the rounded row of A X; GPU and oracle sum in different orders, so
+  |dW| <= 1e-11 * (column scale) (about 100 u times sqrt(number of terms)).
+* y, x0 on a well-conditioned history: perturbation theory of least squares,
+  cond(W1) ~ 1e2 => 1e-10 relative.
+* On real solution histories W1 is ill-conditioned (Theorem 1); y is then not
+  unique to working precision, and parity is on the residuals (the sketched
+  residual and the true guess residual), which are stable.
+* Krylov: both sides stop on the same test; rounding differences move the
+  stopping iteration by a few steps, so counts agree within a small margin and
+  both final true residuals satisfy the tolerance.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import krylov, method, sketch
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_02156_gb300 as sa
+    sa.load()
+    yield
+
+
+def _sa():
+    import paper_2309_02156_gb300 as sa
+    return sa
+
+
+def _dev_system(rowptr, colind, vals, b):
+    sa = _sa()
+    A = sa.CSR(torch.from_numpy(rowptr).to(DEV), torch.from_numpy(colind).to(DEV),
+               torch.from_numpy(vals).to(DEV))
+    return A, torch.from_numpy(b).to(DEV)
+
+
+def _tensor(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(DEV)
+
+
+@pytest.mark.parametrize("n,s,zeta,seed", [(1, 40, 8, 3), (1000, 40, 8, 0x5EEDBA5E),
+                                           (4099, 80, 8, 7), (2500, 48, 8, 99),
+                                           (300, 8, 8, 5), (777, 128, 16, 2**63 + 5)])
+def test_sketch_columns_bitwise(n, s, zeta, seed):
+    rows, signs = _sa().sketch_columns(n, s, zeta, seed)
+    r_ref, s_ref = sketch.sparse_sign_columns(n, s, zeta, seed)
+    assert np.array_equal(rows.cpu().numpy(), r_ref)
+    assert np.array_equal(signs.cpu().numpy(), s_ref)
+
+
+def _run_guess(seq, p, i, hist_cols):
+    """Push hist_cols (oldest first) into a fresh sequence and guess system i."""
+    for c in hist_cols:
+        seq.push(_tensor(c))
+    rowptr, colind, vals, b = workloads.csr_system(p, i)
+    A, bd = _dev_system(rowptr, colind, vals, b)
+    x0 = torch.empty(p.n, dtype=torch.float64, device=DEV)
+    info = seq.guess(A, bd, x0)
+    return info, x0.cpu().numpy(), krylov.csr(rowptr, colind, vals, p.n), b
+
+
+@pytest.mark.parametrize("N,M,s,extra", [(40, 10, 40, 3), (37, 20, 80, 0), (23, 7, 48, 11),
+                                         (64, 1, 40, 0), (9, 5, 16, 2)])
+def test_guess_parity_well_conditioned(N, M, s, extra):
+    """Random history (ring wrapped `extra` times): W, y and x0 agree tightly."""
+    p = workloads.plain_nonsym(N)
+    rng = np.random.default_rng(N * 100 + M)
+    cols = [rng.standard_normal(p.n) for _ in range(M + extra)]
+    seq = _sa().Sequence(p.n, M, s, zeta=8, seed=123)
+    info, x0, A, b = _run_guess(seq, p, 5, cols)
+    X = np.stack(cols[-M:], axis=1)
+    S = sketch.sparse_sign_matrix(p.n, s, 8, 123)
+    ref = method.sketched_guess(A, b, X, S)
+    W, y = seq.last_sketch()
+    W = W[: s * (M + 1)].reshape(s, M + 1)
+    scale = np.linalg.norm(ref.W, axis=0)
+    assert np.all(np.abs(W - ref.W) <= 1e-11 * scale)
+    assert info["history_cols"] == M and info["rank"] == ref.rank
+    np.testing.assert_allclose(y[:M], ref.y, rtol=1e-10, atol=1e-10 * np.abs(ref.y).max())
+    assert np.linalg.norm(x0 - ref.x0) <= 1e-10 * np.linalg.norm(ref.x0)
+    assert info["sketch_resid"] == pytest.approx(ref.rho_s, rel=1e-10)
+    assert info["guess_relres"] == pytest.approx(method.relres(A, b, ref.x0), rel=1e-10)
+    seq.close()
+
+
+def _oracle_history(p, upto, M, tol, kind):
+    """Solutions x(t_0..t_{upto-1}) computed by the oracle from its own guesses."""
+    S = sketch.sparse_sign_matrix(p.n, 40, 8, 77)
+    h = method.History(p.n, M)
+    xs = []
+    for i in range(upto):
+        rowptr, colind, vals, b = workloads.csr_system(p, i)
+        A = krylov.csr(rowptr, colind, vals, p.n)
+        out = method.solve_step(A, b, h, S, tol, kind, max_iters=50000)
+        xs.append(out["x"])
+    return xs
+
+
+@pytest.mark.parametrize("kind,N,M,s", [("cg", 64, 10, 40), ("gmres", 48, 20, 80)])
+def test_guess_parity_on_solution_history(kind, N, M, s):
+    """Ill-conditioned (real) history: sketched and true guess residuals agree."""
+    p = workloads.plain_spd(N) if kind == "cg" else workloads.plain_nonsym(N)
+    tol = 1e-10 if kind == "cg" else 1e-8
+    xs = _oracle_history(p, M + 4, M, tol, kind)
+    seq = _sa().Sequence(p.n, M, s, zeta=8, seed=0x5EEDBA5E, krylov=kind)
+    i = M + 4
+    info, x0, A, b = _run_guess(seq, p, i, xs)
+    S = sketch.sparse_sign_matrix(p.n, s, 8, 0x5EEDBA5E)
+    ref = method.sketched_guess(A, b, np.stack(xs[-M:], axis=1), S)
+    W, _ = seq.last_sketch()
+    W = W[: s * (M + 1)].reshape(s, M + 1)
+    assert np.all(np.abs(W - ref.W) <= 1e-11 * np.linalg.norm(ref.W, axis=0))
+    r_gpu = method.relres(A, b, x0)
+    r_ref = method.relres(A, b, ref.x0)
+    assert r_gpu == pytest.approx(r_ref, rel=1e-3)
+    assert info["guess_relres"] == pytest.approx(r_gpu, rel=1e-6)
+    assert info["sketch_resid"] == pytest.approx(ref.rho_s, rel=1e-3)
+    seq.close()
+
+
+@pytest.mark.parametrize("N,guess_scale", [(32, 0.0), (45, 1.0), (20, 1.0)])
+def test_gmres_parity(N, guess_scale):
+    p = workloads.plain_nonsym(N)
+    rowptr, colind, vals, b = workloads.csr_system(p, 7)
+    A = krylov.csr(rowptr, colind, vals, p.n)
+    x0 = guess_scale * np.linalg.solve(A.toarray(), b) * (1 + 1e-3 * np.sin(np.arange(p.n)))
+    xr, it_ref, rel_ref, st_ref = krylov.gmres(A, b, x0, 1e-8, 30, 20000)
+    seq = _sa().Sequence(p.n, 4, 16, krylov="gmres", restart=30, max_iters=20000)
+    Ad, bd = _dev_system(rowptr, colind, vals, b)
+    x = _tensor(x0)
+    info = seq.solve(Ad, bd, 1e-8, x)
+    assert info["status"] == 0 and st_ref == 0
+    assert abs(info["iters"] - it_ref) <= max(2, 0.02 * it_ref)
+    assert method.relres(A, b, x.cpu().numpy()) <= 1e-8 * (1 + 1e-9)
+    assert info["final_relres"] == pytest.approx(method.relres(A, b, x.cpu().numpy()), rel=1e-6)
+    assert info["guess_relres"] == pytest.approx(method.relres(A, b, x0), rel=1e-9)
+    seq.close()
+
+
+@pytest.mark.parametrize("N", [64, 31, 5])
+def test_cg_parity(N):
+    p = workloads.plain_spd(N)
+    rowptr, colind, vals, b = workloads.csr_system(p, 3)
+    A = krylov.csr(rowptr, colind, vals, p.n)
+    xr, it_ref, rel_ref, st_ref = krylov.cg(A, b, np.zeros(p.n), 1e-10, 10000)
+    seq = _sa().Sequence(p.n, 4, 16, krylov="cg", max_iters=10000)
+    Ad, bd = _dev_system(rowptr, colind, vals, b)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    info = seq.solve(Ad, bd, 1e-10, x)
+    assert info["status"] == 0 and st_ref == 0
+    assert abs(info["iters"] - it_ref) <= 2
+    assert method.relres(A, b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-9)
+    seq.close()
+
+
+def test_sequence_spd_plain_workload():
+    """64x64 SPD sequence (n = 4096, M = 10, s = 40, CG to 1e-10), 60 systems run
+    end to end on the GPU (its own history) and in the oracle (its own history)."""
+    p = workloads.plain_spd(64)
+    M, s = 10, 40
+    S = sketch.sparse_sign_matrix(p.n, s, 8, 0x5EEDBA5E)
+    h = method.History(p.n, M)
+    seq = _sa().Sequence(p.n, M, s, seed=0x5EEDBA5E, krylov="cg", max_iters=20000)
+    it_gpu, it_ref = [], []
+    for i in range(60):
+        rowptr, colind, vals, b = workloads.csr_system(p, i)
+        A = krylov.csr(rowptr, colind, vals, p.n)
+        out = method.solve_step(A, b, h, S, 1e-10, "cg")
+        Ad, bd = _dev_system(rowptr, colind, vals, b)
+        x = torch.empty(p.n, dtype=torch.float64, device=DEV)
+        seq.guess(Ad, bd, x)
+        info = seq.solve(Ad, bd, 1e-10, x)
+        seq.push(x)
+        assert info["status"] == 0
+        assert method.relres(A, b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-9)
+        it_gpu.append(info["iters"])
+        it_ref.append(out["iters"])
+    it_gpu, it_ref = np.array(it_gpu), np.array(it_ref)
+    assert np.all(np.abs(it_gpu - it_ref) <= np.maximum(4, 0.1 * it_ref))
+    assert abs(it_gpu[10:].mean() - it_ref[10:].mean()) <= 0.03 * it_ref[10:].mean()
+    seq.close()
+
+
+def test_full_size_nonsymmetric_workload():
+    """1024x1024 advection-diffusion (n = 1,048,576, nnz = 5,238,784), M = 20,
+    s = 80, launched exactly as the benchmark launches it.  W is compared entry
+    by entry with the oracle; GMRES(30) reaches 1e-8, checked by the oracle's
+    own FP64 residual."""
+    p = workloads.plain_nonsym(1024)
+    M, s = 20, 80
+    i = 21
+    rng = np.random.default_rng(5)
+    hist = []
+    for k in range(M):       # smooth synthetic history: right-hand sides of earlier times
+        hist.append(workloads.rhs(p, workloads.time_grid(p, k)) * (1 + 0.01 * rng.standard_normal()))
+    seq = _sa().Sequence(p.n, M, s, seed=0x5EEDBA5E, krylov="gmres", restart=30, max_iters=30000)
+    info, x0, A, b = _run_guess(seq, p, i, hist)
+    S = sketch.sparse_sign_matrix(p.n, s, 8, 0x5EEDBA5E)
+    ref = method.sketched_guess(A, b, np.stack(hist, axis=1), S)
+    W, _ = seq.last_sketch()
+    W = W[: s * (M + 1)].reshape(s, M + 1)
+    assert np.all(np.abs(W - ref.W) <= 1e-11 * np.linalg.norm(ref.W, axis=0))
+    assert info["guess_relres"] == pytest.approx(method.relres(A, b, ref.x0), rel=1e-3)
+    rowptr, colind, vals, _ = workloads.csr_system(p, i)
+    Ad, bd = _dev_system(rowptr, colind, vals, b)
+    x = _tensor(x0)
+    sol = seq.solve(Ad, bd, 1e-8, x)
+    assert sol["status"] == 0
+    assert method.relres(A, b, x.cpu().numpy()) <= 1e-8 * (1 + 1e-9)
+    seq.close()
+
+
+def test_edge_cases():
+    sa = _sa()
+    p = workloads.plain_nonsym(7)        # n = 49: one ragged warp tile
+    rowptr, colind, vals, b = workloads.csr_system(p, 2)
+    A = krylov.csr(rowptr, colind, vals, p.n)
+    Ad, bd = _dev_system(rowptr, colind, vals, b)
+    seq = sa.Sequence(p.n, 3, 8, zeta=4, seed=1, krylov="gmres", restart=5, max_iters=1000)
+    x = torch.full((p.n,), 7.0, dtype=torch.float64, device=DEV)
+    info = seq.guess(Ad, bd, x)          # empty history: x0 = 0
+    assert info["history_cols"] == 0 and torch.all(x == 0)
+    assert info["guess_relres"] == pytest.approx(1.0)
+    info = seq.solve(Ad, bd, 1e3, x)     # already below the tolerance: 0 iterations
+    assert info["iters"] == 0 and info["status"] == 0
+    info = seq.solve(Ad, bd, 1e-14, x, allow=(1,))   # cap reached
+    assert info["rc"] == 1
+    seq2 = sa.Sequence(p.n, 3, 8, zeta=4, seed=1, krylov="gmres", restart=5, max_iters=7)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    info = seq2.solve(Ad, bd, 1e-14, x, allow=(1,))
+    assert info["rc"] == 1 and info["iters"] == 7
+    # One pushed column: the guess uses it (m < M start-up).
+    xs = np.linalg.solve(A.toarray(), b)
+    seq.push(_tensor(xs))
+    info = seq.guess(Ad, bd, x)
+    assert info["history_cols"] == 1
+    assert method.relres(A, b, x.cpu().numpy()) < 1e-12
+    # Previous-solution guess returns the newest pushed column.
+    seq3 = sa.Sequence(p.n, 3, 8, zeta=4, guess="prev")
+    for k in range(5):
+        seq3.push(_tensor(np.full(p.n, float(k))))
+    seq3.guess(Ad, bd, x)
+    assert torch.all(x == 4.0)
+    # A column index outside [0, n) is reported, not dereferenced.
+    bad = colind.copy()
+    bad[10] = p.n + 5
+    Ab, _ = _dev_system(rowptr, bad, vals, b)
+    with pytest.raises(sa.SeqError) as e:
+        seq.guess(Ab, bd, x)
+    assert e.value.code == -1
+    with pytest.raises(sa.SeqError):
+        seq.solve(Ab, bd, 1e-8, x)
+    # 1 x 1 system.
+    q = workloads.plain_spd(1)
+    r1, c1, v1, b1 = workloads.csr_system(q, 0)
+    A1, b1d = _dev_system(r1, c1, v1, b1)
+    s1 = sa.Sequence(1, 1, 2, zeta=1, krylov="cg")
+    x1 = torch.zeros(1, dtype=torch.float64, device=DEV)
+    info = s1.solve(A1, b1d, 1e-12, x1)
+    assert info["status"] == 0 and abs(x1.item() - b1[0] / v1[0]) <= 1e-15 * abs(b1[0] / v1[0])
+    for sq in (seq, seq2, seq3, s1):
+        sq.close()
+
+
+def test_repeatable_bit_for_bit():
+    p = workloads.plain_nonsym(40)
+    rowptr, colind, vals, b = workloads.csr_system(p, 3)
+    Ad, bd = _dev_system(rowptr, colind, vals, b)
+    outs = []
+    for _ in range(2):
+        seq = _sa().Sequence(p.n, 4, 16, krylov="gmres", max_iters=3000)
+        x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+        seq.solve(Ad, bd, 1e-9, x)
+        outs.append(x.cpu().numpy().copy())
+        seq.close()
+    assert np.array_equal(outs[0], outs[1])

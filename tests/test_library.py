@@ -1,0 +1,51 @@
+"""The C-ABI library builds, loads and exports every declared entry point (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(seq_\w+)\s*\(", text, flags=re.M)
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = set(_declared())
+    for required in ("seq_create", "seq_destroy", "seq_push_solution", "seq_guess", "seq_solve"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    if not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2309_02156_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_create_rejects_bad_config_without_gpu_work():
+    """Argument validation happens on the host before any device call."""
+    if not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    import paper_2309_02156_gb300._binding as b
+    lib = b.load()
+    h = ctypes.c_void_p()
+    bad = [b._Config(0, 10, 40, 8, 1, 0, 2, 1, 30, 100, 0, 0),     # n = 0
+           b._Config(100, 10, 10, 8, 1, 0, 2, 1, 30, 100, 0, 0),   # s < M + 1
+           b._Config(100, 40, 80, 8, 1, 0, 2, 1, 30, 100, 0, 0),   # M > 31
+           b._Config(100, 10, 40, 8, 1, 0, 2, 1, 99, 100, 0, 0),   # restart > 64
+           b._Config(100, 10, 40, 41, 1, 0, 2, 1, 30, 100, 0, 0)]  # zeta > s
+    for cfg in bad:
+        assert lib.seq_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
+        assert not h.value
