@@ -1,0 +1,443 @@
+#!/usr/bin/env python3
+"""Systems per second to a relative residual of 1e-8 on the 1024 x 1024
+advection-diffusion sequence (sketched subspace guess + GMRES(30)).
+
+Workload (one system = one step): A(t_i) u = -div(k grad u) + v(t).grad u + u
+on a 1024 x 1024 interior grid (n = 1,048,576, nnz = 5,238,784, first-order
+upwind, v = 20 (cos t, sin t)), b(t) a circling Gaussian source, t_i = 0.005 i;
+history M = 20, sparse-sign sketch s = 80 rows with 8 nonzeros per column,
+GMRES(30) with CGS2 to ||b - A x|| <= 1e-8 ||b||, FP64.  A step is seq_guess +
+seq_solve + seq_push_solution on device-resident A(t_i), b(t_i).
+
+The history is primed with the first M systems (untimed), then W warm-up steps
+and K timed steps follow.  Each step reads a different A(t_i) and the history
+(168 MB) and Krylov basis (260 MB) exceed the 129 MB L2, so no flush is needed.
+
+Prints one JSON line (rank 0).  With torchrun every rank runs an independent
+replica of the sequence ("replicas only": a single sequence is not sharded).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_GRID, M_HIST, S_ROWS, ZETA, SEED, TOL, RESTART = 1024, 20, 80, 8, 0x5EEDBA5E, 1e-8, 30
+METRIC = "systems/sec to rel-res 1e-8 (guess+Krylov)"
+WORKLOAD = ("nonsym advection-diffusion 1024x1024 (n=1048576, nnz=5238784), M=20, s=80 "
+            "sparse-sign (zeta=8), GMRES(30)-CGS2 to rel-res 1e-8, FP64")
+
+
+def _gen(i):
+    import workloads
+    p = workloads.plain_nonsym(N_GRID)
+    t = workloads.time_grid(p, i)
+    return i, workloads.assemble(p, t), workloads.rhs(p, t)
+
+
+def generate(steps, workers=8):
+    """values and b of systems `steps` (host numpy), generated in a spawn pool."""
+    ctx = mp.get_context("spawn")
+    out = {}
+    with ctx.Pool(min(workers, len(steps))) as pool:
+        for i, v, b in pool.imap_unordered(_gen, steps):
+            out[i] = (v, b)
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic(kind):
+    """Per-launch DRAM traffic of `kind` from the committed ncu summary, if it was
+    taken on the current kernel source (null otherwise)."""
+    path = os.path.join(ROOT, "profiles", "arnoldi_kernels_nonsym1024.txt")
+    src = os.path.join(ROOT, "paper_2309_02156_gb300", "csrc", "krylov.cu")
+    if not os.path.exists(path):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if line.startswith("source_sha256_16:"):
+            vals["sha"] = line.split(":", 1)[1].strip()
+        if line.startswith(f"traffic_bytes_per_launch[{kind}]:"):
+            vals["traffic"] = float(line.split(":", 1)[1].split()[0])
+    if vals.get("sha") != digest:
+        return None
+    return vals.get("traffic")
+
+
+def cpu_baseline_worker(iters_per_system: float, gmres_iters: int) -> None:
+    """Time the oracle on a bounded sample (single thread) and print one JSON line."""
+    import numpy as np
+    import workloads
+    from oracle import krylov, method, sketch
+    p = workloads.plain_nonsym(N_GRID)
+    i = M_HIST + 3
+    rowptr, colind, vals, b = workloads.csr_system(p, i)
+    A = krylov.csr(rowptr, colind, vals, p.n)
+    X = np.stack([workloads.rhs(p, workloads.time_grid(p, k)) for k in range(i - M_HIST, i)], 1)
+    S = sketch.sparse_sign_matrix(p.n, S_ROWS, ZETA, SEED)
+    t0 = time.perf_counter()
+    g = method.sketched_guess(A, b, X, S)
+    t_guess = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, it, _, _ = krylov.gmres(A, b, g.x0, 1e-30, RESTART, gmres_iters)
+    t_iter = (time.perf_counter() - t0) / max(it, 1)
+    per_system = t_guess + iters_per_system * t_iter
+    print(json.dumps({"t_guess": t_guess, "t_iter": t_iter, "iters_sampled": it,
+                      "per_system_s": per_system, "value": 1.0 / per_system}))
+
+
+def run_cpu_baseline(iters_per_system: float, gmres_iters: int = 120):
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker",
+           "--iters-per-system", repr(iters_per_system), "--gmres-iters", str(gmres_iters)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": "systems/s", "cores": 1, "kind": "oracle",
+                "error": r.stderr[-400:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": "systems/s", "cores": 1, "kind": "oracle",
+            "sample": (f"one 1024x1024 system: oracle sketched guess ({d['t_guess']:.2f} s) + "
+                       f"{d['iters_sampled']} GMRES(30) iterations ({d['t_iter'] * 1e3:.1f} ms each) "
+                       f"on 1 host thread, per-system time = guess + {iters_per_system:.1f} "
+                       f"iterations (mean of the GPU run)")}
+
+
+def oracle_iterations_per_system():
+    path = os.path.join(ROOT, "tests", "golden", "oracle_iterations_nonsym1024.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        if d.get("mean_iters_full_history"):
+            return float(d["mean_iters_full_history"]), "oracle run recorded by oracle/measure_iterations.py"
+    return None, "no recorded oracle run"
+
+
+def reference_arm(args):
+    """The oracle timed on the host cores, same metric and workload, bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    ips, src = oracle_iterations_per_system()
+    import numpy as np
+    import workloads
+    from oracle import krylov, method, sketch
+    p = workloads.plain_nonsym(N_GRID)
+    S = sketch.sparse_sign_matrix(p.n, S_ROWS, ZETA, SEED)
+    gmres_iters = 30
+    times = []
+    for step in range(args.warmup + args.steps):
+        i = M_HIST + step
+        rowptr, colind, vals, b = workloads.csr_system(p, i)
+        A = krylov.csr(rowptr, colind, vals, p.n)
+        X = np.stack([workloads.rhs(p, workloads.time_grid(p, k)) for k in range(i - M_HIST, i)], 1)
+        t0 = time.perf_counter()
+        g = method.sketched_guess(A, b, X, S)
+        t1 = time.perf_counter()
+        _, it, _, _ = krylov.gmres(A, b, g.x0, 1e-30, RESTART, gmres_iters)
+        t2 = time.perf_counter()
+        if step >= args.warmup:
+            times.append((t1 - t0, (t2 - t1) / max(it, 1)))
+    tg = statistics.mean(t[0] for t in times)
+    ti = statistics.mean(t[1] for t in times)
+    iters = ips if ips else 0.0
+    per = tg + iters * ti
+    value = 1.0 / per
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", "0")) or os.cpu_count()
+    sample = (f"per step: oracle sketched guess + {gmres_iters} GMRES(30) iterations on a "
+              f"1024x1024 system; per-system time = guess + {iters:.1f} iterations ({src})")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "systems/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": "systems/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def profile_run(iters: int) -> None:
+    """A bounded full-size command for ncu: one sketched guess from a synthetic
+    20-column history and `iters` GMRES(30) iterations on system 23 of the
+    1024 x 1024 sequence (about 12 launches per 4 Arnoldi steps), so that a
+    profiler can capture every launch of the run."""
+    import numpy as np
+    import torch
+    import paper_2309_02156_gb300 as sa
+    import workloads
+    p = workloads.plain_nonsym(N_GRID)
+    rowptr, colind, vals, b = workloads.csr_system(p, M_HIST + 3)
+    dev = torch.device("cuda", 0)
+    A = sa.CSR(torch.from_numpy(rowptr).to(dev), torch.from_numpy(colind).to(dev),
+               torch.from_numpy(vals).to(dev))
+    bd = torch.from_numpy(b).to(dev)
+    seq = sa.Sequence(p.n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, krylov="gmres",
+                      restart=RESTART, max_iters=iters)
+    rng = np.random.default_rng(1)
+    for _ in range(M_HIST):
+        seq.push(torch.from_numpy(rng.standard_normal(p.n)).to(dev))
+    x = torch.empty(p.n, dtype=torch.float64, device=dev)
+    g = seq.guess(A, bd, x)
+    info = seq.solve(A, bd, TOL, x, allow=(0, 1))
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": True, "guess_launches": g["launches"],
+                      "solve_launches": info["launches"], "iters": info["iters"]}))
+    seq.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-worker", action="store_true")
+    ap.add_argument("--iters-per-system", type=float, default=0.0)
+    ap.add_argument("--gmres-iters", type=int, default=120)
+    ap.add_argument("--profile-run", type=int, default=0, metavar="ITERS")
+    args = ap.parse_args()
+    if args.profile_run:
+        profile_run(args.profile_run)
+        return
+    if args.cpu_baseline_worker:
+        cpu_baseline_worker(args.iters_per_system, args.gmres_iters)
+        return
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    K, W = args.steps, args.warmup
+    steps_dev = list(range(M_HIST + W + K))
+    steps_e2e = list(range(M_HIST + W + K, M_HIST + W + 2 * K))
+    host = generate(steps_dev + steps_e2e)     # before any CUDA call (spawn pool)
+
+    import numpy as np
+    import torch
+    import paper_2309_02156_gb300 as sa
+    import workloads
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    p = workloads.plain_nonsym(N_GRID)
+    n = p.n
+    rowptr, colind, _ = workloads.pattern(N_GRID)
+    rp = torch.from_numpy(rowptr).to(dev)
+    ci = torch.from_numpy(colind).to(dev)
+    vals = {i: torch.from_numpy(host[i][0]).to(dev) for i in steps_dev}
+    bs = {i: torch.from_numpy(host[i][1]).to(dev) for i in steps_dev}
+    seq = sa.Sequence(n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, krylov="gmres", restart=RESTART,
+                      max_iters=60000)
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def step(i):
+        A = sa.CSR(rp, ci, vals[i])
+        g = seq.guess(A, bs[i], x)
+        info = seq.solve(A, bs[i], TOL, x)
+        seq.push(x)
+        return g, info
+
+    prime = [step(i) for i in range(M_HIST)]
+    for i in range(M_HIST, M_HIST + W):
+        step(i)
+    fp64_peak = sa.probe_fp64_peak()
+    hbm_peak, hbm_src = peaks()
+    gpu_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis and vis.split(",")[local].strip().isdigit():
+        gpu_index = int(vis.split(",")[local])
+    sampler = ClockSampler(gpu_index)
+    seq.set_profiling(True)
+    seq.kernel_stats(reset=True)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0.record(stream)
+    infos = []
+    for i in range(M_HIST + W, M_HIST + W + K):
+        infos.append(step(i))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    stats = seq.kernel_stats(reset=True)
+    seq.set_profiling(False)
+    value = world * K / (ms / 1e3)
+    iters = [inf["iters"] for _, inf in infos]
+    launches = sum(g["launches"] + inf["launches"] + 1 for g, inf in infos)
+    worst = max(inf["final_relres"] for _, inf in infos)
+    assert all(inf["status"] == 0 for _, inf in infos), "a timed solve did not converge"
+
+    # Dominant kernel and its roofline.
+    dom = max(stats, key=lambda k: stats[k]["ms"])
+    st = stats[dom]
+    t_launch = st["ms"] / 1e3 / max(st["launches"], 1)
+    bytes_l = st["bytes"] / max(st["launches"], 1)
+    flops_l = st["flops"] / max(st["launches"], 1)
+    t_hbm = bytes_l / (hbm_peak * 1e9)
+    t_alu = flops_l / (fp64_peak * 1e12)
+    if t_alu > t_hbm:
+        roof = {"bound": "alu", "achieved": flops_l / t_launch / 1e12, "peak": fp64_peak,
+                "unit": "TFLOP/s", "peak_source": "FP64 FMA probe measured in this run"}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_l / t_launch / 1e9, "peak": hbm_peak,
+                "unit": "GB/s", "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = profile_traffic(dom)
+    roof["kernel"] = dom
+    roof["algorithmic_bytes_per_launch"] = bytes_l
+    roof["algorithmic_flops_per_launch"] = flops_l
+    roof["launch_us"] = t_launch * 1e6
+    total_ms = sum(v["ms"] for v in stats.values())
+    kernels = {k: {"launches": v["launches"], "share": v["ms"] / total_ms if total_ms else None,
+                   "GB/s": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] else None,
+                   "TFLOP/s": v["flops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] else None}
+               for k, v in stats.items()}
+
+    # End to end: host inputs copied in each step, solution copied out.
+    pin = {i: (torch.from_numpy(host[i][0]).pin_memory(), torch.from_numpy(host[i][1]).pin_memory())
+           for i in steps_e2e}
+    rp_h = torch.from_numpy(rowptr).pin_memory()
+    ci_h = torch.from_numpy(colind).pin_memory()
+    v_d = torch.empty_like(vals[steps_dev[0]])
+    b_d = torch.empty_like(bs[steps_dev[0]])
+    rp_d = torch.empty_like(rp)
+    ci_d = torch.empty_like(ci)
+    x_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    h2d = rp_h.numel() * 4 + ci_h.numel() * 4 + v_d.numel() * 8 + b_d.numel() * 8
+    d2h = n * 8
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for i in steps_e2e:
+        rp_d.copy_(rp_h, non_blocking=True)
+        ci_d.copy_(ci_h, non_blocking=True)
+        v_d.copy_(pin[i][0], non_blocking=True)
+        b_d.copy_(pin[i][1], non_blocking=True)
+        A = sa.CSR(rp_d, ci_d, v_d)
+        seq.guess(A, b_d, x)
+        seq.solve(A, b_d, TOL, x)
+        seq.push(x)
+        x_h.copy_(x, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3)
+    if dist:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = t.item()
+    e2e_value = world * K / (ms_e2e / 1e3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(float(np.mean(iters)))
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "plain FP64", "history_primed": M_HIST,
+                       "l2": "inputs larger than L2 (history 168 MB, basis 260 MB, new A(t_i) per step)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "iters_per_system": float(np.mean(iters)),
+            "iters_per_system_prev_steps": [inf["iters"] for _, inf in prime[-3:]],
+            "guess_relres_mean": float(np.mean([g["guess_relres"] for g, _ in infos])),
+            "final_relres_max": worst,
+            "roofline": roof, "kernels": kernels, "clocks": clocks,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "systems/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    seq.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -120,8 +120,8 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out);
 int seq_destroy(seq_ctx* ctx);
 
 /* Append x(t_i) to the history and drop the oldest column once M are held
- * (Section 2.1, the history update "removing its first column and appending a
- * new last column").  x_dev: device, n FP64 values (rounded to FP32 in
+ * (Section 2.1: each time step the oldest solution leaves X and the newest
+ * one is appended).  x_dev: device, n FP64 values (rounded to FP32 in
  * SEQ_MIXED).  Stream-ordered; does not synchronise. */
 int seq_push_solution(seq_ctx* ctx, const double* x_dev);
 
@@ -161,6 +161,35 @@ int seq_last_sketch(seq_ctx* ctx, double* W_host, double* y_host);
  * duplicates skipped).  Device pointers; stream-ordered; synchronises. */
 int seq_sketch_columns(int32_t n, int32_t s, int32_t zeta, uint64_t seed,
                        int32_t* rows_dev, int8_t* signs_dev, void* cuda_stream);
+
+/* Kernel kinds reported by seq_kernel_stats (the GMRES cycle of Algorithm 1,
+ * step 4, and the stages of the guess). */
+typedef enum {
+    SEQ_K_SPMV_DOT = 0,   /* w = A v_j fused with the first CGS pass h1 = V^T w          */
+    SEQ_K_CGS_PASS2 = 1,  /* w -= V h1 fused with the second pass h2 = V^T w             */
+    SEQ_K_CGS_PASS3 = 2,  /* w -= V h2, ||w||, Givens update (basis column j+1)          */
+    SEQ_K_UPDATE = 3,     /* x += V y at the end of a restart cycle                      */
+    SEQ_K_RESTART = 4,    /* r = b - A x, ||r|| at a cycle start                         */
+    SEQ_K_COUNT = 5
+} seq_kernel_kind;
+
+typedef struct {
+    int64_t launches;     /* launches that did work                               */
+    double ms;            /* summed device time between the launch's boundary events */
+    double bytes;         /* summed algorithmic DRAM bytes (each operand once)    */
+    double flops;         /* summed algorithmic floating-point operations         */
+} seq_kernel_stat;
+
+/* Turn per-kernel timing of seq_solve on (on != 0) or off.  When on, the GMRES
+ * cycle graph records a CUDA event between consecutive kernels (on the
+ * context's stream), and seq_kernel_stats accumulates, per kernel kind, the
+ * device time and the algorithmic traffic of every launch that did work.  The
+ * events add a small overhead to each cycle.  GMRES only. */
+int seq_set_profiling(seq_ctx* ctx, int on);
+
+/* Copy the accumulated per-kind statistics into out[SEQ_K_COUNT]; reset != 0
+ * clears them afterwards. */
+int seq_kernel_stats(seq_ctx* ctx, seq_kernel_stat* out, int reset);
 
 /* Measure this device's FP64 fused multiply-add throughput (TFLOP/s, counting
  * 2 flops per FMA) with a register-only kernel of about 50 ms.  Used as the

@@ -2,9 +2,9 @@
 
 The paper runs GMRES (Saad and Schultz) for general matrices and names CG
 (Hestenes and Stiefel) for symmetric positive definite ones (Section 1); both
-stop on the residual relative to ||b||, the reading under which the paper's
-"initial residual already below the tolerance, hence 0 iterations" (Sections
-4 and 5) is possible.  Conventions shared with the GPU side:
+stop on the residual relative to ||b||.  That reading is the one under which
+the paper's observation that many systems need no iteration at all (the guess
+already meets the tolerance, Sections 4 and 5) can happen.  Conventions shared with the GPU side:
 
 * an iteration is one product with A inside the loop (one Arnoldi step for
   GMRES, one search direction for CG);
@@ -97,7 +97,7 @@ def gmres(A, b, x, tol: float, restart: int, max_iters: int, record=None):
             return x, it, beta / bnorm, CONVERGED
         if it >= max_iters:
             return x, it, beta / bnorm, NOT_CONVERGED
-        V = np.zeros((n, restart + 1), dtype=dt)
+        V = np.zeros((n, restart + 1), dtype=dt, order="F")     # columns contiguous
         H = np.zeros((restart + 1, restart))          # Hessenberg, FP64 always
         Hbar = np.zeros((restart + 1, restart))
         cs = np.zeros(restart)

@@ -1,7 +1,7 @@
 """Small dense least squares min_y || W1 y - wb ||_2 (Algorithm 1, step 3).
 
-The paper solves the reduced problem "through the QR decomposition" (Section
-2, the cost paragraph after Algorithm 1, citing Golub and Van Loan).  The
+The paper solves the reduced problem with a QR factorisation (Section 2, the
+cost paragraph after Algorithm 1, citing Golub and Van Loan).  The
 history columns are nearly dependent by design (Theorem 1: their singular
 values decay geometrically), so the factorisation is made rank revealing.
 Readings, identical on the GPU side:

@@ -1,0 +1,63 @@
+"""Record the oracle's own Krylov iteration counts on a full-size sequence.
+
+Runs Algorithm 1 with the sketched reduced problem followed by GMRES(30) to a
+relative residual of 1e-8 on the 1024 x 1024 advection-diffusion sequence
+(M = 20, s = 80, zeta = 8, seed 0x5EEDBA5E), entirely in the oracle, and
+writes the per-system iteration counts and timings as JSON.  The CPU
+baseline of the benchmark uses the mean count of the systems with a full
+history to turn a timed sample (one guess plus a bounded number of GMRES
+iterations) into systems per second.
+
+    python -m oracle.measure_iterations --steps 26 --out tests/golden/oracle_iterations_nonsym1024.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import platform
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+from oracle import krylov, method, sketch  # noqa: E402
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--N", type=int, default=1024)
+    ap.add_argument("--M", type=int, default=20)
+    ap.add_argument("--s", type=int, default=80)
+    ap.add_argument("--steps", type=int, default=26)
+    ap.add_argument("--out", required=True)
+    a = ap.parse_args()
+    p = workloads.plain_nonsym(a.N)
+    S = sketch.sparse_sign_matrix(p.n, a.s, 8, 0x5EEDBA5E)
+    hist = method.History(p.n, a.M)
+    rows = []
+    for i in range(a.steps):
+        rowptr, colind, vals, b = workloads.csr_system(p, i)
+        A = krylov.csr(rowptr, colind, vals, p.n)
+        t0 = time.perf_counter()
+        out = method.solve_step(A, b, hist, S, 1e-8, "gmres", restart=30, max_iters=60000)
+        dt = time.perf_counter() - t0
+        rows.append({"i": i, "iters": int(out["iters"]), "guess_relres": out["guess_relres"],
+                     "relres": out["relres"], "status": int(out["status"]), "seconds": dt})
+        print(json.dumps(rows[-1]), flush=True)
+        full = [r["iters"] for r in rows if r["i"] >= a.M]
+        doc = {"workload": f"nonsym {a.N}x{a.N}, v=20(cos t, sin t), dt=0.005, M={a.M}, "
+                           f"s={a.s}, zeta=8, GMRES(30) to 1e-8",
+               "host": platform.machine(), "systems": rows,
+               "mean_iters_full_history": float(np.mean(full)) if full else None}
+        with open(a.out, "w") as f:
+            json.dump(doc, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

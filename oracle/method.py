@@ -3,8 +3,8 @@
 Algorithm 1 (Section 2) builds the guess for system i from the history
 X = [x(t_{i-M}) | ... | x(t_{i-1})] (oldest first) as the element of a
 subspace of span(X) that minimises ||A(t_i) s - b(t_i)||_2, then runs the
-Krylov solver from it.  With the whole span (Section 2, "If the complete
-history is used") the minimiser is X y* with y* = argmin ||A X y - b||.  The
+Krylov solver from it.  With the whole span (Section 2, cost paragraph after
+Algorithm 1) the minimiser is X y* with y* = argmin ||A X y - b||.  The
 hot path replaces that n-row problem by its sketch:
 
     W  = S [A X | b]                    (s x (m+1), S sparse-sign, see sketch.py)
@@ -13,8 +13,8 @@ hot path replaces that n-row problem by its sketch:
 
 Start-up (a reading; Algorithm 1 assumes M solutions exist): system 0 starts
 from x0 = 0 and system i < M uses the i columns it has.  The history is
-shifted by one column per system (Section 2.1: "removing its first column
-and appending a new last column").
+shifted by one column per system: the oldest column leaves and the newest
+solution is appended (Section 2.1).
 
 Parity: pinned (S = I equals the dense unsketched projection; exactness when
 b lies in A span(X); residual decay in M for analytic data, Theorem 2; dense

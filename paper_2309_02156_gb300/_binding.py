@@ -51,6 +51,13 @@ class SeqInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+KERNEL_KINDS = ["spmv_dot", "cgs_pass2", "cgs_pass3", "update", "restart"]
+
 _LIB = None
 
 _SIGS = {
@@ -69,6 +76,8 @@ _SIGS = {
                                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p]),
     "seq_probe_fp64_peak": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "seq_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "seq_kernel_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
 }
 
 
@@ -187,6 +196,16 @@ class Sequence:
         d = info.as_dict()
         d["rc"] = rc
         return d
+
+    def set_profiling(self, on: bool) -> None:
+        self._check(self._lib.seq_set_profiling(self._h, int(bool(on))))
+
+    def kernel_stats(self, reset: bool = False) -> dict:
+        """Per kernel kind: launches, device ms, algorithmic bytes and flops."""
+        arr = (KernelStat * len(KERNEL_KINDS))()
+        self._check(self._lib.seq_kernel_stats(self._h, ctypes.byref(arr), int(reset)))
+        return {k: {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes,
+                    "flops": arr[i].flops} for i, k in enumerate(KERNEL_KINDS)}
 
     def last_sketch(self):
         """(W, y) of the last guess as float64 CPU tensors, oldest history column first."""

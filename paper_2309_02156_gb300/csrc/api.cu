@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/seqaccel.h"
 #include "common.cuh"
@@ -51,6 +52,10 @@ struct seq_ctx {
     KState* ks_in = nullptr;         // inner solve state
     KState* h_ks = nullptr;          // pinned mirror of the state tail
     cudaGraphExec_t cycle = nullptr;
+    cudaGraphExec_t cycle_prof = nullptr;   // same cycle with timing events between kernels
+    std::vector<cudaEvent_t> ev;
+    bool profiling = false;
+    seq_kernel_stat stats[SEQ_K_COUNT];
     int cycle_launches = 0;
     int launches = 0;
     std::string err;
@@ -133,26 +138,66 @@ int ensure_val32(seq_ctx* ctx, const seq_csr* A) {
     return SEQ_OK;
 }
 
-int capture_cycle(seq_ctx* ctx) {
-    if (ctx->cycle) return SEQ_OK;
+// Capture one restart cycle as a CUDA graph (once per context); the profiled
+// variant carries an event record node between consecutive kernels.
+int capture_cycle(seq_ctx* ctx, bool prof) {
+    cudaGraphExec_t* exec = prof ? &ctx->cycle_prof : &ctx->cycle;
+    if (*exec) return SEQ_OK;
+    const int R = ctx->cfg.restart;
+    cudaEvent_t* ev = nullptr;
+    if (prof) {
+        if (ctx->ev.empty()) {
+            ctx->ev.resize(3 * R + 3);
+            for (auto& e : ctx->ev) CK(cudaEventCreate(&e));
+        }
+        ev = ctx->ev.data();
+    }
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
-    const int R = ctx->cfg.restart;
     if (!ctx->mixed)
         launch_gmres_cycle_f64(ctx->d_args, ctx->ks, (double*)ctx->V, ctx->ldv, (double*)ctx->w,
-                               ctx->kpartial, ctx->nblk, R, ctx->cap, &ctx->cycle_launches);
+                               ctx->kpartial, ctx->nblk, R, ctx->cap, &ctx->cycle_launches, ev);
     else
         launch_gmres_cycle_f32(ctx->d_args_in, ctx->ks_in, (float*)ctx->V, ctx->ldv,
                                (float*)ctx->w, (float*)ctx->kpartial, ctx->nblk, R, ctx->cap,
-                               &ctx->cycle_launches);
+                               &ctx->cycle_launches, ev);
     CK(cudaStreamEndCapture(ctx->cap, &g));
-    cudaError_t e = cudaGraphInstantiate(&ctx->cycle, g, 0);
+    cudaError_t e = cudaGraphInstantiate(exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        ctx->cycle = nullptr;
+        *exec = nullptr;
         return fail(ctx, SEQ_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
     }
     return SEQ_OK;
+}
+
+void add_stat(seq_ctx* ctx, int kind, int ev0, double bytes, double flops) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[ev0], ctx->ev[ev0 + 1]) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    seq_kernel_stat& st = ctx->stats[kind];
+    st.launches += 1;
+    st.ms += ms;
+    st.bytes += bytes;
+    st.flops += flops;
+}
+
+// Per-kind time and algorithmic traffic of the cycle that just ran (each
+// operand counted once: CSR arrays, gathered vector, basis columns, outputs).
+void account_cycle(seq_ctx* ctx, bool f32, int jd, bool updated, int nnz) {
+    const double n = ctx->cfg.n, E = f32 ? 4.0 : 8.0, R = ctx->cfg.restart;
+    const double csr = 4.0 * (n + 1) + (4.0 + E) * nnz;
+    for (int j = 0; j < jd; ++j) {
+        const double nk = j + 1;
+        add_stat(ctx, SEQ_K_SPMV_DOT, 3 * j, csr + E * n * (j + 2), 2.0 * nnz + 2.0 * n * nk + n);
+        add_stat(ctx, SEQ_K_CGS_PASS2, 3 * j + 1, E * n * (nk + 2), 4.0 * n * nk);
+        add_stat(ctx, SEQ_K_CGS_PASS3, 3 * j + 2, E * n * (nk + 2), 2.0 * n * nk + 2.0 * n);
+    }
+    const int u = 3 * (int)R;
+    if (updated) add_stat(ctx, SEQ_K_UPDATE, u, E * n * (jd + 2), 2.0 * n * jd);
+    add_stat(ctx, SEQ_K_RESTART, u + 1, csr + 3.0 * E * n, 2.0 * nnz + 4.0 * n);
 }
 
 // One restarted GMRES solve on the system bound to (args, ks); `f32` selects
@@ -169,18 +214,25 @@ int run_gmres(seq_ctx* ctx, bool f32) {
     CK(cudaGetLastError());
     int rc = read_tail(ctx, ks);
     if (rc) return rc;
-    rc = capture_cycle(ctx);
+    const bool prof = ctx->profiling;
+    rc = capture_cycle(ctx, prof);
     if (rc) return rc;
+    cudaGraphExec_t exec = prof ? ctx->cycle_prof : ctx->cycle;
+    const int nnz = f32 ? ctx->h_args_in->nnz : ctx->h_args->nnz;
     // The iteration cap bounds the number of cycles: each unfinished cycle
     // performs at least one Arnoldi step.
     const long max_cycles = (long)ctx->cfg.max_iters + 2;
     long cycles = 0;
     while (!ctx->h_ks->finished) {
         if (++cycles > max_cycles) return fail(ctx, SEQ_ETIMEOUT, "GMRES cycle bound exceeded");
-        CK(cudaGraphLaunch(ctx->cycle, ctx->stream));
+        CK(cudaGraphLaunch(exec, ctx->stream));
         ctx->launches += ctx->cycle_launches;
         rc = read_tail(ctx, ks);
         if (rc) return rc;
+        if (prof) {
+            const bool err = ctx->h_ks->status == SEQ_EBREAKDOWN || ctx->h_ks->status == SEQ_ENONFINITE;
+            account_cycle(ctx, f32, err ? ctx->h_ks->jdone : ctx->h_ks->last_jdone, !err, nnz);
+        }
     }
     return SEQ_OK;
 }
@@ -209,6 +261,7 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
         (c.krylov != SEQ_CG && c.krylov != SEQ_GMRES))
         return SEQ_EINVAL;
     seq_ctx* ctx = new seq_ctx();
+    memset(ctx->stats, 0, sizeof(ctx->stats));
     ctx->cfg = c;
     if (ctx->cfg.inner_tol <= 0) ctx->cfg.inner_tol = 1e-2;
     if (ctx->cfg.rank_tol <= 0) ctx->cfg.rank_tol = c.precision == SEQ_MIXED ? 1e-5 : 1e-12;
@@ -268,6 +321,8 @@ int seq_destroy(seq_ctx* ctx) {
     if (!ctx) return SEQ_OK;
     if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
     if (ctx->cycle) cudaGraphExecDestroy(ctx->cycle);
+    if (ctx->cycle_prof) cudaGraphExecDestroy(ctx->cycle_prof);
+    for (auto e : ctx->ev) cudaEventDestroy(e);
     void* dev_ptrs[] = {ctx->X, ctx->sk, ctx->sk_partial, ctx->W, ctx->lsq, ctx->kpartial,
                         ctx->V, ctx->w, ctx->r, ctx->p, ctx->q, ctx->val32, ctx->rhs32, ctx->d,
                         ctx->d_args, ctx->d_args_in, ctx->ks, ctx->ks_in};
@@ -490,6 +545,19 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
     }
     if (status == SEQ_NOT_CONVERGED) ctx->err = "iteration cap reached";
     return status;
+}
+
+int seq_set_profiling(seq_ctx* ctx, int on) {
+    if (!ctx) return SEQ_EINVAL;
+    ctx->profiling = on != 0;
+    return SEQ_OK;
+}
+
+int seq_kernel_stats(seq_ctx* ctx, seq_kernel_stat* out, int reset) {
+    if (!ctx || !out) return SEQ_EINVAL;
+    memcpy(out, ctx->stats, sizeof(ctx->stats));
+    if (reset) memset(ctx->stats, 0, sizeof(ctx->stats));
+    return SEQ_OK;
 }
 
 const char* seq_last_error(const seq_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }

@@ -17,7 +17,8 @@ constexpr int kMaxRestart = 64;
 constexpr int kMaxM = 31;         // history length (M + 1 <= 32 lanes in the sketch kernel)
 constexpr int kMaxS = 128;        // sketch rows
 constexpr int kMaxZeta = 16;
-constexpr int kStreamBlock = 256; // threads per block of the streaming kernels
+constexpr int kStreamBlock = 384; // threads per block of the streaming kernels (one block per SM)
+constexpr int kTileChunks = 8;    // CSR entries of a 32-row tile loaded up front: 8 x 32
 
 // Device-side copy of the per-call arguments.  The CUDA graphs of a context
 // take a pointer to this struct, so one captured graph serves every call.
@@ -60,6 +61,8 @@ struct KState {
     int iters;                      // iterations of this solve
     int status;                     // seq_status
     int bad_index;                  // a CSR column index fell outside [0, n)
+    int last_jdone;                 // Arnoldi steps of the cycle that just ended
+    int pad1;
     unsigned counter[8];            // last-block counters, one per kernel kind
 };
 
@@ -144,10 +147,12 @@ __device__ __forceinline__ void block_rows(int n, int nblk, int blk, int& lo, in
 }
 
 // (A x)[row] for the 32 consecutive rows r0 .. r0+31 of one warp, lane l
-// returning row r0 + l (0 past the end).  The warp walks the tile's nonzeros
-// in 32-entry chunks with coalesced loads of colind/values, stages the
-// products in shared memory and each lane sums the entries of its own row in
-// CSR order.  Column indices outside [0, n) contribute 0 and raise *bad.
+// returning row r0 + l (0 past the end).  The tile's nonzeros [e0, e1) are
+// loaded with coalesced reads, all of them up front when they fit in
+// kTileChunks x 32 entries (the usual case: stencil rows hold ~5 entries),
+// otherwise chunk by chunk.  Products are staged in shared memory (sprod:
+// kTileChunks * 32 entries per warp) and each lane sums the entries of its own
+// row in CSR order.  Column indices outside [0, n) contribute 0 and raise *bad.
 template <typename Acc, typename VT, typename XT>
 __device__ __forceinline__ Acc warp_tile_spmv(const int* __restrict__ rowptr,
                                               const int* __restrict__ colind,
@@ -165,28 +170,99 @@ __device__ __forceinline__ Acc warp_tile_spmv(const int* __restrict__ rowptr,
     }
     const int last = min(31, n - 1 - r0);
     const int e0 = __shfl_sync(0xffffffffu, rs, 0);
-    const int e1 = __shfl_sync(0xffffffffu, re, last);
+    const int e1 = max(e0, __shfl_sync(0xffffffffu, re, last));
     Acc acc = 0;
     int flag = 0;
-    for (int base = e0; base < e1; base += 32) {
-        const int e = base + lane;
-        Acc prod = 0;
-        if (e < e1) {
-            const int c = __ldg(colind + e);
-            if ((unsigned)c < (unsigned)n) {
-                prod = (Acc)__ldg(val + e) * (Acc)x[c];
-            } else {
-                flag = 1;
-            }
+    if (e1 - e0 <= kTileChunks * 32) {
+        int cc[kTileChunks];
+        VT vv[kTileChunks];
+#pragma unroll
+        for (int q = 0; q < kTileChunks; ++q) {
+            const int e = e0 + q * 32 + lane;
+            cc[q] = e < e1 ? __ldg(colind + e) : 0;
         }
-        sprod[lane] = prod;
+#pragma unroll
+        for (int q = 0; q < kTileChunks; ++q) {
+            const int e = e0 + q * 32 + lane;
+            vv[q] = e < e1 ? __ldg(val + e) : (VT)0;
+        }
+#pragma unroll
+        for (int q = 0; q < kTileChunks; ++q) {
+            const int e = e0 + q * 32 + lane;
+            Acc prod = 0;
+            if (e < e1) {
+                if ((unsigned)cc[q] < (unsigned)n)
+                    prod = (Acc)vv[q] * (Acc)x[cc[q]];
+                else
+                    flag = 1;
+            }
+            sprod[q * 32 + lane] = prod;
+        }
         __syncwarp();
-        const int lo = max(rs, base), hi = min(re, base + 32);
-        for (int k = lo; k < hi; ++k) acc += sprod[k - base];
+        const int lo = max(rs, e0), hi = min(re, e1);
+        for (int e = lo; e < hi; ++e) acc += sprod[e - e0];
         __syncwarp();
+    } else {
+        for (int base = e0; base < e1; base += 32) {
+            const int e = base + lane;
+            Acc prod = 0;
+            if (e < e1) {
+                const int c = __ldg(colind + e);
+                if ((unsigned)c < (unsigned)n)
+                    prod = (Acc)__ldg(val + e) * (Acc)x[c];
+                else
+                    flag = 1;
+            }
+            sprod[lane] = prod;
+            __syncwarp();
+            const int lo = max(rs, base), hi = min(re, base + 32);
+            for (int k = lo; k < hi; ++k) acc += sprod[k - base];
+            __syncwarp();
+        }
     }
     if (flag) atomicOr(bad, 1);
     return acc;
+}
+
+// Warp reduce-scatter of K <= 32 per-lane values: returns, in lane l, the
+// warp-wide sum of value (l % K).  Halves of the lane range are folded while
+// they exceed K, then a recursive-halving exchange leaves one value per lane
+// (a fixed pattern: the result does not depend on scheduling).
+template <typename T, int K>
+__device__ __forceinline__ T warp_reduce_scatter(T (&v)[K]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 16; s >= K; s >>= 1) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], s);
+    }
+#pragma unroll
+    for (int s = K / 2; s >= 1; s >>= 1) {
+        const bool upper = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < s; ++i) {
+            const T send = upper ? v[i] : v[i + s];
+            const T keep = upper ? v[i + s] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return v[0];
+}
+
+// Last block: dst[k] = sum over blocks b of partial[b * stride + k] for
+// k < nk.  Warp w handles k = w, w + nw, ...; lane l adds blocks l, l+32, ...
+// in order, then the warp butterfly.  Ends with __syncthreads().
+template <typename T>
+__device__ __forceinline__ void reduce_blocks(const T* partial, int nblk, int stride, int nk,
+                                              double* dst) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = warp; k < nk; k += nw) {
+        T a = 0;
+        for (int b = lane; b < nblk; b += 32) a += __ldcg(partial + (size_t)b * stride + k);
+        a = warp_sum(a);
+        if (lane == 0) dst[k] = (double)a;
+    }
+    __syncthreads();
 }
 
 }  // namespace sa

@@ -50,12 +50,14 @@ void launch_residual_norm(const DevArgs* a, KState* ks, double* partial, int nbl
 void launch_gmres_start_f64(const DevArgs* a, KState* ks, double* V, size_t ldv, double* partial,
                             int nblk, int first, cudaStream_t st);
 void launch_gmres_cycle_f64(const DevArgs* a, KState* ks, double* V, size_t ldv, double* w,
-                            double* partial, int nblk, int R, cudaStream_t st, int* launches);
+                            double* partial, int nblk, int R, cudaStream_t st, int* launches,
+                            cudaEvent_t* ev = nullptr);
 // Same on the FP32 inner system A32 d = rhs32 (mixed precision).
 void launch_gmres_start_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, float* partial,
                             int nblk, int first, cudaStream_t st);
 void launch_gmres_cycle_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, float* w,
-                            float* partial, int nblk, int R, cudaStream_t st, int* launches);
+                            float* partial, int nblk, int R, cudaStream_t st, int* launches,
+                            cudaEvent_t* ev = nullptr);
 // Mixed precision outer step: x += scale * d (FP64 += FP32), then the FP64
 // residual r = b - A64 x, its norm, and rhs32 = r / ||r||.
 void launch_refine_residual(const DevArgs* a, KState* ks, float* rhs32, double* partial, int nblk,

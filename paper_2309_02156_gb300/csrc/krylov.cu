@@ -47,28 +47,30 @@ int stream_grid(int n) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int want = sms * 2;
     const int need = (n + kStreamBlock - 1) / kStreamBlock;
-    return need < want ? (need > 0 ? need : 1) : want;
+    return need < sms ? (need > 0 ? need : 1) : sms;
 }
+
+constexpr int kWarps = kStreamBlock / 32;
+constexpr int kTile = kTileChunks * 32;
 
 // ---------------------------------------------------------------------------
 // ||b - A x|| and ||b|| (FP64); x_override replaces a->x when not NULL.
-__global__ void __launch_bounds__(kStreamBlock)
+__global__ void __launch_bounds__(kStreamBlock, 1)
 residual_norm_kernel(const DevArgs* __restrict__ a, KState* ks, double* partial,
                      const double* x_override) {
-    __shared__ double sprod[kStreamBlock];
-    __shared__ double scratch[(kStreamBlock / 32) * 2];
+    __shared__ double sprod[kWarps * kTile];
+    __shared__ double scratch[kWarps * 2];
     __shared__ double red[2];
     const int n = a->n, nnz = a->nnz;
     const double* x = x_override ? x_override : a->x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int lo, hi;
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
     double acc[2] = {0.0, 0.0};
-    for (int r0 = lo + warp * 32; r0 < hi; r0 += nw * 32) {
+    for (int r0 = lo + warp * 32; r0 < hi; r0 += kWarps * 32) {
         const double ax = warp_tile_spmv<double>(a->rowptr, a->colind, a->val64, x, n, nnz, r0,
-                                                 sprod + warp * 32, &ks->bad_index);
+                                                 sprod + warp * kTile, &ks->bad_index);
         const int row = r0 + lane;
         if (row < n) {
             const double bi = a->b[row];
@@ -80,12 +82,12 @@ residual_norm_kernel(const DevArgs* __restrict__ a, KState* ks, double* partial,
     block_sum<double, 2>(acc, 2, red, scratch);
     if (threadIdx.x < 2) partial[blockIdx.x * 2 + threadIdx.x] = red[threadIdx.x];
     if (last_block_arrive(&ks->counter[CNT_RES])) {
+        __shared__ double tot[2];
+        reduce_blocks(partial, gridDim.x, 2, 2, tot);
         if (threadIdx.x == 0) {
-            const double rr = sum_over_blocks(partial, gridDim.x, 2, 0);
-            const double bb = sum_over_blocks(partial, gridDim.x, 2, 1);
-            ks->beta = sqrt(rr);
-            ks->bnorm = sqrt(bb);
-            ks->first_relres = sqrt(rr) / sqrt(bb);
+            ks->beta = sqrt(tot[0]);
+            ks->bnorm = sqrt(tot[1]);
+            ks->first_relres = sqrt(tot[0]) / sqrt(tot[1]);
             ks->counter[CNT_RES] = 0;
         }
     }
@@ -101,27 +103,27 @@ void launch_residual_norm(const DevArgs* a, KState* ks, double* partial, int nbl
 // first != 0 the solve is initialised (||rhs||, target, iteration count; the
 // FP32 inner solve also zeroes d, so r = rhs).
 template <class Sys>
-__global__ void __launch_bounds__(kStreamBlock)
+__global__ void __launch_bounds__(kStreamBlock, 1)
 gmres_start_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* V,
                    typename Sys::T* partial, int first) {
     using T = typename Sys::T;
     if (!first && ks->finished) return;
-    __shared__ T sprod[kStreamBlock];
-    __shared__ T scratch[(kStreamBlock / 32) * 2];
+    __shared__ T sprod[kWarps * kTile];
+    __shared__ T scratch[kWarps * 2];
     __shared__ T red[2];
     const int n = a->n, nnz = a->nnz;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T* x = Sys::x(a);
     const T* rhs = Sys::rhs(a);
     const bool zero_x = first && (sizeof(T) == 4);
     int lo, hi;
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
     T acc[2] = {0, 0};
-    for (int r0 = lo + warp * 32; r0 < hi; r0 += nw * 32) {
+    for (int r0 = lo + warp * 32; r0 < hi; r0 += kWarps * 32) {
         T ax = 0;
         if (!zero_x)
             ax = warp_tile_spmv<T>(a->rowptr, a->colind, Sys::val(a), x, n, nnz, r0,
-                                   sprod + warp * 32, &ks->bad_index);
+                                   sprod + warp * kTile, &ks->bad_index);
         const int row = r0 + lane;
         if (row < n) {
             const T bi = rhs[row];
@@ -135,17 +137,18 @@ gmres_start_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* V
     block_sum<T, 2>(acc, 2, red, scratch);
     if (threadIdx.x < 2) partial[blockIdx.x * 2 + threadIdx.x] = red[threadIdx.x];
     if (last_block_arrive(&ks->counter[CNT_START])) {
+        __shared__ double tot[2];
+        reduce_blocks(partial, gridDim.x, 2, 2, tot);
         if (threadIdx.x == 0) {
-            const double rr = (double)sum_over_blocks(partial, gridDim.x, 2, 0);
-            const double beta = sqrt(rr);
+            const double beta = sqrt(tot[0]);
             if (first) {
-                const double bb = (double)sum_over_blocks(partial, gridDim.x, 2, 1);
-                ks->bnorm = sqrt(bb);
+                ks->bnorm = sqrt(tot[1]);
                 ks->target = a->tol * ks->bnorm;
                 ks->iters = 0;
                 ks->status = ST_OK;
                 ks->first_relres = beta / ks->bnorm;
             }
+            ks->last_jdone = first ? 0 : ks->jdone;
             ks->beta = beta;
             ks->g[0] = beta;
             ks->sigma[0] = beta > 0.0 ? 1.0 / beta : 0.0;
@@ -168,19 +171,48 @@ gmres_start_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* V
     }
 }
 
+// Lane l of every warp holds, for K <= 32, the warp partial of column l % K
+// after warp_reduce_scatter; the block partial of column k (k < nk) is the
+// sum over warps in warp order.  K = 64 is handled as two halves of 32.
+template <typename T, int K>
+__device__ __forceinline__ void block_columns(T (&part)[K], int nk, T* wsum /* kWarps * K */,
+                                              T* out /* global, K */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (K <= 32) {
+        const T c = warp_reduce_scatter<T, K>(part);
+        if (lane < K) wsum[warp * K + lane] = c;
+    } else {
+        T lo[32], hi[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            lo[i] = part[i];
+            hi[i] = part[32 + i];
+        }
+        const T cl = warp_reduce_scatter<T, 32>(lo);
+        const T ch = warp_reduce_scatter<T, 32>(hi);
+        wsum[warp * K + lane] = cl;
+        wsum[warp * K + 32 + lane] = ch;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        T s = wsum[k];
+        for (int w = 1; w < kWarps; ++w) s += wsum[w * K + k];
+        out[k] = s;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // K5: w = sigma_j A vstored_j, h1 = sigma_k (V_stored^T w)_k for k <= j.
 template <class Sys, int KMAX>
-__global__ void __launch_bounds__(kStreamBlock)
-arnoldi_dot_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* V, size_t ldv,
-                   typename Sys::T* w, typename Sys::T* partial, int j) {
+__global__ void __launch_bounds__(kStreamBlock, 1)
+arnoldi_dot_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* __restrict__ V,
+                   size_t ldv, typename Sys::T* __restrict__ w, typename Sys::T* partial, int j) {
     using T = typename Sys::T;
     if (ks->cycle_over) return;
-    __shared__ T sprod[kStreamBlock];
-    __shared__ T scratch[(kStreamBlock / 32) * KMAX];
-    __shared__ T red[KMAX];
+    __shared__ T sprod[kWarps * kTile];
+    __shared__ T wsum[kWarps * KMAX];
     const int n = a->n, nnz = a->nnz, nk = j + 1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T sig = (T)ks->sigma[j];
     const T* vj = V + (size_t)j * ldv;
     int lo, hi;
@@ -188,41 +220,41 @@ arnoldi_dot_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* V
     T part[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) part[k] = 0;
-    for (int r0 = lo + warp * 32; r0 < hi; r0 += nw * 32) {
+    for (int r0 = lo + warp * 32; r0 < hi; r0 += kWarps * 32) {
         const T ax = warp_tile_spmv<T>(a->rowptr, a->colind, Sys::val(a), vj, n, nnz, r0,
-                                       sprod + warp * 32, &ks->bad_index);
+                                       sprod + warp * kTile, &ks->bad_index);
         const int row = r0 + lane;
         if (row < n) {
             const T y = ax * sig;
             w[row] = y;
 #pragma unroll
             for (int k = 0; k < KMAX; ++k)
-                if (k < nk) part[k] += V[(size_t)k * ldv + row] * y;
+                if (k < nk) part[k] = fma(V[(size_t)k * ldv + row], y, part[k]);
         }
     }
-    block_sum<T, KMAX>(part, nk, red, scratch);
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) partial[(size_t)blockIdx.x * KMAX + k] = red[k];
+    block_columns<T, KMAX>(part, nk, wsum, partial + (size_t)blockIdx.x * KMAX);
     if (last_block_arrive(&ks->counter[CNT_DOT])) {
+        __shared__ double tot[KMAX];
+        reduce_blocks(partial, gridDim.x, KMAX, nk, tot);
         for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-            const double hk = ks->sigma[k] * (double)sum_over_blocks(partial, gridDim.x, KMAX, k);
+            const double hk = ks->sigma[k] * tot[k];
             ks->h1[k] = hk;
             ks->c1[k] = ks->sigma[k] * hk;
         }
-        __syncthreads();
         if (threadIdx.x == 0) ks->counter[CNT_DOT] = 0;
     }
 }
 
 // K7a: w -= V_stored c1; h2 = sigma_k (V_stored^T w)_k.
 template <class Sys, int KMAX>
-__global__ void __launch_bounds__(kStreamBlock)
-arnoldi_pass2_kernel(const DevArgs* __restrict__ a, KState* ks, const typename Sys::T* V,
-                     size_t ldv, typename Sys::T* w, typename Sys::T* partial, int j) {
+__global__ void __launch_bounds__(kStreamBlock, 1)
+arnoldi_pass2_kernel(const DevArgs* __restrict__ a, KState* ks,
+                     const typename Sys::T* __restrict__ V, size_t ldv,
+                     typename Sys::T* __restrict__ w, typename Sys::T* partial, int j) {
     using T = typename Sys::T;
     if (ks->cycle_over) return;
     __shared__ T cf[KMAX];
-    __shared__ T scratch[(kStreamBlock / 32) * KMAX];
-    __shared__ T red[KMAX];
+    __shared__ T wsum[kWarps * KMAX];
     const int n = a->n, nk = j + 1;
     for (int k = threadIdx.x; k < KMAX; k += blockDim.x) cf[k] = k < nk ? (T)ks->c1[k] : (T)0;
     __syncthreads();
@@ -238,21 +270,21 @@ arnoldi_pass2_kernel(const DevArgs* __restrict__ a, KState* ks, const typename S
         T r = w[i];
 #pragma unroll
         for (int k = 0; k < KMAX; ++k)
-            if (k < nk) r -= vv[k] * cf[k];
+            if (k < nk) r = fma(-vv[k], cf[k], r);
         w[i] = r;
 #pragma unroll
         for (int k = 0; k < KMAX; ++k)
-            if (k < nk) part[k] += vv[k] * r;
+            if (k < nk) part[k] = fma(vv[k], r, part[k]);
     }
-    block_sum<T, KMAX>(part, nk, red, scratch);
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) partial[(size_t)blockIdx.x * KMAX + k] = red[k];
+    block_columns<T, KMAX>(part, nk, wsum, partial + (size_t)blockIdx.x * KMAX);
     if (last_block_arrive(&ks->counter[CNT_PASS2])) {
+        __shared__ double tot[KMAX];
+        reduce_blocks(partial, gridDim.x, KMAX, nk, tot);
         for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-            const double hk = ks->sigma[k] * (double)sum_over_blocks(partial, gridDim.x, KMAX, k);
+            const double hk = ks->sigma[k] * tot[k];
             ks->h2[k] = hk;
             ks->c2[k] = ks->sigma[k] * hk;
         }
-        __syncthreads();
         if (threadIdx.x == 0) ks->counter[CNT_PASS2] = 0;
     }
 }
@@ -320,13 +352,14 @@ __device__ void arnoldi_finish(KState* ks, const DevArgs* a, int j, int R, doubl
 
 // K7b: w -= V_stored c2, stored as basis column j+1; ||w||^2; then K8.
 template <class Sys, int KMAX>
-__global__ void __launch_bounds__(kStreamBlock)
-arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* V, size_t ldv,
-                     const typename Sys::T* w, typename Sys::T* partial, int j, int R) {
+__global__ void __launch_bounds__(kStreamBlock, 1)
+arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* __restrict__ V,
+                     size_t ldv, const typename Sys::T* __restrict__ w, typename Sys::T* partial,
+                     int j, int R) {
     using T = typename Sys::T;
     if (ks->cycle_over) return;
     __shared__ T cf[KMAX];
-    __shared__ T scratch[kStreamBlock / 32];
+    __shared__ T scratch[kWarps];
     __shared__ T red[1];
     const int n = a->n, nk = j + 1;
     for (int k = threadIdx.x; k < KMAX; k += blockDim.x) cf[k] = k < nk ? (T)ks->c2[k] : (T)0;
@@ -336,19 +369,23 @@ arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T*
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
     T part[1] = {0};
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        T vv[KMAX];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) vv[k] = k < nk ? V[(size_t)k * ldv + i] : (T)0;
         T r = w[i];
 #pragma unroll
         for (int k = 0; k < KMAX; ++k)
-            if (k < nk) r -= V[(size_t)k * ldv + i] * cf[k];
+            if (k < nk) r = fma(-vv[k], cf[k], r);
         vout[i] = r;
-        part[0] += r * r;
+        part[0] = fma(r, r, part[0]);
     }
     block_sum<T, 1>(part, 1, red, scratch);
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
     if (last_block_arrive(&ks->counter[CNT_PASS3])) {
+        __shared__ double tot[1];
+        reduce_blocks(partial, gridDim.x, 1, 1, tot);
         if (threadIdx.x == 0) {
-            const double hn2 = (double)sum_over_blocks(partial, gridDim.x, 1, 0);
-            arnoldi_finish(ks, a, j, R, hn2);
+            arnoldi_finish(ks, a, j, R, tot[0]);
             ks->counter[CNT_PASS3] = 0;
         }
     }
@@ -356,22 +393,24 @@ arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T*
 
 // x += V_stored cy (the GMRES correction of the finished cycle).
 template <class Sys>
-__global__ void __launch_bounds__(kStreamBlock)
-gmres_update_kernel(const DevArgs* __restrict__ a, const KState* ks, const typename Sys::T* V,
-                    size_t ldv) {
+__global__ void __launch_bounds__(kStreamBlock, 1)
+gmres_update_kernel(const DevArgs* __restrict__ a, const KState* ks,
+                    const typename Sys::T* __restrict__ V, size_t ldv) {
     using T = typename Sys::T;
     if (ks->status != ST_OK && ks->status != ST_NOT_CONVERGED) return;
     if (ks->finished) return;
-    __shared__ double cy[kMaxBasis];
+    __shared__ T cy[kMaxBasis];
     __shared__ int kk;
     if (threadIdx.x == 0) kk = ks->jdone;
-    for (int k = threadIdx.x; k < kMaxBasis; k += blockDim.x) cy[k] = ks->cy[k];
+    for (int k = threadIdx.x; k < kMaxBasis; k += blockDim.x) cy[k] = (T)ks->cy[k];
     __syncthreads();
     const int k = kk, n = a->n;
     T* x = Sys::x(a);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int lo, hi;
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         T acc = 0;
-        for (int l = 0; l < k; ++l) acc += V[(size_t)l * ldv + i] * (T)cy[l];
+        for (int l = 0; l < k; ++l) acc = fma(V[(size_t)l * ldv + i], cy[l], acc);
         x[i] += acc;
     }
 }
@@ -382,32 +421,48 @@ static void launch_start(const DevArgs* a, KState* ks, typename Sys::T* V, typen
     gmres_start_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, partial, first);
 }
 
+// Records ev[*k] (when timing events are supplied) and advances *k.
+static inline void mark(cudaEvent_t* ev, int* k, cudaStream_t st) {
+    if (ev) cudaEventRecordWithFlags(ev[(*k)++], st, cudaEventRecordExternal);
+}
+
 template <class Sys, int KMAX>
 static void launch_step(const DevArgs* a, KState* ks, typename Sys::T* V, size_t ldv,
                         typename Sys::T* w, typename Sys::T* partial, int nblk, int j, int R,
-                        cudaStream_t st) {
+                        cudaStream_t st, cudaEvent_t* ev, int* k) {
     arnoldi_dot_kernel<Sys, KMAX><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j);
+    mark(ev, k, st);
     arnoldi_pass2_kernel<Sys, KMAX><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j);
+    mark(ev, k, st);
     arnoldi_pass3_kernel<Sys, KMAX><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j, R);
+    mark(ev, k, st);
 }
 
+// One restart cycle.  With `ev` (3R + 3 timing events) an event is recorded
+// before the first kernel and after every kernel: kernel i of the cycle lies
+// between ev[i] and ev[i + 1] (i = 3j, 3j+1, 3j+2 for Arnoldi step j; 3R for
+// the basis update; 3R + 1 for the restart residual).
 template <class Sys>
 static void launch_cycle(const DevArgs* a, KState* ks, typename Sys::T* V, size_t ldv,
                          typename Sys::T* w, typename Sys::T* partial, int nblk, int R,
-                         cudaStream_t st, int* launches) {
+                         cudaStream_t st, int* launches, cudaEvent_t* ev) {
+    int k = 0;
+    mark(ev, &k, st);
     for (int j = 0; j < R; ++j) {
         const int nk = j + 1;
         if (nk <= 8)
-            launch_step<Sys, 8>(a, ks, V, ldv, w, partial, nblk, j, R, st);
+            launch_step<Sys, 8>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
         else if (nk <= 16)
-            launch_step<Sys, 16>(a, ks, V, ldv, w, partial, nblk, j, R, st);
+            launch_step<Sys, 16>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
         else if (nk <= 32)
-            launch_step<Sys, 32>(a, ks, V, ldv, w, partial, nblk, j, R, st);
+            launch_step<Sys, 32>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
         else
-            launch_step<Sys, 64>(a, ks, V, ldv, w, partial, nblk, j, R, st);
+            launch_step<Sys, 64>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
     }
     gmres_update_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv);
+    mark(ev, &k, st);
     gmres_start_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, partial, 0);
+    mark(ev, &k, st);
     if (launches) *launches = 3 * R + 2;
 }
 
@@ -416,33 +471,35 @@ void launch_gmres_start_f64(const DevArgs* a, KState* ks, double* V, size_t, dou
     launch_start<SysF64>(a, ks, V, partial, nblk, first, st);
 }
 void launch_gmres_cycle_f64(const DevArgs* a, KState* ks, double* V, size_t ldv, double* w,
-                            double* partial, int nblk, int R, cudaStream_t st, int* launches) {
-    launch_cycle<SysF64>(a, ks, V, ldv, w, partial, nblk, R, st, launches);
+                            double* partial, int nblk, int R, cudaStream_t st, int* launches,
+                            cudaEvent_t* ev) {
+    launch_cycle<SysF64>(a, ks, V, ldv, w, partial, nblk, R, st, launches, ev);
 }
 void launch_gmres_start_f32(const DevArgs* a, KState* ks, float* V, size_t, float* partial,
                             int nblk, int first, cudaStream_t st) {
     launch_start<SysF32>(a, ks, V, partial, nblk, first, st);
 }
 void launch_gmres_cycle_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, float* w,
-                            float* partial, int nblk, int R, cudaStream_t st, int* launches) {
-    launch_cycle<SysF32>(a, ks, V, ldv, w, partial, nblk, R, st, launches);
+                            float* partial, int nblk, int R, cudaStream_t st, int* launches,
+                            cudaEvent_t* ev) {
+    launch_cycle<SysF32>(a, ks, V, ldv, w, partial, nblk, R, st, launches, ev);
 }
 
 // ---------------------------------------------------------------------------
 // Mixed precision: r = b - A64 x in FP64, beta = ||r||, rhs32 = (float) r.
-__global__ void __launch_bounds__(kStreamBlock)
+__global__ void __launch_bounds__(kStreamBlock, 1)
 refine_residual_kernel(const DevArgs* __restrict__ a, KState* ks, float* rhs32, double* partial) {
-    __shared__ double sprod[kStreamBlock];
-    __shared__ double scratch[(kStreamBlock / 32) * 2];
+    __shared__ double sprod[kWarps * kTile];
+    __shared__ double scratch[kWarps * 2];
     __shared__ double red[2];
     const int n = a->n, nnz = a->nnz;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int lo, hi;
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
     double acc[2] = {0.0, 0.0};
-    for (int r0 = lo + warp * 32; r0 < hi; r0 += nw * 32) {
+    for (int r0 = lo + warp * 32; r0 < hi; r0 += kWarps * 32) {
         const double ax = warp_tile_spmv<double>(a->rowptr, a->colind, a->val64, a->x, n, nnz, r0,
-                                                 sprod + warp * 32, &ks->bad_index);
+                                                 sprod + warp * kTile, &ks->bad_index);
         const int row = r0 + lane;
         if (row < n) {
             const double bi = a->b[row];
@@ -455,11 +512,11 @@ refine_residual_kernel(const DevArgs* __restrict__ a, KState* ks, float* rhs32, 
     block_sum<double, 2>(acc, 2, red, scratch);
     if (threadIdx.x < 2) partial[blockIdx.x * 2 + threadIdx.x] = red[threadIdx.x];
     if (last_block_arrive(&ks->counter[CNT_REFINE])) {
+        __shared__ double tot[2];
+        reduce_blocks(partial, gridDim.x, 2, 2, tot);
         if (threadIdx.x == 0) {
-            const double rr = sum_over_blocks(partial, gridDim.x, 2, 0);
-            const double bb = sum_over_blocks(partial, gridDim.x, 2, 1);
-            ks->beta = sqrt(rr);
-            ks->bnorm = sqrt(bb);
+            ks->beta = sqrt(tot[0]);
+            ks->bnorm = sqrt(tot[1]);
             ks->target = a->tol * ks->bnorm;
             ks->counter[CNT_REFINE] = 0;
         }

@@ -166,9 +166,15 @@ def test_cg_parity(N):
     seq.close()
 
 
-def test_sequence_spd_plain_workload():
-    """64x64 SPD sequence (n = 4096, M = 10, s = 40, CG to 1e-10), 60 systems run
-    end to end on the GPU (its own history) and in the oracle (its own history)."""
+@pytest.mark.parametrize("shared_history", [True, False])
+def test_sequence_spd_plain_workload(shared_history):
+    """64x64 SPD sequence (n = 4096, M = 10, s = 40, CG to 1e-10), 60 systems.
+
+    shared_history: the GPU ring receives the oracle's solutions, so both sides
+    guess from identical data and per-step CG counts must agree.  Otherwise
+    each side keeps its own history; the two trajectories then drift apart by
+    rounding (each solution is only accurate to the 1e-10 tolerance), so only
+    the mean count over the steps with a full history is compared."""
     p = workloads.plain_spd(64)
     M, s = 10, 40
     S = sketch.sparse_sign_matrix(p.n, s, 8, 0x5EEDBA5E)
@@ -183,14 +189,16 @@ def test_sequence_spd_plain_workload():
         x = torch.empty(p.n, dtype=torch.float64, device=DEV)
         seq.guess(Ad, bd, x)
         info = seq.solve(Ad, bd, 1e-10, x)
-        seq.push(x)
+        seq.push(_tensor(out["x"]) if shared_history else x)
         assert info["status"] == 0
         assert method.relres(A, b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-9)
         it_gpu.append(info["iters"])
         it_ref.append(out["iters"])
     it_gpu, it_ref = np.array(it_gpu), np.array(it_ref)
-    assert np.all(np.abs(it_gpu - it_ref) <= np.maximum(4, 0.1 * it_ref))
-    assert abs(it_gpu[10:].mean() - it_ref[10:].mean()) <= 0.03 * it_ref[10:].mean()
+    assert np.all(np.abs(it_gpu[:M] - it_ref[:M]) <= 2)
+    if shared_history:
+        assert np.all(np.abs(it_gpu - it_ref) <= np.maximum(3, 0.05 * it_ref))
+    assert abs(it_gpu[M:].mean() - it_ref[M:].mean()) <= 0.03 * it_ref[M:].mean()
     seq.close()
 
 
@@ -203,17 +211,23 @@ def test_full_size_nonsymmetric_workload():
     M, s = 20, 80
     i = 21
     rng = np.random.default_rng(5)
-    hist = []
-    for k in range(M):       # smooth synthetic history: right-hand sides of earlier times
-        hist.append(workloads.rhs(p, workloads.time_grid(p, k)) * (1 + 0.01 * rng.standard_normal()))
-    seq = _sa().Sequence(p.n, M, s, seed=0x5EEDBA5E, krylov="gmres", restart=30, max_iters=30000)
+    # Well-conditioned synthetic history (seeded Gaussian columns), so that y and
+    # x0 are determined to working precision and can be compared directly.
+    hist = [rng.standard_normal(p.n) for _ in range(M)]
+    seq = _sa().Sequence(p.n, M, s, seed=0x5EEDBA5E, krylov="gmres", restart=30, max_iters=60000)
     info, x0, A, b = _run_guess(seq, p, i, hist)
     S = sketch.sparse_sign_matrix(p.n, s, 8, 0x5EEDBA5E)
     ref = method.sketched_guess(A, b, np.stack(hist, axis=1), S)
-    W, _ = seq.last_sketch()
+    W, y = seq.last_sketch()
     W = W[: s * (M + 1)].reshape(s, M + 1)
     assert np.all(np.abs(W - ref.W) <= 1e-11 * np.linalg.norm(ref.W, axis=0))
-    assert info["guess_relres"] == pytest.approx(method.relres(A, b, ref.x0), rel=1e-3)
+    np.testing.assert_allclose(y[:M], ref.y, rtol=1e-9, atol=1e-9 * np.abs(ref.y).max())
+    assert np.linalg.norm(x0 - ref.x0) <= 1e-9 * np.linalg.norm(ref.x0)
+    assert info["guess_relres"] == pytest.approx(method.relres(A, b, ref.x0), rel=1e-9)
+    # Sampled rows of the GPU guess against the oracle, one by one.
+    Xs = np.stack(hist, axis=1)
+    for r in rng.integers(0, p.n, 64):
+        assert abs(x0[r] - Xs[r] @ ref.y) <= 1e-9 * np.abs(Xs[r]).sum() * np.abs(ref.y).max()
     rowptr, colind, vals, _ = workloads.csr_system(p, i)
     Ad, bd = _dev_system(rowptr, colind, vals, b)
     x = _tensor(x0)
@@ -236,11 +250,11 @@ def test_edge_cases():
     assert info["guess_relres"] == pytest.approx(1.0)
     info = seq.solve(Ad, bd, 1e3, x)     # already below the tolerance: 0 iterations
     assert info["iters"] == 0 and info["status"] == 0
-    info = seq.solve(Ad, bd, 1e-14, x, allow=(1,))   # cap reached
-    assert info["rc"] == 1
+    info = seq.solve(Ad, bd, 1e-30, x, allow=(1,))   # unreachable: cap reached
+    assert info["rc"] == 1 and info["iters"] == 1000
     seq2 = sa.Sequence(p.n, 3, 8, zeta=4, seed=1, krylov="gmres", restart=5, max_iters=7)
     x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
-    info = seq2.solve(Ad, bd, 1e-14, x, allow=(1,))
+    info = seq2.solve(Ad, bd, 1e-30, x, allow=(1,))
     assert info["rc"] == 1 and info["iters"] == 7
     # One pushed column: the guess uses it (m < M start-up).
     xs = np.linalg.solve(A.toarray(), b)
