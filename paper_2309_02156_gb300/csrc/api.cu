@@ -33,7 +33,7 @@ struct seq_ctx {
     LsqOut* lsq = nullptr;
     LsqOut* lsq_host = nullptr;      // pinned
     int nblk = 0;
-    double* kpartial = nullptr;      // nblk * 64 doubles
+    double* kpartial = nullptr;      // nblk * 80 doubles (per-block partial sums)
     size_t ldv = 0;
     void* V = nullptr;               // (restart+1) x ldv basis (GMRES)
     void* w = nullptr;
@@ -281,7 +281,7 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
     ok = ok && cudaMalloc(&ctx->lsq, sizeof(LsqOut)) == cudaSuccess;
     ok = ok && cudaMallocHost(&ctx->lsq_host, sizeof(LsqOut)) == cudaSuccess;
     ctx->nblk = stream_grid(n);
-    ok = ok && cudaMalloc(&ctx->kpartial, sizeof(double) * (size_t)ctx->nblk * 64) == cudaSuccess;
+    ok = ok && cudaMalloc(&ctx->kpartial, sizeof(double) * (size_t)ctx->nblk * 80) == cudaSuccess;
     ctx->ldv = (size_t)round_up(n, 64);
     if (c.krylov == SEQ_GMRES) {
         ok = ok && cudaMalloc(&ctx->V, el * ctx->ldv * (c.restart + 1)) == cudaSuccess;

@@ -178,8 +178,14 @@ template <typename T, int K>
 __device__ __forceinline__ void block_columns(T (&part)[K], int nk, T* wsum /* kWarps * K */,
                                               T* out /* global, K */) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if constexpr (K <= 32) {
+    if constexpr (K <= 32 && (K & (K - 1)) == 0) {
         const T c = warp_reduce_scatter<T, K>(part);
+        if (lane < K) wsum[warp * K + lane] = c;
+    } else if constexpr (K < 32) {
+        T v[32];                                   // pad to the next power of two
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = i < K ? part[i] : (T)0;
+        const T c = warp_reduce_scatter<T, 32>(v);
         if (lane < K) wsum[warp * K + lane] = c;
     } else {
         T lo[32], hi[32];
@@ -203,39 +209,64 @@ __device__ __forceinline__ void block_columns(T (&part)[K], int nk, T* wsum /* k
 
 // ---------------------------------------------------------------------------
 // K5: w = sigma_j A vstored_j, h1 = sigma_k (V_stored^T w)_k for k <= j.
-template <class Sys, int KMAX>
-__global__ void __launch_bounds__(kStreamBlock, 1)
+// Phase 1: warp tiles of the CSR product write w (global, and shared memory
+// when the block's rows fit).  Phase 2: warp q takes basis columns q, q+nw, ...
+// and streams V[k][lo:hi) against w; each lane keeps four accumulators (rows
+// l, l+32, l+64, l+96 of every 128) combined in a fixed order, then the warp
+// butterfly.  Column-wise dots need no per-thread array of partial sums.
+constexpr int kDotBlock = 768;
+constexpr int kDotWarps = kDotBlock / 32;
+constexpr int kDotSmemRows = 8192;
+
+template <class Sys>
+__global__ void __launch_bounds__(kDotBlock, 1)
 arnoldi_dot_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* __restrict__ V,
-                   size_t ldv, typename Sys::T* __restrict__ w, typename Sys::T* partial, int j) {
+                   size_t ldv, typename Sys::T* __restrict__ w, typename Sys::T* partial, int j,
+                   int stride) {
     using T = typename Sys::T;
     if (ks->cycle_over) return;
-    __shared__ T sprod[kWarps * kTile];
-    __shared__ T wsum[kWarps * KMAX];
+    extern __shared__ unsigned char dsm[];
+    T* sprod = reinterpret_cast<T*>(dsm);                   // kDotWarps * kTile
+    T* ws = sprod + kDotWarps * kTile;                       // kDotSmemRows
     const int n = a->n, nnz = a->nnz, nk = j + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T sig = (T)ks->sigma[j];
     const T* vj = V + (size_t)j * ldv;
     int lo, hi;
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
-    T part[KMAX];
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k) part[k] = 0;
-    for (int r0 = lo + warp * 32; r0 < hi; r0 += kWarps * 32) {
+    const bool in_smem = (hi - lo) <= kDotSmemRows;
+    for (int r0 = lo + warp * 32; r0 < hi; r0 += kDotWarps * 32) {
         const T ax = warp_tile_spmv<T>(a->rowptr, a->colind, Sys::val(a), vj, n, nnz, r0,
                                        sprod + warp * kTile, &ks->bad_index);
         const int row = r0 + lane;
-        if (row < n) {
+        if (row < hi) {
             const T y = ax * sig;
             w[row] = y;
-#pragma unroll
-            for (int k = 0; k < KMAX; ++k)
-                if (k < nk) part[k] = fma(V[(size_t)k * ldv + row], y, part[k]);
+            if (in_smem) ws[row - lo] = y;
         }
     }
-    block_columns<T, KMAX>(part, nk, wsum, partial + (size_t)blockIdx.x * KMAX);
+    __syncthreads();
+    const T* wsrc = in_smem ? ws - lo : w;
+    __shared__ T colsum[kMaxBasis];
+    for (int k = warp; k < nk; k += kDotWarps) {
+        const T* vk = V + (size_t)k * ldv;
+        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        int i = lo + lane;
+        for (; i + 96 < hi; i += 128) {
+            s0 = fma(vk[i], wsrc[i], s0);
+            s1 = fma(vk[i + 32], wsrc[i + 32], s1);
+            s2 = fma(vk[i + 64], wsrc[i + 64], s2);
+            s3 = fma(vk[i + 96], wsrc[i + 96], s3);
+        }
+        for (; i < hi; i += 32) s0 = fma(vk[i], wsrc[i], s0);
+        T t = warp_sum((s0 + s1) + (s2 + s3));
+        if (lane == 0) colsum[k] = t;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) partial[(size_t)blockIdx.x * stride + k] = colsum[k];
     if (last_block_arrive(&ks->counter[CNT_DOT])) {
-        __shared__ double tot[KMAX];
-        reduce_blocks(partial, gridDim.x, KMAX, nk, tot);
+        __shared__ double tot[kMaxBasis];
+        reduce_blocks(partial, gridDim.x, stride, nk, tot);
         for (int k = threadIdx.x; k < nk; k += blockDim.x) {
             const double hk = ks->sigma[k] * tot[k];
             ks->h1[k] = hk;
@@ -245,7 +276,10 @@ arnoldi_dot_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* _
     }
 }
 
-// K7a: w -= V_stored c1; h2 = sigma_k (V_stored^T w)_k.
+// K7a: w -= V_stored c1; h2 = sigma_k (V_stored^T w)_k.  One row per thread;
+// the subtraction runs as four interleaved partial sums (independent FMA
+// chains), the dot partials accumulate per thread and are reduce-scattered
+// over the warp once at the end.
 template <class Sys, int KMAX>
 __global__ void __launch_bounds__(kStreamBlock, 1)
 arnoldi_pass2_kernel(const DevArgs* __restrict__ a, KState* ks,
@@ -267,10 +301,11 @@ arnoldi_pass2_kernel(const DevArgs* __restrict__ a, KState* ks,
         T vv[KMAX];
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) vv[k] = k < nk ? V[(size_t)k * ldv + i] : (T)0;
-        T r = w[i];
+        T q[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int k = 0; k < KMAX; ++k)
-            if (k < nk) r = fma(-vv[k], cf[k], r);
+            if (k < nk) q[k & 3] = fma(vv[k], cf[k], q[k & 3]);
+        const T r = w[i] - ((q[0] + q[1]) + (q[2] + q[3]));
         w[i] = r;
 #pragma unroll
         for (int k = 0; k < KMAX; ++k)
@@ -351,6 +386,8 @@ __device__ void arnoldi_finish(KState* ks, const DevArgs* a, int j, int R, doubl
 }
 
 // K7b: w -= V_stored c2, stored as basis column j+1; ||w||^2; then K8.
+// Each thread handles two rows per iteration, each subtraction as two
+// interleaved partial sums, to keep several independent FMA chains in flight.
 template <class Sys, int KMAX>
 __global__ void __launch_bounds__(kStreamBlock, 1)
 arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* __restrict__ V,
@@ -368,16 +405,39 @@ arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T*
     int lo, hi;
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
     T part[1] = {0};
-    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        T vv[KMAX];
+    const int bd = blockDim.x;
+    int i = lo + threadIdx.x;
+    for (; i + bd < hi; i += 2 * bd) {
+        const int i2 = i + bd;
+        T a0 = 0, a1 = 0, b0 = 0, b1 = 0;
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k) vv[k] = k < nk ? V[(size_t)k * ldv + i] : (T)0;
-        T r = w[i];
+        for (int k = 0; k < KMAX; k += 2) {
+            if (k < nk) {
+                a0 = fma(V[(size_t)k * ldv + i], cf[k], a0);
+                b0 = fma(V[(size_t)k * ldv + i2], cf[k], b0);
+            }
+            if (k + 1 < nk) {
+                a1 = fma(V[(size_t)(k + 1) * ldv + i], cf[k + 1], a1);
+                b1 = fma(V[(size_t)(k + 1) * ldv + i2], cf[k + 1], b1);
+            }
+        }
+        const T ra = w[i] - (a0 + a1);
+        const T rb = w[i2] - (b0 + b1);
+        vout[i] = ra;
+        vout[i2] = rb;
+        part[0] = fma(ra, ra, part[0]);
+        part[0] = fma(rb, rb, part[0]);
+    }
+    for (; i < hi; i += bd) {
+        T a0 = 0, a1 = 0;
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < nk) r = fma(-vv[k], cf[k], r);
-        vout[i] = r;
-        part[0] = fma(r, r, part[0]);
+        for (int k = 0; k < KMAX; k += 2) {
+            if (k < nk) a0 = fma(V[(size_t)k * ldv + i], cf[k], a0);
+            if (k + 1 < nk) a1 = fma(V[(size_t)(k + 1) * ldv + i], cf[k + 1], a1);
+        }
+        const T ra = w[i] - (a0 + a1);
+        vout[i] = ra;
+        part[0] = fma(ra, ra, part[0]);
     }
     block_sum<T, 1>(part, 1, red, scratch);
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
@@ -421,6 +481,19 @@ static void launch_start(const DevArgs* a, KState* ks, typename Sys::T* V, typen
     gmres_start_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, partial, first);
 }
 
+template <class Sys>
+static size_t dot_smem() {
+    using T = typename Sys::T;
+    const size_t bytes = sizeof(T) * ((size_t)kDotWarps * kTile + kDotSmemRows);
+    static bool set = false;
+    if (!set) {
+        cudaFuncSetAttribute(arnoldi_dot_kernel<Sys>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+        set = true;
+    }
+    return bytes;
+}
+
 // Records ev[*k] (when timing events are supplied) and advances *k.
 static inline void mark(cudaEvent_t* ev, int* k, cudaStream_t st) {
     if (ev) cudaEventRecordWithFlags(ev[(*k)++], st, cudaEventRecordExternal);
@@ -430,7 +503,8 @@ template <class Sys, int KMAX>
 static void launch_step(const DevArgs* a, KState* ks, typename Sys::T* V, size_t ldv,
                         typename Sys::T* w, typename Sys::T* partial, int nblk, int j, int R,
                         cudaStream_t st, cudaEvent_t* ev, int* k) {
-    arnoldi_dot_kernel<Sys, KMAX><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j);
+    arnoldi_dot_kernel<Sys><<<nblk, kDotBlock, dot_smem<Sys>(), st>>>(a, ks, V, ldv, w, partial, j,
+                                                                      kMaxBasis);
     mark(ev, k, st);
     arnoldi_pass2_kernel<Sys, KMAX><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j);
     mark(ev, k, st);
@@ -454,6 +528,8 @@ static void launch_cycle(const DevArgs* a, KState* ks, typename Sys::T* V, size_
             launch_step<Sys, 8>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
         else if (nk <= 16)
             launch_step<Sys, 16>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
+        else if (nk <= 24)
+            launch_step<Sys, 24>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
         else if (nk <= 32)
             launch_step<Sys, 32>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
         else
