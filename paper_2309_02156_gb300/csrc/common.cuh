@@ -224,6 +224,105 @@ __device__ __forceinline__ Acc warp_tile_spmv(const int* __restrict__ rowptr,
     return acc;
 }
 
+// Software-pipelined warp tiles.  A tile's CSR row range is fetched one
+// stage ahead of its column/value loads, which are fetched one stage ahead of
+// the gathers and sums, so three tiles' loads are in flight per warp.
+struct TileRows {
+    int rs, re;     // this lane's row range, clamped to [0, nnz]
+    int e0, e1;     // the tile's entry range
+};
+
+__device__ __forceinline__ TileRows tile_rows(const int* __restrict__ rowptr, int n, int nnz,
+                                              int r0, int hi) {
+    const int lane = threadIdx.x & 31;
+    const int row = r0 + lane;
+    TileRows t;
+    t.rs = t.re = 0;
+    if (r0 < hi && row < n) {
+        t.rs = max(0, min(__ldg(rowptr + row), nnz));
+        t.re = max(t.rs, min(__ldg(rowptr + row + 1), nnz));
+    }
+    return t;
+}
+
+__device__ __forceinline__ void tile_span(TileRows& t, int n, int r0) {
+    const int last = max(0, min(31, n - 1 - r0));
+    t.e0 = __shfl_sync(0xffffffffu, t.rs, 0);
+    t.e1 = max(t.e0, __shfl_sync(0xffffffffu, t.re, last));
+}
+
+template <typename VT>
+struct TileData {
+    int cc[kTileChunks];
+    VT vv[kTileChunks];
+};
+
+template <typename VT>
+__device__ __forceinline__ void tile_load(const int* __restrict__ colind, const VT* __restrict__ val,
+                                          const TileRows& t, TileData<VT>& d) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < kTileChunks; ++q) {
+        const int e = t.e0 + q * 32 + lane;
+        d.cc[q] = e < t.e1 ? __ldg(colind + e) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < kTileChunks; ++q) {
+        const int e = t.e0 + q * 32 + lane;
+        d.vv[q] = e < t.e1 ? __ldg(val + e) : (VT)0;
+    }
+}
+
+// Gathers, products and per-row sums of a tile whose loads are in `d`; rows
+// with more than kTileChunks x 32 entries in the tile fall back to a chunked
+// loop over the CSR arrays.
+template <typename Acc, typename VT, typename XT>
+__device__ __forceinline__ Acc tile_finish(const int* __restrict__ colind,
+                                           const VT* __restrict__ val, const XT* __restrict__ x,
+                                           int n, const TileRows& t, const TileData<VT>& d,
+                                           Acc* sprod, int* bad) {
+    const int lane = threadIdx.x & 31;
+    Acc acc = 0;
+    int flag = 0;
+    if (t.e1 - t.e0 <= kTileChunks * 32) {
+#pragma unroll
+        for (int q = 0; q < kTileChunks; ++q) {
+            const int e = t.e0 + q * 32 + lane;
+            Acc prod = 0;
+            if (e < t.e1) {
+                if ((unsigned)d.cc[q] < (unsigned)n)
+                    prod = (Acc)d.vv[q] * (Acc)x[d.cc[q]];
+                else
+                    flag = 1;
+            }
+            sprod[q * 32 + lane] = prod;
+        }
+        __syncwarp();
+        const int lo = max(t.rs, t.e0), hi = min(t.re, t.e1);
+        for (int e = lo; e < hi; ++e) acc += sprod[e - t.e0];
+        __syncwarp();
+    } else {
+        for (int base = t.e0; base < t.e1; base += 32) {
+            const int e = base + lane;
+            Acc prod = 0;
+            if (e < t.e1) {
+                const int c = __ldg(colind + e);
+                if ((unsigned)c < (unsigned)n)
+                    prod = (Acc)__ldg(val + e) * (Acc)x[c];
+                else
+                    flag = 1;
+            }
+            sprod[lane] = prod;
+            __syncwarp();
+            const int lo = max(t.rs, base), hi = min(t.re, base + 32);
+            for (int k = lo; k < hi; ++k) acc += sprod[k - base];
+            __syncwarp();
+        }
+    }
+    if (flag) atomicOr(bad, 1);
+    return acc;
+}
+
 // Warp reduce-scatter of K <= 32 per-lane values: returns, in lane l, the
 // warp-wide sum of value (l % K).  Halves of the lane range are folded while
 // they exceed K, then a recursive-halving exchange leaves one value per lane

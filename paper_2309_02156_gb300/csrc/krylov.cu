@@ -182,10 +182,11 @@ __device__ __forceinline__ void block_columns(T (&part)[K], int nk, T* wsum /* k
         const T c = warp_reduce_scatter<T, K>(part);
         if (lane < K) wsum[warp * K + lane] = c;
     } else if constexpr (K < 32) {
-        T v[32];                                   // pad to the next power of two
+        constexpr int P = K <= 8 ? 8 : (K <= 16 ? 16 : 32);   // next power of two
+        T v[P];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = i < K ? part[i] : (T)0;
-        const T c = warp_reduce_scatter<T, 32>(v);
+        for (int i = 0; i < P; ++i) v[i] = i < K ? part[i] : (T)0;
+        const T c = warp_reduce_scatter<T, P>(v);
         if (lane < K) wsum[warp * K + lane] = c;
     } else {
         T lo[32], hi[32];
@@ -235,14 +236,30 @@ arnoldi_dot_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* _
     int lo, hi;
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
     const bool in_smem = (hi - lo) <= kDotSmemRows;
-    for (int r0 = lo + warp * 32; r0 < hi; r0 += kDotWarps * 32) {
-        const T ax = warp_tile_spmv<T>(a->rowptr, a->colind, Sys::val(a), vj, n, nnz, r0,
-                                       sprod + warp * kTile, &ks->bad_index);
-        const int row = r0 + lane;
-        if (row < hi) {
-            const T y = ax * sig;
-            w[row] = y;
-            if (in_smem) ws[row - lo] = y;
+    {
+        const int step = kDotWarps * 32;
+        const T* val = Sys::val(a);
+        int r0 = lo + warp * 32;
+        TileRows ta = tile_rows(a->rowptr, n, nnz, r0, hi);
+        TileRows tb = tile_rows(a->rowptr, n, nnz, r0 + step, hi);
+        TileData<T> da, db;
+        tile_span(ta, n, r0);
+        tile_load(a->colind, val, ta, da);
+        for (; r0 < hi; r0 += step) {
+            const TileRows tc = tile_rows(a->rowptr, n, nnz, r0 + 2 * step, hi);
+            tile_span(tb, n, r0 + step);
+            if (r0 + step < hi) tile_load(a->colind, val, tb, db);
+            const T ax = tile_finish<T>(a->colind, val, vj, n, ta, da, sprod + warp * kTile,
+                                        &ks->bad_index);
+            const int row = r0 + lane;
+            if (row < hi) {
+                const T y = ax * sig;
+                w[row] = y;
+                if (in_smem) ws[row - lo] = y;
+            }
+            ta = tb;
+            da = db;
+            tb = tc;
         }
     }
     __syncthreads();
@@ -324,64 +341,109 @@ arnoldi_pass2_kernel(const DevArgs* __restrict__ a, KState* ks,
     }
 }
 
-// Thread 0 of the last block of K7b: Hessenberg column, Givens, stopping test.
+// Last block of K7b, all threads: Hessenberg column j = h1 + h2 with
+// h_{j+1,j} = ||w||, the previous Givens rotations applied to it, the new
+// rotation, the residual estimate |g_{j+1}| and the end-of-cycle decision;
+// at the end of a cycle the triangular system R y = g is solved by warp 0
+// (column-oriented back substitution from shared memory) and sigma_k y_k
+// stored for the basis update.  Everything is staged in shared memory, so
+// thread 0's serial part touches no global memory.
 __device__ void arnoldi_finish(KState* ks, const DevArgs* a, int j, int R, double hn2) {
-    const double hn = sqrt(hn2);
-    const int nk = j + 1;
-    double* Hc = ks->H + (size_t)j * kMaxBasis;
-    double hh = 0.0;
-    for (int i = 0; i < nk; ++i) {
-        const double h = ks->h1[i] + ks->h2[i];
-        Hc[i] = h;
-        hh += h * h;
+    __shared__ double hc[kMaxBasis + 1];
+    __shared__ double cs_s[kMaxRestart], sn_s[kMaxRestart];
+    __shared__ double Hs[kMaxBasis * kMaxRestart];
+    __shared__ int end_cycle, k_s, ok_s;
+    const int tid = threadIdx.x, nk = j + 1;
+    for (int i = tid; i < nk; i += blockDim.x) hc[i] = ks->h1[i] + ks->h2[i];
+    for (int i = tid; i < j; i += blockDim.x) {
+        cs_s[i] = ks->cs[i];
+        sn_s[i] = ks->sn[i];
     }
-    Hc[j + 1] = hn;
-    for (int i = 0; i < j; ++i) {
-        const double t = ks->cs[i] * Hc[i] + ks->sn[i] * Hc[i + 1];
-        Hc[i + 1] = -ks->sn[i] * Hc[i] + ks->cs[i] * Hc[i + 1];
-        Hc[i] = t;
-    }
-    const double av = Hc[j], bv = Hc[j + 1];
-    const double rr = hypot(av, bv);
-    double c = 1.0, s = 0.0;
-    if (rr != 0.0) {
-        c = av / rr;
-        s = bv / rr;
-    }
-    ks->cs[j] = c;
-    ks->sn[j] = s;
-    Hc[j] = rr;
-    Hc[j + 1] = 0.0;
-    ks->g[j + 1] = -s * ks->g[j];
-    ks->g[j] = c * ks->g[j];
-    ks->iters += 1;
-    ks->sigma[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
-    const bool nonfinite = !isfinite(hn) || !isfinite(ks->g[j + 1]);
-    const bool happy = hn <= 1e-14 * sqrt(hh + hn * hn);
-    const bool conv = fabs(ks->g[j + 1]) <= ks->target;
-    if (nonfinite || happy || conv || ks->iters >= a->max_iters || j == R - 1) {
-        const int k = j + 1;
-        ks->cycle_over = 1;
-        ks->jdone = k;
-        for (int i = 0; i < kMaxBasis; ++i) ks->cy[i] = 0.0;
-        if (nonfinite) {
-            ks->status = ST_NONFINITE;
-            ks->finished = 1;
-            return;
+    __syncthreads();
+    if (tid == 0) {
+        const double hn = sqrt(hn2);
+        double hh = 0.0;
+        for (int i = 0; i < nk; ++i) hh += hc[i] * hc[i];
+        hc[j + 1] = hn;
+        for (int i = 0; i < j; ++i) {
+            const double t = cs_s[i] * hc[i] + sn_s[i] * hc[i + 1];
+            hc[i + 1] = -sn_s[i] * hc[i] + cs_s[i] * hc[i + 1];
+            hc[i] = t;
         }
-        for (int i = 0; i < k; ++i)
-            if (ks->H[(size_t)i * kMaxBasis + i] == 0.0) {
+        const double av = hc[j], bv = hc[j + 1];
+        const double rr = hypot(av, bv);
+        double c = 1.0, sv = 0.0;
+        if (rr != 0.0) {
+            c = av / rr;
+            sv = bv / rr;
+        }
+        ks->cs[j] = c;
+        ks->sn[j] = sv;
+        hc[j] = rr;
+        hc[j + 1] = 0.0;
+        const double gj = ks->g[j];
+        const double gj1 = -sv * gj;
+        ks->g[j + 1] = gj1;
+        ks->g[j] = c * gj;
+        ks->iters += 1;
+        ks->sigma[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+        const bool nonfinite = !isfinite(hn) || !isfinite(gj1);
+        const bool happy = hn <= 1e-14 * sqrt(hh + hn * hn);
+        const bool conv = fabs(gj1) <= ks->target;
+        const int e = nonfinite || happy || conv || ks->iters >= a->max_iters || j == R - 1;
+        end_cycle = e;
+        k_s = j + 1;
+        ok_s = 1;
+        if (e) {
+            ks->cycle_over = 1;
+            ks->jdone = j + 1;
+            if (nonfinite) {
+                ks->status = ST_NONFINITE;
+                ks->finished = 1;
+                ok_s = 0;
+            }
+        }
+    }
+    __syncthreads();
+    double* Hcol = ks->H + (size_t)j * kMaxBasis;
+    for (int i = tid; i <= j + 1; i += blockDim.x) Hcol[i] = hc[i];
+    if (!end_cycle) return;
+    const int k = k_s;
+    for (int i = tid; i < kMaxBasis; i += blockDim.x) ks->cy[i] = 0.0;
+    if (!ok_s) return;
+    // Upper triangle of H (columns 0..k-1; column j is the one just formed).
+    for (int idx = tid; idx < k * k; idx += blockDim.x) {
+        const int col = idx / k, row = idx - col * k;
+        Hs[col * kMaxBasis + row] = (col == j) ? hc[row] : ks->H[(size_t)col * kMaxBasis + row];
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const int lane = tid;
+        bool sing = false;
+        for (int i = lane; i < k; i += 32) sing |= (Hs[i * kMaxBasis + i] == 0.0);
+        sing = __any_sync(0xffffffffu, sing);
+        if (sing) {
+            if (lane == 0) {
                 ks->status = ST_BREAKDOWN;
                 ks->finished = 1;
-                return;
             }
-        double y[kMaxBasis];
-        for (int i = k - 1; i >= 0; --i) {
-            double acc = 0.0;
-            for (int l = i + 1; l < k; ++l) acc += ks->H[(size_t)l * kMaxBasis + i] * y[l];
-            y[i] = (ks->g[i] - acc) / ks->H[(size_t)i * kMaxBasis + i];
+            return;
         }
-        for (int i = 0; i < k; ++i) ks->cy[i] = ks->sigma[i] * y[i];
+        // Lane l owns rows l and l + 32; acc starts at g and loses H[row][i] y_i.
+        double acc0 = lane < k ? ks->g[lane] : 0.0;
+        double acc1 = lane + 32 < k ? ks->g[lane + 32] : 0.0;
+        double y0 = 0.0, y1 = 0.0;
+        for (int i = k - 1; i >= 0; --i) {
+            const double own = (i < 32) ? acc0 : acc1;
+            double yi = __shfl_sync(0xffffffffu, own, i & 31) / Hs[i * kMaxBasis + i];
+            if (lane == (i & 31)) {
+                if (i < 32) y0 = yi; else y1 = yi;
+            }
+            if (lane < i) acc0 -= Hs[i * kMaxBasis + lane] * yi;
+            if (lane + 32 < i) acc1 -= Hs[i * kMaxBasis + lane + 32] * yi;
+        }
+        if (lane < k) ks->cy[lane] = ks->sigma[lane] * y0;
+        if (lane + 32 < k) ks->cy[lane + 32] = ks->sigma[lane + 32] * y1;
     }
 }
 
@@ -444,10 +506,8 @@ arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T*
     if (last_block_arrive(&ks->counter[CNT_PASS3])) {
         __shared__ double tot[1];
         reduce_blocks(partial, gridDim.x, 1, 1, tot);
-        if (threadIdx.x == 0) {
-            arnoldi_finish(ks, a, j, R, tot[0]);
-            ks->counter[CNT_PASS3] = 0;
-        }
+        if (threadIdx.x == 0) ks->counter[CNT_PASS3] = 0;
+        arnoldi_finish(ks, a, j, R, tot[0]);
     }
 }
 
@@ -524,16 +584,17 @@ static void launch_cycle(const DevArgs* a, KState* ks, typename Sys::T* V, size_
     mark(ev, &k, st);
     for (int j = 0; j < R; ++j) {
         const int nk = j + 1;
-        if (nk <= 8)
-            launch_step<Sys, 8>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
-        else if (nk <= 16)
-            launch_step<Sys, 16>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
-        else if (nk <= 24)
-            launch_step<Sys, 24>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
-        else if (nk <= 32)
-            launch_step<Sys, 32>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
-        else
-            launch_step<Sys, 64>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
+        switch ((nk + 3) / 4) {
+            case 1: launch_step<Sys, 4>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
+            case 2: launch_step<Sys, 8>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
+            case 3: launch_step<Sys, 12>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
+            case 4: launch_step<Sys, 16>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
+            case 5: launch_step<Sys, 20>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
+            case 6: launch_step<Sys, 24>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
+            case 7: launch_step<Sys, 28>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
+            case 8: launch_step<Sys, 32>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
+            default: launch_step<Sys, 64>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
+        }
     }
     gmres_update_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv);
     mark(ev, &k, st);
