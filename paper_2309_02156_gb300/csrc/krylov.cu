@@ -264,20 +264,35 @@ arnoldi_dot_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* _
     }
     __syncthreads();
     const T* wsrc = in_smem ? ws - lo : w;
+    // Work items (column k, row segment g): nseg segments per column so that
+    // all warps have work even for small nk; partial sums per item are
+    // combined over segments in segment order.
+    __shared__ T segsum[kMaxBasis * kDotWarps];
     __shared__ T colsum[kMaxBasis];
-    for (int k = warp; k < nk; k += kDotWarps) {
+    const int nseg = max(1, kDotWarps / nk);
+    const int seglen = (((hi - lo) + nseg - 1) / nseg + 31) & ~31;
+    for (int item = warp; item < nk * nseg; item += kDotWarps) {
+        const int k = item / nseg, g = item - k * nseg;
+        const int s0 = lo + g * seglen, s1 = min(hi, s0 + seglen);
         const T* vk = V + (size_t)k * ldv;
-        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-        int i = lo + lane;
-        for (; i + 96 < hi; i += 128) {
-            s0 = fma(vk[i], wsrc[i], s0);
-            s1 = fma(vk[i + 32], wsrc[i + 32], s1);
-            s2 = fma(vk[i + 64], wsrc[i + 64], s2);
-            s3 = fma(vk[i + 96], wsrc[i + 96], s3);
+        T acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = 0;
+        int i = s0 + lane;
+        for (; i + 7 * 32 < s1; i += 8 * 32) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = fma(vk[i + u * 32], wsrc[i + u * 32], acc[u]);
         }
-        for (; i < hi; i += 32) s0 = fma(vk[i], wsrc[i], s0);
-        T t = warp_sum((s0 + s1) + (s2 + s3));
-        if (lane == 0) colsum[k] = t;
+        for (; i < s1; i += 32) acc[0] = fma(vk[i], wsrc[i], acc[0]);
+        const T t = warp_sum(((acc[0] + acc[1]) + (acc[2] + acc[3])) +
+                             ((acc[4] + acc[5]) + (acc[6] + acc[7])));
+        if (lane == 0) segsum[k * kDotWarps + g] = t;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        T t = segsum[k * kDotWarps];
+        for (int g = 1; g < nseg; ++g) t += segsum[k * kDotWarps + g];
+        colsum[k] = t;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < nk; k += blockDim.x) partial[(size_t)blockIdx.x * stride + k] = colsum[k];
@@ -314,19 +329,35 @@ arnoldi_pass2_kernel(const DevArgs* __restrict__ a, KState* ks,
     T part[KMAX];
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) part[k] = 0;
-    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        T vv[KMAX];
+    // ROWS rows per thread and iteration keep >= 16 loads in flight.
+    constexpr int ROWS = KMAX >= 16 ? 1 : (16 + KMAX - 1) / KMAX;
+    const int bd = blockDim.x;
+    for (int i0 = lo + threadIdx.x; i0 < hi; i0 += ROWS * bd) {
+        T vv[ROWS][KMAX];
+        T wr[ROWS];
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k) vv[k] = k < nk ? V[(size_t)k * ldv + i] : (T)0;
-        T q[4] = {0, 0, 0, 0};
+        for (int u = 0; u < ROWS; ++u) {
+            const int i = i0 + u * bd;
+            const bool ok = i < hi;
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < nk) q[k & 3] = fma(vv[k], cf[k], q[k & 3]);
-        const T r = w[i] - ((q[0] + q[1]) + (q[2] + q[3]));
-        w[i] = r;
+            for (int k = 0; k < KMAX; ++k) vv[u][k] = (ok && k < nk) ? V[(size_t)k * ldv + i] : (T)0;
+            wr[u] = ok ? w[i] : (T)0;
+        }
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            if (k < nk) part[k] = fma(vv[k], r, part[k]);
+        for (int u = 0; u < ROWS; ++u) {
+            const int i = i0 + u * bd;
+            T q[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < nk) q[k & 3] = fma(vv[u][k], cf[k], q[k & 3]);
+            const T r = wr[u] - ((q[0] + q[1]) + (q[2] + q[3]));
+            if (i < hi) {
+                w[i] = r;
+#pragma unroll
+                for (int k = 0; k < KMAX; ++k)
+                    if (k < nk) part[k] = fma(vv[u][k], r, part[k]);
+            }
+        }
     }
     block_columns<T, KMAX>(part, nk, wsum, partial + (size_t)blockIdx.x * KMAX);
     if (last_block_arrive(&ks->counter[CNT_PASS2])) {
@@ -468,38 +499,33 @@ arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T*
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
     T part[1] = {0};
     const int bd = blockDim.x;
-    int i = lo + threadIdx.x;
-    for (; i + bd < hi; i += 2 * bd) {
-        const int i2 = i + bd;
-        T a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+    // ROWS rows per thread and iteration keep >= 16 loads in flight; each
+    // subtraction runs as two interleaved partial sums.
+    constexpr int ROWS = KMAX >= 16 ? 2 : (16 + KMAX - 1) / KMAX;
+    for (int i0 = lo + threadIdx.x; i0 < hi; i0 += ROWS * bd) {
+        T s0[ROWS], s1[ROWS], wr[ROWS];
 #pragma unroll
-        for (int k = 0; k < KMAX; k += 2) {
-            if (k < nk) {
-                a0 = fma(V[(size_t)k * ldv + i], cf[k], a0);
-                b0 = fma(V[(size_t)k * ldv + i2], cf[k], b0);
+        for (int u = 0; u < ROWS; ++u) {
+            const int i = i0 + u * bd;
+            const bool ok = i < hi;
+            s0[u] = 0;
+            s1[u] = 0;
+#pragma unroll
+            for (int k = 0; k < KMAX; k += 2) {
+                if (ok && k < nk) s0[u] = fma(V[(size_t)k * ldv + i], cf[k], s0[u]);
+                if (ok && k + 1 < nk) s1[u] = fma(V[(size_t)(k + 1) * ldv + i], cf[k + 1], s1[u]);
             }
-            if (k + 1 < nk) {
-                a1 = fma(V[(size_t)(k + 1) * ldv + i], cf[k + 1], a1);
-                b1 = fma(V[(size_t)(k + 1) * ldv + i2], cf[k + 1], b1);
+            wr[u] = ok ? w[i] : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+            const int i = i0 + u * bd;
+            if (i < hi) {
+                const T r = wr[u] - (s0[u] + s1[u]);
+                vout[i] = r;
+                part[0] = fma(r, r, part[0]);
             }
         }
-        const T ra = w[i] - (a0 + a1);
-        const T rb = w[i2] - (b0 + b1);
-        vout[i] = ra;
-        vout[i2] = rb;
-        part[0] = fma(ra, ra, part[0]);
-        part[0] = fma(rb, rb, part[0]);
-    }
-    for (; i < hi; i += bd) {
-        T a0 = 0, a1 = 0;
-#pragma unroll
-        for (int k = 0; k < KMAX; k += 2) {
-            if (k < nk) a0 = fma(V[(size_t)k * ldv + i], cf[k], a0);
-            if (k + 1 < nk) a1 = fma(V[(size_t)(k + 1) * ldv + i], cf[k + 1], a1);
-        }
-        const T ra = w[i] - (a0 + a1);
-        vout[i] = ra;
-        part[0] = fma(ra, ra, part[0]);
     }
     block_sum<T, 1>(part, 1, red, scratch);
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
