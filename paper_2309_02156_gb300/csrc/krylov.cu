@@ -503,25 +503,23 @@ arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T*
     // subtraction runs as two interleaved partial sums.
     constexpr int ROWS = KMAX >= 16 ? 2 : (16 + KMAX - 1) / KMAX;
     for (int i0 = lo + threadIdx.x; i0 < hi; i0 += ROWS * bd) {
-        T s0[ROWS], s1[ROWS], wr[ROWS];
+        T s0[ROWS], s1[ROWS];
 #pragma unroll
-        for (int u = 0; u < ROWS; ++u) {
-            const int i = i0 + u * bd;
-            const bool ok = i < hi;
-            s0[u] = 0;
-            s1[u] = 0;
+        for (int u = 0; u < ROWS; ++u) s0[u] = s1[u] = 0;
 #pragma unroll
-            for (int k = 0; k < KMAX; k += 2) {
-                if (ok && k < nk) s0[u] = fma(V[(size_t)k * ldv + i], cf[k], s0[u]);
-                if (ok && k + 1 < nk) s1[u] = fma(V[(size_t)(k + 1) * ldv + i], cf[k + 1], s1[u]);
+        for (int k = 0; k < KMAX; k += 2) {
+#pragma unroll
+            for (int u = 0; u < ROWS; ++u) {
+                const int i = min(i0 + u * bd, hi - 1);
+                if (k < nk) s0[u] = fma(V[(size_t)k * ldv + i], cf[k], s0[u]);
+                if (k + 1 < nk) s1[u] = fma(V[(size_t)(k + 1) * ldv + i], cf[k + 1], s1[u]);
             }
-            wr[u] = ok ? w[i] : (T)0;
         }
 #pragma unroll
         for (int u = 0; u < ROWS; ++u) {
             const int i = i0 + u * bd;
             if (i < hi) {
-                const T r = wr[u] - (s0[u] + s1[u]);
+                const T r = w[i] - (s0[u] + s1[u]);
                 vout[i] = r;
                 part[0] = fma(r, r, part[0]);
             }
