@@ -19,6 +19,7 @@ constexpr int kMaxS = 128;        // sketch rows
 constexpr int kMaxZeta = 16;
 constexpr int kStreamBlock = 384; // threads per block of the streaming kernels (one block per SM)
 constexpr int kTileChunks = 8;    // CSR entries of a 32-row tile loaded up front: 8 x 32
+constexpr int kTileStage = 2 * kTileChunks * 32;   // shared staging per warp (values, x)
 
 // Device-side copy of the per-call arguments.  The CUDA graphs of a context
 // take a pointer to this struct, so one captured graph serves every call.
@@ -285,21 +286,26 @@ __device__ __forceinline__ Acc tile_finish(const int* __restrict__ colind,
     Acc acc = 0;
     int flag = 0;
     if (t.e1 - t.e0 <= kTileChunks * 32) {
+        // Stage (value, x[col]) pairs; the row's lane then forms its sum with
+        // one fused multiply-add per entry, in CSR order.
+        Acc* sval = sprod;
+        Acc* sx = sprod + kTileChunks * 32;
 #pragma unroll
         for (int q = 0; q < kTileChunks; ++q) {
             const int e = t.e0 + q * 32 + lane;
-            Acc prod = 0;
+            Acc xv = 0;
             if (e < t.e1) {
                 if ((unsigned)d.cc[q] < (unsigned)n)
-                    prod = (Acc)d.vv[q] * (Acc)x[d.cc[q]];
+                    xv = (Acc)x[d.cc[q]];
                 else
                     flag = 1;
             }
-            sprod[q * 32 + lane] = prod;
+            sval[q * 32 + lane] = (Acc)d.vv[q];
+            sx[q * 32 + lane] = xv;
         }
         __syncwarp();
         const int lo = max(t.rs, t.e0), hi = min(t.re, t.e1);
-        for (int e = lo; e < hi; ++e) acc += sprod[e - t.e0];
+        for (int e = lo; e < hi; ++e) acc = fma(sval[e - t.e0], sx[e - t.e0], acc);
         __syncwarp();
     } else {
         for (int base = t.e0; base < t.e1; base += 32) {

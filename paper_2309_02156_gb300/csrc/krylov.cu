@@ -52,14 +52,15 @@ int stream_grid(int n) {
 }
 
 constexpr int kWarps = kStreamBlock / 32;
-constexpr int kTile = kTileChunks * 32;
+constexpr int kTile = kTileStage;              // pipelined tiles: (value, x) staging
+constexpr int kTileP = kTileChunks * 32;       // single-stage tiles: product staging
 
 // ---------------------------------------------------------------------------
 // ||b - A x|| and ||b|| (FP64); x_override replaces a->x when not NULL.
 __global__ void __launch_bounds__(kStreamBlock, 1)
 residual_norm_kernel(const DevArgs* __restrict__ a, KState* ks, double* partial,
                      const double* x_override) {
-    __shared__ double sprod[kWarps * kTile];
+    __shared__ double sprod[kWarps * kTileP];
     __shared__ double scratch[kWarps * 2];
     __shared__ double red[2];
     const int n = a->n, nnz = a->nnz;
@@ -70,7 +71,7 @@ residual_norm_kernel(const DevArgs* __restrict__ a, KState* ks, double* partial,
     double acc[2] = {0.0, 0.0};
     for (int r0 = lo + warp * 32; r0 < hi; r0 += kWarps * 32) {
         const double ax = warp_tile_spmv<double>(a->rowptr, a->colind, a->val64, x, n, nnz, r0,
-                                                 sprod + warp * kTile, &ks->bad_index);
+                                                 sprod + warp * kTileP, &ks->bad_index);
         const int row = r0 + lane;
         if (row < n) {
             const double bi = a->b[row];
@@ -108,7 +109,7 @@ gmres_start_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* V
                    typename Sys::T* partial, int first) {
     using T = typename Sys::T;
     if (!first && ks->finished) return;
-    __shared__ T sprod[kWarps * kTile];
+    __shared__ T sprod[kWarps * kTileP];
     __shared__ T scratch[kWarps * 2];
     __shared__ T red[2];
     const int n = a->n, nnz = a->nnz;
@@ -123,7 +124,7 @@ gmres_start_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* V
         T ax = 0;
         if (!zero_x)
             ax = warp_tile_spmv<T>(a->rowptr, a->colind, Sys::val(a), x, n, nnz, r0,
-                                   sprod + warp * kTile, &ks->bad_index);
+                                   sprod + warp * kTileP, &ks->bad_index);
         const int row = r0 + lane;
         if (row < n) {
             const T bi = rhs[row];
@@ -308,61 +309,62 @@ arnoldi_dot_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* _
     }
 }
 
-// K7a: w -= V_stored c1; h2 = sigma_k (V_stored^T w)_k.  One row per thread;
-// the subtraction runs as four interleaved partial sums (independent FMA
-// chains), the dot partials accumulate per thread and are reduce-scattered
-// over the warp once at the end.
-template <class Sys, int KMAX>
+// K7a: w -= V_stored c1; h2 = sigma_k (V_stored^T w)_k.  NK (the number of
+// basis columns) is a compile-time constant, so the row loop issues exactly
+// 2 NK FP64 fused multiply-adds per row and no predicated-off ones (on this
+// GPU one warp-wide FP64 instruction occupies a sub-partition's FP64 unit for
+// many cycles, so the instruction count, not latency, bounds the kernel).
+// ROWS rows per thread and iteration keep >= 16 loads in flight; the dot
+// partials accumulate per thread and are reduce-scattered over the warp once.
+template <class Sys, int NK>
 __global__ void __launch_bounds__(kStreamBlock, 1)
 arnoldi_pass2_kernel(const DevArgs* __restrict__ a, KState* ks,
                      const typename Sys::T* __restrict__ V, size_t ldv,
                      typename Sys::T* __restrict__ w, typename Sys::T* partial, int j) {
     using T = typename Sys::T;
     if (ks->cycle_over) return;
-    __shared__ T cf[KMAX];
-    __shared__ T wsum[kWarps * KMAX];
-    const int n = a->n, nk = j + 1;
-    for (int k = threadIdx.x; k < KMAX; k += blockDim.x) cf[k] = k < nk ? (T)ks->c1[k] : (T)0;
+    __shared__ T cf[NK];
+    __shared__ T wsum[kWarps * NK];
+    const int n = a->n;
+    const int nk = NK;
+    for (int k = threadIdx.x; k < NK; k += blockDim.x) cf[k] = (T)ks->c1[k];
     __syncthreads();
     int lo, hi;
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
-    T part[KMAX];
+    T part[NK];
 #pragma unroll
-    for (int k = 0; k < KMAX; ++k) part[k] = 0;
-    // ROWS rows per thread and iteration keep >= 16 loads in flight.
-    constexpr int ROWS = KMAX >= 16 ? 1 : (16 + KMAX - 1) / KMAX;
+    for (int k = 0; k < NK; ++k) part[k] = 0;
+    constexpr int ROWS = NK >= 16 ? 1 : (16 + NK - 1) / NK;
     const int bd = blockDim.x;
     for (int i0 = lo + threadIdx.x; i0 < hi; i0 += ROWS * bd) {
-        T vv[ROWS][KMAX];
-        T wr[ROWS];
+        T vv[ROWS][NK];
+        T r[ROWS];
 #pragma unroll
         for (int u = 0; u < ROWS; ++u) {
-            const int i = i0 + u * bd;
-            const bool ok = i < hi;
+            const int i = min(i0 + u * bd, hi - 1);
 #pragma unroll
-            for (int k = 0; k < KMAX; ++k) vv[u][k] = (ok && k < nk) ? V[(size_t)k * ldv + i] : (T)0;
-            wr[u] = ok ? w[i] : (T)0;
+            for (int k = 0; k < NK; ++k) vv[u][k] = V[(size_t)k * ldv + i];
+            r[u] = w[i];
+        }
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+#pragma unroll
+            for (int k = 0; k < NK; ++k) r[u] = fma(-vv[u][k], cf[k], r[u]);
         }
 #pragma unroll
         for (int u = 0; u < ROWS; ++u) {
             const int i = i0 + u * bd;
-            T q[4] = {0, 0, 0, 0};
-#pragma unroll
-            for (int k = 0; k < KMAX; ++k)
-                if (k < nk) q[k & 3] = fma(vv[u][k], cf[k], q[k & 3]);
-            const T r = wr[u] - ((q[0] + q[1]) + (q[2] + q[3]));
             if (i < hi) {
-                w[i] = r;
+                w[i] = r[u];
 #pragma unroll
-                for (int k = 0; k < KMAX; ++k)
-                    if (k < nk) part[k] = fma(vv[u][k], r, part[k]);
+                for (int k = 0; k < NK; ++k) part[k] = fma(vv[u][k], r[u], part[k]);
             }
         }
     }
-    block_columns<T, KMAX>(part, nk, wsum, partial + (size_t)blockIdx.x * KMAX);
+    block_columns<T, NK>(part, nk, wsum, partial + (size_t)blockIdx.x * kMaxBasis);
     if (last_block_arrive(&ks->counter[CNT_PASS2])) {
-        __shared__ double tot[KMAX];
-        reduce_blocks(partial, gridDim.x, KMAX, nk, tot);
+        __shared__ double tot[NK];
+        reduce_blocks(partial, gridDim.x, kMaxBasis, nk, tot);
         for (int k = threadIdx.x; k < nk; k += blockDim.x) {
             const double hk = ks->sigma[k] * tot[k];
             ks->h2[k] = hk;
@@ -479,49 +481,48 @@ __device__ void arnoldi_finish(KState* ks, const DevArgs* a, int j, int R, doubl
 }
 
 // K7b: w -= V_stored c2, stored as basis column j+1; ||w||^2; then K8.
-// Each thread handles two rows per iteration, each subtraction as two
-// interleaved partial sums, to keep several independent FMA chains in flight.
-template <class Sys, int KMAX>
+// A runtime loop over the nk columns (exactly nk + 1 FP64 instructions per
+// row); four rows per thread and iteration keep loads in flight.
+template <class Sys>
 __global__ void __launch_bounds__(kStreamBlock, 1)
 arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* __restrict__ V,
                      size_t ldv, const typename Sys::T* __restrict__ w, typename Sys::T* partial,
                      int j, int R) {
     using T = typename Sys::T;
     if (ks->cycle_over) return;
-    __shared__ T cf[KMAX];
+    __shared__ T cf[kMaxBasis];
     __shared__ T scratch[kWarps];
     __shared__ T red[1];
     const int n = a->n, nk = j + 1;
-    for (int k = threadIdx.x; k < KMAX; k += blockDim.x) cf[k] = k < nk ? (T)ks->c2[k] : (T)0;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) cf[k] = (T)ks->c2[k];
     __syncthreads();
     T* vout = V + (size_t)(j + 1) * ldv;
     int lo, hi;
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
     T part[1] = {0};
     const int bd = blockDim.x;
-    // ROWS rows per thread and iteration keep >= 16 loads in flight; each
-    // subtraction runs as two interleaved partial sums.
-    constexpr int ROWS = KMAX >= 16 ? 2 : (16 + KMAX - 1) / KMAX;
+    constexpr int ROWS = 4;
     for (int i0 = lo + threadIdx.x; i0 < hi; i0 += ROWS * bd) {
-        T s0[ROWS], s1[ROWS];
+        int ii[ROWS];
+        T r[ROWS];
 #pragma unroll
-        for (int u = 0; u < ROWS; ++u) s0[u] = s1[u] = 0;
+        for (int u = 0; u < ROWS; ++u) {
+            ii[u] = min(i0 + u * bd, hi - 1);
+            r[u] = w[ii[u]];
+        }
+#pragma unroll 2
+        for (int k = 0; k < nk; ++k) {
+            const T c = cf[k];
+            const T* vk = V + (size_t)k * ldv;
 #pragma unroll
-        for (int k = 0; k < KMAX; k += 2) {
-#pragma unroll
-            for (int u = 0; u < ROWS; ++u) {
-                const int i = min(i0 + u * bd, hi - 1);
-                if (k < nk) s0[u] = fma(V[(size_t)k * ldv + i], cf[k], s0[u]);
-                if (k + 1 < nk) s1[u] = fma(V[(size_t)(k + 1) * ldv + i], cf[k + 1], s1[u]);
-            }
+            for (int u = 0; u < ROWS; ++u) r[u] = fma(-vk[ii[u]], c, r[u]);
         }
 #pragma unroll
         for (int u = 0; u < ROWS; ++u) {
             const int i = i0 + u * bd;
             if (i < hi) {
-                const T r = w[i] - (s0[u] + s1[u]);
-                vout[i] = r;
-                part[0] = fma(r, r, part[0]);
+                vout[i] = r[u];
+                part[0] = fma(r[u], r[u], part[0]);
             }
         }
     }
@@ -583,18 +584,35 @@ static inline void mark(cudaEvent_t* ev, int* k, cudaStream_t st) {
     if (ev) cudaEventRecordWithFlags(ev[(*k)++], st, cudaEventRecordExternal);
 }
 
-template <class Sys, int KMAX>
+template <class Sys, int NK>
 static void launch_step(const DevArgs* a, KState* ks, typename Sys::T* V, size_t ldv,
                         typename Sys::T* w, typename Sys::T* partial, int nblk, int j, int R,
                         cudaStream_t st, cudaEvent_t* ev, int* k) {
     arnoldi_dot_kernel<Sys><<<nblk, kDotBlock, dot_smem<Sys>(), st>>>(a, ks, V, ldv, w, partial, j,
                                                                       kMaxBasis);
     mark(ev, k, st);
-    arnoldi_pass2_kernel<Sys, KMAX><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j);
+    arnoldi_pass2_kernel<Sys, NK><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j);
     mark(ev, k, st);
-    arnoldi_pass3_kernel<Sys, KMAX><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j, R);
+    arnoldi_pass3_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j, R);
     mark(ev, k, st);
 }
+
+template <class Sys, int NK>
+struct StepTable {
+    static void launch(int nk, const DevArgs* a, KState* ks, typename Sys::T* V, size_t ldv,
+                       typename Sys::T* w, typename Sys::T* partial, int nblk, int j, int R,
+                       cudaStream_t st, cudaEvent_t* ev, int* k) {
+        if (nk == NK)
+            launch_step<Sys, NK>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, k);
+        else
+            StepTable<Sys, NK + 1>::launch(nk, a, ks, V, ldv, w, partial, nblk, j, R, st, ev, k);
+    }
+};
+template <class Sys>
+struct StepTable<Sys, kMaxRestart + 1> {
+    static void launch(int, const DevArgs*, KState*, typename Sys::T*, size_t, typename Sys::T*,
+                       typename Sys::T*, int, int, int, cudaStream_t, cudaEvent_t*, int*) {}
+};
 
 // One restart cycle.  With `ev` (3R + 3 timing events) an event is recorded
 // before the first kernel and after every kernel: kernel i of the cycle lies
@@ -606,20 +624,8 @@ static void launch_cycle(const DevArgs* a, KState* ks, typename Sys::T* V, size_
                          cudaStream_t st, int* launches, cudaEvent_t* ev) {
     int k = 0;
     mark(ev, &k, st);
-    for (int j = 0; j < R; ++j) {
-        const int nk = j + 1;
-        switch ((nk + 3) / 4) {
-            case 1: launch_step<Sys, 4>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
-            case 2: launch_step<Sys, 8>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
-            case 3: launch_step<Sys, 12>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
-            case 4: launch_step<Sys, 16>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
-            case 5: launch_step<Sys, 20>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
-            case 6: launch_step<Sys, 24>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
-            case 7: launch_step<Sys, 28>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
-            case 8: launch_step<Sys, 32>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
-            default: launch_step<Sys, 64>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k); break;
-        }
-    }
+    for (int j = 0; j < R; ++j)
+        StepTable<Sys, 1>::launch(j + 1, a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
     gmres_update_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv);
     mark(ev, &k, st);
     gmres_start_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, partial, 0);
@@ -650,7 +656,7 @@ void launch_gmres_cycle_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, 
 // Mixed precision: r = b - A64 x in FP64, beta = ||r||, rhs32 = (float) r.
 __global__ void __launch_bounds__(kStreamBlock, 1)
 refine_residual_kernel(const DevArgs* __restrict__ a, KState* ks, float* rhs32, double* partial) {
-    __shared__ double sprod[kWarps * kTile];
+    __shared__ double sprod[kWarps * kTileP];
     __shared__ double scratch[kWarps * 2];
     __shared__ double red[2];
     const int n = a->n, nnz = a->nnz;
@@ -660,7 +666,7 @@ refine_residual_kernel(const DevArgs* __restrict__ a, KState* ks, float* rhs32, 
     double acc[2] = {0.0, 0.0};
     for (int r0 = lo + warp * 32; r0 < hi; r0 += kWarps * 32) {
         const double ax = warp_tile_spmv<double>(a->rowptr, a->colind, a->val64, a->x, n, nnz, r0,
-                                                 sprod + warp * kTile, &ks->bad_index);
+                                                 sprod + warp * kTileP, &ks->bad_index);
         const int row = r0 + lane;
         if (row < n) {
             const double bi = a->b[row];
