@@ -56,7 +56,7 @@ class KernelStat(ctypes.Structure):
                 ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
-KERNEL_KINDS = ["spmv_dot", "cgs_pass2", "cgs_pass3", "update", "restart"]
+KERNEL_KINDS = ["spmv", "cgs_dot", "cgs_pass2", "cgs_pass3", "update", "restart"]
 
 _LIB = None
 

@@ -147,7 +147,7 @@ int capture_cycle(seq_ctx* ctx, bool prof) {
     cudaEvent_t* ev = nullptr;
     if (prof) {
         if (ctx->ev.empty()) {
-            ctx->ev.resize(3 * R + 3);
+            ctx->ev.resize(kKernelsPerStep * R + 3);
             for (auto& e : ctx->ev) CK(cudaEventCreate(&e));
         }
         ev = ctx->ev.data();
@@ -189,13 +189,15 @@ void add_stat(seq_ctx* ctx, int kind, int ev0, double bytes, double flops) {
 void account_cycle(seq_ctx* ctx, bool f32, int jd, bool updated, int nnz) {
     const double n = ctx->cfg.n, E = f32 ? 4.0 : 8.0, R = ctx->cfg.restart;
     const double csr = 4.0 * (n + 1) + (4.0 + E) * nnz;
+    const int S = kKernelsPerStep;
     for (int j = 0; j < jd; ++j) {
         const double nk = j + 1;
-        add_stat(ctx, SEQ_K_SPMV_DOT, 3 * j, csr + E * n * (j + 2), 2.0 * nnz + 2.0 * n * nk + n);
-        add_stat(ctx, SEQ_K_CGS_PASS2, 3 * j + 1, E * n * (nk + 2), 4.0 * n * nk);
-        add_stat(ctx, SEQ_K_CGS_PASS3, 3 * j + 2, E * n * (nk + 2), 2.0 * n * nk + 2.0 * n);
+        add_stat(ctx, SEQ_K_SPMV, S * j, csr + 2.0 * E * n, 2.0 * nnz + n);
+        add_stat(ctx, SEQ_K_CGS_DOT, S * j + 1, E * n * (nk + 1), 2.0 * n * nk);
+        add_stat(ctx, SEQ_K_CGS_PASS2, S * j + 2, E * n * (nk + 2), 4.0 * n * nk);
+        add_stat(ctx, SEQ_K_CGS_PASS3, S * j + 3, E * n * (nk + 2), 2.0 * n * nk + 2.0 * n);
     }
-    const int u = 3 * (int)R;
+    const int u = S * (int)R;
     if (updated) add_stat(ctx, SEQ_K_UPDATE, u, E * n * (jd + 2), 2.0 * n * jd);
     add_stat(ctx, SEQ_K_RESTART, u + 1, csr + 3.0 * E * n, 2.0 * nnz + 4.0 * n);
 }

@@ -17,6 +17,7 @@ constexpr int kMaxRestart = 64;
 constexpr int kMaxM = 31;         // history length (M + 1 <= 32 lanes in the sketch kernel)
 constexpr int kMaxS = 128;        // sketch rows
 constexpr int kMaxZeta = 16;
+constexpr int kKernelsPerStep = 4; // SpMV, first-pass dots, CGS pass 2, CGS pass 3
 constexpr int kStreamBlock = 384; // threads per block of the streaming kernels (one block per SM)
 constexpr int kTileChunks = 8;    // CSR entries of a 32-row tile loaded up front: 8 x 32
 constexpr int kTileStage = 2 * kTileChunks * 32;   // shared staging per warp (values, x)

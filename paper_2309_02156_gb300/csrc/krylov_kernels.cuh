@@ -1,0 +1,595 @@
+// Krylov kernel templates shared by the FP64 and FP32 translation units.
+//
+// Krylov solvers started from the subspace guess (Algorithm 1, step 4; the
+// paper uses GMRES for general matrices and names CG for SPD ones, Section 1).
+//
+// Restarted GMRES(R) with CGS2 Arnoldi.  One Arnoldi step j is four
+// streaming kernels over the n rows:
+//   K5a w = A v_j                 software-pipelined warp-tile CSR product
+//   K5b h1 = V_j^T w              column-segment dots over all warps
+//   K7a w -= V_j h1, h2 = V_j^T w fused: each basis element is read once
+//   K7b w -= V_j h2, v_{j+1} = w (unnormalised), ||w||^2; the last block then
+//       forms the Hessenberg column h1 + h2, applies the Givens rotations,
+//       updates the residual estimate and decides whether the cycle ends.
+// Reductions end in a deterministic last-block pass.  On this GPU a
+// warp-wide FP64 instruction occupies a sub-partition's FP64 unit for many
+// cycles, so the CGS kernels are specialised on the exact number of basis
+// columns and issue exactly the algorithmic count of FP64 operations.
+// Basis columns are stored unnormalised with sigma_k = 1/||.|| kept on the
+// device, so no extra pass rescales them.  A cycle (R steps, the basis update
+// x += V y and the true residual of the new iterate) is captured once as a
+// CUDA graph; kernels after the end of a cycle return at once.
+//
+// The same templates run the FP32 inner solve of mixed precision (system
+// A32 d = rhs32 from d = 0, FP32 vectors and FP32 dot accumulation; the
+// Hessenberg and rotations stay FP64).
+#pragma once
+
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sa {
+
+enum { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_BREAKDOWN = -4, ST_NONFINITE = -5 };
+enum { CNT_START = 0, CNT_DOT = 1, CNT_PASS2 = 2, CNT_PASS3 = 3, CNT_RES = 4, CNT_REFINE = 5 };
+
+struct SysF64 {
+    using T = double;
+    using V = double;
+    __device__ static const double* val(const DevArgs* a) { return a->val64; }
+    __device__ static const double* rhs(const DevArgs* a) { return a->b; }
+    __device__ static double* x(const DevArgs* a) { return a->x; }
+};
+struct SysF32 {
+    using T = float;
+    using V = float;
+    __device__ static const float* val(const DevArgs* a) { return a->val32; }
+    __device__ static const float* rhs(const DevArgs* a) { return a->rhs32; }
+    __device__ static float* x(const DevArgs* a) { return reinterpret_cast<float*>(a->d); }
+};
+
+constexpr int kWarps = kStreamBlock / 32;
+constexpr int kTile = kTileStage;              // pipelined tiles: (value, x) staging
+constexpr int kTileP = kTileChunks * 32;       // single-stage tiles: product staging
+
+// ---------------------------------------------------------------------------
+// Cycle start: r = rhs - A x written to basis column 0, beta = ||r||.  With
+// first != 0 the solve is initialised (||rhs||, target, iteration count; the
+// FP32 inner solve also zeroes d, so r = rhs).
+template <class Sys>
+__global__ void __launch_bounds__(kStreamBlock, 1)
+gmres_start_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* V,
+                   typename Sys::T* partial, int first) {
+    using T = typename Sys::T;
+    if (!first && ks->finished) return;
+    __shared__ T sprod[kWarps * kTileP];
+    __shared__ T scratch[kWarps * 2];
+    __shared__ T red[2];
+    const int n = a->n, nnz = a->nnz;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T* x = Sys::x(a);
+    const T* rhs = Sys::rhs(a);
+    const bool zero_x = first && (sizeof(T) == 4);
+    int lo, hi;
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    T acc[2] = {0, 0};
+    for (int r0 = lo + warp * 32; r0 < hi; r0 += kWarps * 32) {
+        T ax = 0;
+        if (!zero_x)
+            ax = warp_tile_spmv<T>(a->rowptr, a->colind, Sys::val(a), x, n, nnz, r0,
+                                   sprod + warp * kTileP, &ks->bad_index);
+        const int row = r0 + lane;
+        if (row < n) {
+            const T bi = rhs[row];
+            const T r = bi - ax;
+            V[row] = r;
+            if (zero_x) x[row] = 0;
+            acc[0] += r * r;
+            acc[1] += bi * bi;
+        }
+    }
+    block_sum<T, 2>(acc, 2, red, scratch);
+    if (threadIdx.x < 2) partial[blockIdx.x * 2 + threadIdx.x] = red[threadIdx.x];
+    if (last_block_arrive(&ks->counter[CNT_START])) {
+        __shared__ double tot[2];
+        reduce_blocks(partial, gridDim.x, 2, 2, tot);
+        if (threadIdx.x == 0) {
+            const double beta = sqrt(tot[0]);
+            if (first) {
+                ks->bnorm = sqrt(tot[1]);
+                ks->target = a->tol * ks->bnorm;
+                ks->iters = 0;
+                ks->status = ST_OK;
+                ks->first_relres = beta / ks->bnorm;
+            }
+            ks->last_jdone = first ? 0 : ks->jdone;
+            ks->beta = beta;
+            ks->g[0] = beta;
+            ks->sigma[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+            ks->jdone = 0;
+            ks->cycle_over = 0;
+            ks->finished = 0;
+            if (!isfinite(beta)) {
+                ks->status = ST_NONFINITE;
+                ks->finished = 1;
+            } else if (beta <= ks->target) {
+                ks->status = ST_OK;
+                ks->finished = 1;
+            } else if (ks->iters >= a->max_iters) {
+                ks->status = ST_NOT_CONVERGED;
+                ks->finished = 1;
+            }
+            if (ks->finished) ks->cycle_over = 1;
+            ks->counter[CNT_START] = 0;
+        }
+    }
+}
+
+// Lane l of every warp holds, for K <= 32, the warp partial of column l % K
+// after warp_reduce_scatter; the block partial of column k (k < nk) is the
+// sum over warps in warp order.  K = 64 is handled as two halves of 32.
+template <typename T, int K>
+__device__ __forceinline__ void block_columns(T (&part)[K], int nk, T* wsum /* kWarps * K */,
+                                              T* out /* global, K */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (K <= 32 && (K & (K - 1)) == 0) {
+        const T c = warp_reduce_scatter<T, K>(part);
+        if (lane < K) wsum[warp * K + lane] = c;
+    } else if constexpr (K < 32) {
+        constexpr int P = K <= 8 ? 8 : (K <= 16 ? 16 : 32);   // next power of two
+        T v[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) v[i] = i < K ? part[i] : (T)0;
+        const T c = warp_reduce_scatter<T, P>(v);
+        if (lane < K) wsum[warp * K + lane] = c;
+    } else {
+        T lo[32], hi[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            lo[i] = part[i];
+            hi[i] = part[32 + i];
+        }
+        const T cl = warp_reduce_scatter<T, 32>(lo);
+        const T ch = warp_reduce_scatter<T, 32>(hi);
+        wsum[warp * K + lane] = cl;
+        wsum[warp * K + 32 + lane] = ch;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        T s = wsum[k];
+        for (int w = 1; w < kWarps; ++w) s += wsum[w * K + k];
+        out[k] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5a: w = sigma_j A vstored_j.  Software-pipelined warp tiles (the row range
+// of tile k+2, the CSR loads of tile k+1 and the gathers of tile k in flight
+// together), no reduction, so the block can be large.
+constexpr int kSpmvBlock = 768;
+constexpr int kSpmvWarps = kSpmvBlock / 32;
+
+template <class Sys>
+__global__ void __launch_bounds__(kSpmvBlock, 1)
+arnoldi_spmv_kernel(const DevArgs* __restrict__ a, const KState* __restrict__ ks,
+                    const typename Sys::T* __restrict__ V, size_t ldv,
+                    typename Sys::T* __restrict__ w, int j) {
+    using T = typename Sys::T;
+    if (ks->cycle_over) return;
+    extern __shared__ unsigned char dsm[];
+    T* sprod = reinterpret_cast<T*>(dsm);                   // kSpmvWarps * kTile
+    const int n = a->n, nnz = a->nnz;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const T sig = (T)ks->sigma[j];
+    const T* vj = V + (size_t)j * ldv;
+    const T* val = Sys::val(a);
+    int lo, hi;
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    const int step = kSpmvWarps * 32;
+    int r0 = lo + warp * 32;
+    TileRows ta = tile_rows(a->rowptr, n, nnz, r0, hi);
+    TileRows tb = tile_rows(a->rowptr, n, nnz, r0 + step, hi);
+    TileData<T> da, db;
+    tile_span(ta, n, r0);
+    tile_load(a->colind, val, ta, da);
+    for (; r0 < hi; r0 += step) {
+        const TileRows tc = tile_rows(a->rowptr, n, nnz, r0 + 2 * step, hi);
+        tile_span(tb, n, r0 + step);
+        if (r0 + step < hi) tile_load(a->colind, val, tb, db);
+        const T ax = tile_finish<T>(a->colind, val, vj, n, ta, da, sprod + warp * kTile,
+                                    const_cast<int*>(&ks->bad_index));
+        const int row = r0 + lane;
+        if (row < hi) w[row] = ax * sig;
+        ta = tb;
+        da = db;
+        tb = tc;
+    }
+}
+
+// K5b: h1 = sigma_k (V_stored^T w)_k for k <= j.  Work items (column k, row
+// segment g) spread over all warps (nseg segments per column so that small
+// bases still use every warp); each lane keeps eight accumulators, combined
+// in a fixed order, then the warp butterfly; segments are summed in segment
+// order.
+constexpr int kDotBlock = 768;
+constexpr int kDotWarps = kDotBlock / 32;
+
+template <class Sys>
+__global__ void __launch_bounds__(kDotBlock, 1)
+arnoldi_dot_kernel(const DevArgs* __restrict__ a, KState* ks,
+                   const typename Sys::T* __restrict__ V, size_t ldv,
+                   const typename Sys::T* __restrict__ w, typename Sys::T* partial, int j,
+                   int stride) {
+    using T = typename Sys::T;
+    if (ks->cycle_over) return;
+    __shared__ T segsum[kMaxBasis * kDotWarps];
+    __shared__ T colsum[kMaxBasis];
+    const int n = a->n, nk = j + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int lo, hi;
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    const int nseg = max(1, kDotWarps / nk);
+    const int seglen = (((hi - lo) + nseg - 1) / nseg + 31) & ~31;
+    for (int item = warp; item < nk * nseg; item += kDotWarps) {
+        const int k = item / nseg, g = item - k * nseg;
+        const int s0 = lo + g * seglen, s1 = min(hi, s0 + seglen);
+        const T* vk = V + (size_t)k * ldv;
+        T acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = 0;
+        int i = s0 + lane;
+        for (; i + 7 * 32 < s1; i += 8 * 32) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = fma(vk[i + u * 32], w[i + u * 32], acc[u]);
+        }
+        for (; i < s1; i += 32) acc[0] = fma(vk[i], w[i], acc[0]);
+        const T t = warp_sum(((acc[0] + acc[1]) + (acc[2] + acc[3])) +
+                             ((acc[4] + acc[5]) + (acc[6] + acc[7])));
+        if (lane == 0) segsum[k * kDotWarps + g] = t;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        T t = segsum[k * kDotWarps];
+        for (int g = 1; g < nseg; ++g) t += segsum[k * kDotWarps + g];
+        colsum[k] = t;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) partial[(size_t)blockIdx.x * stride + k] = colsum[k];
+    if (last_block_arrive(&ks->counter[CNT_DOT])) {
+        __shared__ double tot[kMaxBasis];
+        reduce_blocks(partial, gridDim.x, stride, nk, tot);
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+            const double hk = ks->sigma[k] * tot[k];
+            ks->h1[k] = hk;
+            ks->c1[k] = ks->sigma[k] * hk;
+        }
+        if (threadIdx.x == 0) ks->counter[CNT_DOT] = 0;
+    }
+}
+
+// K7a: w -= V_stored c1; h2 = sigma_k (V_stored^T w)_k.  NK (the number of
+// basis columns) is a compile-time constant, so the row loop issues exactly
+// 2 NK FP64 fused multiply-adds per row and no predicated-off ones (on this
+// GPU one warp-wide FP64 instruction occupies a sub-partition's FP64 unit for
+// many cycles, so the instruction count, not latency, bounds the kernel).
+// ROWS rows per thread and iteration keep >= 16 loads in flight; the dot
+// partials accumulate per thread and are reduce-scattered over the warp once.
+template <class Sys, int NK>
+__global__ void __launch_bounds__(kStreamBlock, 1)
+arnoldi_pass2_kernel(const DevArgs* __restrict__ a, KState* ks,
+                     const typename Sys::T* __restrict__ V, size_t ldv,
+                     typename Sys::T* __restrict__ w, typename Sys::T* partial, int j) {
+    using T = typename Sys::T;
+    if (ks->cycle_over) return;
+    __shared__ T cf[NK];
+    __shared__ T wsum[kWarps * NK];
+    const int n = a->n;
+    const int nk = NK;
+    for (int k = threadIdx.x; k < NK; k += blockDim.x) cf[k] = (T)ks->c1[k];
+    __syncthreads();
+    int lo, hi;
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    T part[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) part[k] = 0;
+    constexpr int ROWS = NK >= 16 ? 1 : (16 + NK - 1) / NK;
+    const int bd = blockDim.x;
+    for (int i0 = lo + threadIdx.x; i0 < hi; i0 += ROWS * bd) {
+        T vv[ROWS][NK];
+        T r[ROWS];
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+            const int i = min(i0 + u * bd, hi - 1);
+#pragma unroll
+            for (int k = 0; k < NK; ++k) vv[u][k] = V[(size_t)k * ldv + i];
+            r[u] = w[i];
+        }
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+#pragma unroll
+            for (int k = 0; k < NK; ++k) r[u] = fma(-vv[u][k], cf[k], r[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+            const int i = i0 + u * bd;
+            if (i < hi) {
+                w[i] = r[u];
+#pragma unroll
+                for (int k = 0; k < NK; ++k) part[k] = fma(vv[u][k], r[u], part[k]);
+            }
+        }
+    }
+    block_columns<T, NK>(part, nk, wsum, partial + (size_t)blockIdx.x * kMaxBasis);
+    if (last_block_arrive(&ks->counter[CNT_PASS2])) {
+        __shared__ double tot[NK];
+        reduce_blocks(partial, gridDim.x, kMaxBasis, nk, tot);
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+            const double hk = ks->sigma[k] * tot[k];
+            ks->h2[k] = hk;
+            ks->c2[k] = ks->sigma[k] * hk;
+        }
+        if (threadIdx.x == 0) ks->counter[CNT_PASS2] = 0;
+    }
+}
+
+// Last block of K7b, all threads: Hessenberg column j = h1 + h2 with
+// h_{j+1,j} = ||w||, the previous Givens rotations applied to it, the new
+// rotation, the residual estimate |g_{j+1}| and the end-of-cycle decision;
+// at the end of a cycle the triangular system R y = g is solved by warp 0
+// (column-oriented back substitution from shared memory) and sigma_k y_k
+// stored for the basis update.  Everything is staged in shared memory, so
+// thread 0's serial part touches no global memory.
+__device__ inline void arnoldi_finish(KState* ks, const DevArgs* a, int j, int R, double hn2) {
+    __shared__ double hc[kMaxBasis + 1];
+    __shared__ double cs_s[kMaxRestart], sn_s[kMaxRestart];
+    __shared__ double Hs[kMaxBasis * kMaxRestart];
+    __shared__ int end_cycle, k_s, ok_s;
+    const int tid = threadIdx.x, nk = j + 1;
+    for (int i = tid; i < nk; i += blockDim.x) hc[i] = ks->h1[i] + ks->h2[i];
+    for (int i = tid; i < j; i += blockDim.x) {
+        cs_s[i] = ks->cs[i];
+        sn_s[i] = ks->sn[i];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double hn = sqrt(hn2);
+        double hh = 0.0;
+        for (int i = 0; i < nk; ++i) hh += hc[i] * hc[i];
+        hc[j + 1] = hn;
+        for (int i = 0; i < j; ++i) {
+            const double t = cs_s[i] * hc[i] + sn_s[i] * hc[i + 1];
+            hc[i + 1] = -sn_s[i] * hc[i] + cs_s[i] * hc[i + 1];
+            hc[i] = t;
+        }
+        const double av = hc[j], bv = hc[j + 1];
+        const double rr = hypot(av, bv);
+        double c = 1.0, sv = 0.0;
+        if (rr != 0.0) {
+            c = av / rr;
+            sv = bv / rr;
+        }
+        ks->cs[j] = c;
+        ks->sn[j] = sv;
+        hc[j] = rr;
+        hc[j + 1] = 0.0;
+        const double gj = ks->g[j];
+        const double gj1 = -sv * gj;
+        ks->g[j + 1] = gj1;
+        ks->g[j] = c * gj;
+        ks->iters += 1;
+        ks->sigma[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+        const bool nonfinite = !isfinite(hn) || !isfinite(gj1);
+        const bool happy = hn <= 1e-14 * sqrt(hh + hn * hn);
+        const bool conv = fabs(gj1) <= ks->target;
+        const int e = nonfinite || happy || conv || ks->iters >= a->max_iters || j == R - 1;
+        end_cycle = e;
+        k_s = j + 1;
+        ok_s = 1;
+        if (e) {
+            ks->cycle_over = 1;
+            ks->jdone = j + 1;
+            if (nonfinite) {
+                ks->status = ST_NONFINITE;
+                ks->finished = 1;
+                ok_s = 0;
+            }
+        }
+    }
+    __syncthreads();
+    double* Hcol = ks->H + (size_t)j * kMaxBasis;
+    for (int i = tid; i <= j + 1; i += blockDim.x) Hcol[i] = hc[i];
+    if (!end_cycle) return;
+    const int k = k_s;
+    for (int i = tid; i < kMaxBasis; i += blockDim.x) ks->cy[i] = 0.0;
+    if (!ok_s) return;
+    // Upper triangle of H (columns 0..k-1; column j is the one just formed).
+    for (int idx = tid; idx < k * k; idx += blockDim.x) {
+        const int col = idx / k, row = idx - col * k;
+        Hs[col * kMaxBasis + row] = (col == j) ? hc[row] : ks->H[(size_t)col * kMaxBasis + row];
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const int lane = tid;
+        bool sing = false;
+        for (int i = lane; i < k; i += 32) sing |= (Hs[i * kMaxBasis + i] == 0.0);
+        sing = __any_sync(0xffffffffu, sing);
+        if (sing) {
+            if (lane == 0) {
+                ks->status = ST_BREAKDOWN;
+                ks->finished = 1;
+            }
+            return;
+        }
+        // Lane l owns rows l and l + 32; acc starts at g and loses H[row][i] y_i.
+        double acc0 = lane < k ? ks->g[lane] : 0.0;
+        double acc1 = lane + 32 < k ? ks->g[lane + 32] : 0.0;
+        double y0 = 0.0, y1 = 0.0;
+        for (int i = k - 1; i >= 0; --i) {
+            const double own = (i < 32) ? acc0 : acc1;
+            double yi = __shfl_sync(0xffffffffu, own, i & 31) / Hs[i * kMaxBasis + i];
+            if (lane == (i & 31)) {
+                if (i < 32) y0 = yi; else y1 = yi;
+            }
+            if (lane < i) acc0 -= Hs[i * kMaxBasis + lane] * yi;
+            if (lane + 32 < i) acc1 -= Hs[i * kMaxBasis + lane + 32] * yi;
+        }
+        if (lane < k) ks->cy[lane] = ks->sigma[lane] * y0;
+        if (lane + 32 < k) ks->cy[lane + 32] = ks->sigma[lane + 32] * y1;
+    }
+}
+
+// K7b: w -= V_stored c2, stored as basis column j+1; ||w||^2; then K8.
+// NK is a compile-time constant: all column loads of ROWS rows are issued
+// before the nk + 1 FP64 fused multiply-adds per row.
+template <class Sys, int NK>
+__global__ void __launch_bounds__(kStreamBlock, 1)
+arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* __restrict__ V,
+                     size_t ldv, const typename Sys::T* __restrict__ w, typename Sys::T* partial,
+                     int j, int R) {
+    using T = typename Sys::T;
+    if (ks->cycle_over) return;
+    __shared__ T cf[NK];
+    __shared__ T scratch[kWarps];
+    __shared__ T red[1];
+    const int n = a->n;
+    for (int k = threadIdx.x; k < NK; k += blockDim.x) cf[k] = (T)ks->c2[k];
+    __syncthreads();
+    T* vout = V + (size_t)(j + 1) * ldv;
+    int lo, hi;
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    T part[1] = {0};
+    const int bd = blockDim.x;
+    constexpr int ROWS = NK >= 24 ? 2 : (NK >= 8 ? 4 : 8);
+    for (int i0 = lo + threadIdx.x; i0 < hi; i0 += ROWS * bd) {
+        T vv[ROWS][NK];
+        T r[ROWS];
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+            const int i = min(i0 + u * bd, hi - 1);
+#pragma unroll
+            for (int k = 0; k < NK; ++k) vv[u][k] = V[(size_t)k * ldv + i];
+            r[u] = w[i];
+        }
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+#pragma unroll
+            for (int k = 0; k < NK; ++k) r[u] = fma(-vv[u][k], cf[k], r[u]);
+            const int i = i0 + u * bd;
+            if (i < hi) {
+                vout[i] = r[u];
+                part[0] = fma(r[u], r[u], part[0]);
+            }
+        }
+    }
+    block_sum<T, 1>(part, 1, red, scratch);
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+    if (last_block_arrive(&ks->counter[CNT_PASS3])) {
+        __shared__ double tot[1];
+        reduce_blocks(partial, gridDim.x, 1, 1, tot);
+        if (threadIdx.x == 0) ks->counter[CNT_PASS3] = 0;
+        arnoldi_finish(ks, a, j, R, tot[0]);
+    }
+}
+
+// x += V_stored cy (the GMRES correction of the finished cycle).
+template <class Sys>
+__global__ void __launch_bounds__(kStreamBlock, 1)
+gmres_update_kernel(const DevArgs* __restrict__ a, const KState* ks,
+                    const typename Sys::T* __restrict__ V, size_t ldv) {
+    using T = typename Sys::T;
+    if (ks->status != ST_OK && ks->status != ST_NOT_CONVERGED) return;
+    if (ks->finished) return;
+    __shared__ T cy[kMaxBasis];
+    __shared__ int kk;
+    if (threadIdx.x == 0) kk = ks->jdone;
+    for (int k = threadIdx.x; k < kMaxBasis; k += blockDim.x) cy[k] = (T)ks->cy[k];
+    __syncthreads();
+    const int k = kk, n = a->n;
+    T* x = Sys::x(a);
+    int lo, hi;
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        T acc = 0;
+        for (int l = 0; l < k; ++l) acc = fma(V[(size_t)l * ldv + i], cy[l], acc);
+        x[i] += acc;
+    }
+}
+
+template <class Sys>
+static void launch_start(const DevArgs* a, KState* ks, typename Sys::T* V, typename Sys::T* partial,
+                         int nblk, int first, cudaStream_t st) {
+    gmres_start_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, partial, first);
+}
+
+template <class Sys>
+static size_t spmv_smem() {
+    using T = typename Sys::T;
+    const size_t bytes = sizeof(T) * (size_t)kSpmvWarps * kTile;
+    static bool set = false;
+    if (!set) {
+        cudaFuncSetAttribute(arnoldi_spmv_kernel<Sys>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+        set = true;
+    }
+    return bytes;
+}
+
+// Records ev[*k] (when timing events are supplied) and advances *k.
+inline void mark(cudaEvent_t* ev, int* k, cudaStream_t st) {
+    if (ev) cudaEventRecordWithFlags(ev[(*k)++], st, cudaEventRecordExternal);
+}
+
+template <class Sys, int NK>
+static void launch_step(const DevArgs* a, KState* ks, typename Sys::T* V, size_t ldv,
+                        typename Sys::T* w, typename Sys::T* partial, int nblk, int j, int R,
+                        cudaStream_t st, cudaEvent_t* ev, int* k) {
+    arnoldi_spmv_kernel<Sys><<<nblk, kSpmvBlock, spmv_smem<Sys>(), st>>>(a, ks, V, ldv, w, j);
+    mark(ev, k, st);
+    arnoldi_dot_kernel<Sys><<<nblk, kDotBlock, 0, st>>>(a, ks, V, ldv, w, partial, j, kMaxBasis);
+    mark(ev, k, st);
+    arnoldi_pass2_kernel<Sys, NK><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j);
+    mark(ev, k, st);
+    arnoldi_pass3_kernel<Sys, NK><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j, R);
+    mark(ev, k, st);
+}
+
+template <class Sys, int NK>
+struct StepTable {
+    static void launch(int nk, const DevArgs* a, KState* ks, typename Sys::T* V, size_t ldv,
+                       typename Sys::T* w, typename Sys::T* partial, int nblk, int j, int R,
+                       cudaStream_t st, cudaEvent_t* ev, int* k) {
+        if (nk == NK)
+            launch_step<Sys, NK>(a, ks, V, ldv, w, partial, nblk, j, R, st, ev, k);
+        else
+            StepTable<Sys, NK + 1>::launch(nk, a, ks, V, ldv, w, partial, nblk, j, R, st, ev, k);
+    }
+};
+template <class Sys>
+struct StepTable<Sys, kMaxRestart + 1> {
+    static void launch(int, const DevArgs*, KState*, typename Sys::T*, size_t, typename Sys::T*,
+                       typename Sys::T*, int, int, int, cudaStream_t, cudaEvent_t*, int*) {}
+};
+
+// One restart cycle.  With `ev` (kKernelsPerStep R + 3 timing events) an
+// event is recorded before the first kernel and after every kernel: kernel i
+// of the cycle lies between ev[i] and ev[i + 1] (i = 4j .. 4j+3 for Arnoldi
+// step j: SpMV, first-pass dots, pass 2, pass 3; 4R for the basis update;
+// 4R + 1 for the restart residual).
+template <class Sys>
+static void launch_cycle(const DevArgs* a, KState* ks, typename Sys::T* V, size_t ldv,
+                         typename Sys::T* w, typename Sys::T* partial, int nblk, int R,
+                         cudaStream_t st, int* launches, cudaEvent_t* ev) {
+    int k = 0;
+    mark(ev, &k, st);
+    for (int j = 0; j < R; ++j)
+        StepTable<Sys, 1>::launch(j + 1, a, ks, V, ldv, w, partial, nblk, j, R, st, ev, &k);
+    gmres_update_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv);
+    mark(ev, &k, st);
+    gmres_start_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, partial, 0);
+    mark(ev, &k, st);
+    if (launches) *launches = kKernelsPerStep * R + 2;
+}
+
+}  // namespace sa
