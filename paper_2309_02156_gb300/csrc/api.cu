@@ -51,6 +51,13 @@ struct seq_ctx {
     KState* ks = nullptr;            // outer / FP64 solve state
     KState* ks_in = nullptr;         // inner solve state
     KState* h_ks = nullptr;          // pinned mirror of the state tail
+    int* sell_width = nullptr;       // SELL-32 copy of A used by the GMRES cycles
+    int* sell_off = nullptr;
+    int* sell_col = nullptr;
+    void* sell_val = nullptr;
+    size_t sell_cap = 0;             // entries allocated
+    int* h_int = nullptr;            // pinned scratch word
+    bool sell_ok = false;
     cudaGraphExec_t cycle = nullptr;
     cudaGraphExec_t cycle_prof = nullptr;   // same cycle with timing events between kernels
     std::vector<cudaEvent_t> ev;
@@ -110,6 +117,9 @@ int set_args(seq_ctx* ctx, const seq_csr* A, const double* b, double* x, double 
     h->x = x;
     h->d = ctx->d;
     h->rhs32 = ctx->rhs32;
+    h->sell_off = ctx->sell_ok ? ctx->sell_off : nullptr;
+    h->sell_col = ctx->sell_ok ? ctx->sell_col : nullptr;
+    h->sell_val = ctx->sell_ok ? ctx->sell_val : nullptr;
     h->n = A->n;
     h->nnz = A->nnz;
     h->max_iters = max_iters;
@@ -135,6 +145,47 @@ int ensure_val32(seq_ctx* ctx, const seq_csr* A) {
     }
     launch_round_f32(A->values, ctx->val32, A->nnz, ctx->stream);
     ctx->launches += 1;
+    return SEQ_OK;
+}
+
+// SELL-32 copy of the matrix for the GMRES cycles (values in FP64, or the
+// FP32 copy in mixed precision).  Sized with one small synchronisation; kept
+// off (CSR is used) when padding would more than double the storage.
+int build_sell(seq_ctx* ctx, const seq_csr* A) {
+    ctx->sell_ok = false;
+    const int n = A->n, ns = (n + 31) / 32;
+    launch_sell_layout(A->rowptr, n, A->nnz, ctx->sell_width, ctx->sell_off, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->h_int, ctx->sell_off + ns, sizeof(int), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const long long total = *ctx->h_int;
+    if (total <= 0 || total >= 0x7fffffffLL || total > 2LL * A->nnz + 64LL * ns) return SEQ_OK;
+    const size_t el = ctx->mixed ? sizeof(float) : sizeof(double);
+    if ((size_t)total > ctx->sell_cap) {
+        if (ctx->sell_col) cudaFree(ctx->sell_col);
+        if (ctx->sell_val) cudaFree(ctx->sell_val);
+        ctx->sell_col = nullptr;
+        ctx->sell_val = nullptr;
+        ctx->sell_cap = 0;
+        if (cudaMalloc(&ctx->sell_col, sizeof(int) * (size_t)total) != cudaSuccess ||
+            cudaMalloc(&ctx->sell_val, el * (size_t)total) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, SEQ_ENOMEM, "cannot allocate the SELL-32 copy of A");
+        }
+        ctx->sell_cap = (size_t)total;
+    }
+    if (ctx->mixed) {
+        const float* v32 = A->values_f32 ? A->values_f32 : ctx->val32;
+        launch_sell_fill_f32(A->rowptr, A->colind, v32, n, A->nnz, ctx->sell_off, ctx->sell_col,
+                             (float*)ctx->sell_val, ctx->stream);
+    } else {
+        launch_sell_fill_f64(A->rowptr, A->colind, A->values, n, A->nnz, ctx->sell_off,
+                             ctx->sell_col, (double*)ctx->sell_val, ctx->stream);
+    }
+    ctx->launches += 3;
+    CK(cudaGetLastError());
+    ctx->sell_ok = true;
     return SEQ_OK;
 }
 
@@ -297,6 +348,12 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
         ok = ok && cudaMalloc(&ctx->rhs32, sizeof(float) * (size_t)n) == cudaSuccess;
         ok = ok && cudaMalloc(&ctx->d, sizeof(float) * (size_t)n) == cudaSuccess;
     }
+    if (c.krylov == SEQ_GMRES) {
+        const int ns = (n + 31) / 32;
+        ok = ok && cudaMalloc(&ctx->sell_width, sizeof(int) * (size_t)ns) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->sell_off, sizeof(int) * (size_t)(ns + 1)) == cudaSuccess;
+    }
+    ok = ok && cudaMallocHost(&ctx->h_int, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMalloc(&ctx->d_args, sizeof(DevArgs)) == cudaSuccess;
     ok = ok && cudaMallocHost(&ctx->h_args, sizeof(DevArgs)) == cudaSuccess;
     ok = ok && cudaMalloc(&ctx->d_args_in, sizeof(DevArgs)) == cudaSuccess;
@@ -327,10 +384,11 @@ int seq_destroy(seq_ctx* ctx) {
     for (auto e : ctx->ev) cudaEventDestroy(e);
     void* dev_ptrs[] = {ctx->X, ctx->sk, ctx->sk_partial, ctx->W, ctx->lsq, ctx->kpartial,
                         ctx->V, ctx->w, ctx->r, ctx->p, ctx->q, ctx->val32, ctx->rhs32, ctx->d,
-                        ctx->d_args, ctx->d_args_in, ctx->ks, ctx->ks_in};
+                        ctx->d_args, ctx->d_args_in, ctx->ks, ctx->ks_in, ctx->sell_width,
+                        ctx->sell_off, ctx->sell_col, ctx->sell_val};
     for (void* p : dev_ptrs)
         if (p) cudaFree(p);
-    void* host_ptrs[] = {ctx->lsq_host, ctx->h_args, ctx->h_args_in, ctx->h_ks};
+    void* host_ptrs[] = {ctx->lsq_host, ctx->h_args, ctx->h_args_in, ctx->h_ks, ctx->h_int};
     for (void* p : host_ptrs)
         if (p) cudaFreeHost(p);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
@@ -368,6 +426,7 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
     const int m = seq_history_size(ctx);
     int mode = c.guess;
     if (mode == SEQ_GUESS_LEARNED) mode = SEQ_GUESS_SKETCH;
+    ctx->sell_ok = false;            // the SELL copy belongs to the last seq_solve's matrix
     if (m == 0 && mode != SEQ_GUESS_ZERO) mode = SEQ_GUESS_ZERO;
     CK(cudaMemsetAsync(ctx->ks, 0, sizeof(KState), ctx->stream));
     int rank = 0;
@@ -455,6 +514,10 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
     CK(cudaMemsetAsync(ctx->ks_in, 0, sizeof(KState), ctx->stream));
     rc = ensure_val32(ctx, A);
     if (rc) return rc;
+    if (c.krylov == SEQ_GMRES) {
+        rc = build_sell(ctx, A);
+        if (rc) return rc;
+    }
     rc = set_args(ctx, A, b_dev, x_dev, tol, c.max_iters);
     if (rc) return rc;
     int status = SEQ_OK;

@@ -34,6 +34,9 @@ struct DevArgs {
                         // refinement iterate in mixed precision)
     void* d;            // inner correction vector (mixed precision, FP32)
     const float* rhs32; // inner right-hand side (mixed precision)
+    const int* sell_off;   // SELL-32 copy of the matrix used inside GMRES cycles
+    const int* sell_col;   // (slice offsets, column indices, values; NULL: use CSR)
+    const void* sell_val;
     int n;
     int nnz;
     int max_iters;

@@ -70,6 +70,12 @@ void launch_cg_block_f64(const DevArgs* a, KState* ks, double* r, double* p, dou
 void launch_cg_block_f32(const DevArgs* a, KState* ks, float* r, float* p, float* q,
                          cudaStream_t st);
 void launch_round_f32(const double* src, float* dst, int n, cudaStream_t st);
+// CSR -> SELL-32 (slice widths and offsets, then the padded arrays).
+void launch_sell_layout(const int* rowptr, int n, int nnz, int* width, int* off, cudaStream_t st);
+void launch_sell_fill_f64(const int* rowptr, const int* colind, const double* val, int n, int nnz,
+                          const int* off, int* col, double* v, cudaStream_t st);
+void launch_sell_fill_f32(const int* rowptr, const int* colind, const float* val, int n, int nnz,
+                          const int* off, int* col, float* v, cudaStream_t st);
 
 // probe.cu
 void launch_fp64_probe(double* out, int blocks, int threads, int iters, cudaStream_t st);

@@ -68,6 +68,102 @@ void launch_gmres_cycle_f64(const DevArgs* a, KState* ks, double* V, size_t ldv,
     launch_cycle<SysF64>(a, ks, V, ldv, w, partial, nblk, R, st, launches, ev);
 }
 // ---------------------------------------------------------------------------
+// CSR -> SELL-32 conversion (once per solve; the GMRES cycles then run ~10^3
+// products on the same matrix).  Slice s holds rows 32 s .. 32 s + 31; its
+// width is its longest row; entry k of row 32 s + l sits at
+// off[s] + 32 k + l.  Padding entries have column -1 and value 0.
+__global__ void sell_width_kernel(const int* __restrict__ rowptr, int n, int nnz, int* width) {
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int ns = (n + 31) >> 5;
+    if (s >= ns) return;
+    const int row = s * 32 + lane;
+    int len = 0;
+    if (row < n) {
+        const int rs = max(0, min(rowptr[row], nnz));
+        const int re = max(rs, min(rowptr[row + 1], nnz));
+        len = re - rs;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+    if (lane == 0) width[s] = len;
+}
+
+// Exclusive scan of 32 * width over the slices by one block (off[ns] = total).
+__global__ void sell_scan_kernel(const int* __restrict__ width, int ns, int* off) {
+    __shared__ long long wsum[32];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int base = 0; base < ns; base += blockDim.x) {
+        const int s = base + threadIdx.x;
+        long long v = s < ns ? 32LL * width[s] : 0;
+        long long incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        long long before = 0;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        const long long excl = carry + before + incl - v;
+        if (s < ns) off[s] = (int)min(excl, (long long)0x7fffffff);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long tot = 0;
+            for (int w = 0; w < nw; ++w) tot += wsum[w];
+            carry += tot;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) off[ns] = (int)min(carry, (long long)0x7fffffff);
+}
+
+template <typename VT>
+__global__ void sell_fill_kernel(const int* __restrict__ rowptr, const int* __restrict__ colind,
+                                 const VT* __restrict__ val, int n, int nnz,
+                                 const int* __restrict__ off, int* col_out, VT* val_out) {
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int ns = (n + 31) >> 5;
+    if (s >= ns) return;
+    const int o = off[s], w = (off[s + 1] - o) >> 5;
+    const int row = s * 32 + lane;
+    int rs = 0, re = 0;
+    if (row < n) {
+        rs = max(0, min(rowptr[row], nnz));
+        re = max(rs, min(rowptr[row + 1], nnz));
+    }
+    for (int k = 0; k < w; ++k) {
+        const int e = rs + k;
+        const bool ok = e < re;
+        col_out[o + k * 32 + lane] = ok ? colind[e] : -1;
+        val_out[o + k * 32 + lane] = ok ? val[e] : (VT)0;
+    }
+}
+
+void launch_sell_layout(const int* rowptr, int n, int nnz, int* width, int* off, cudaStream_t st) {
+    const int ns = (n + 31) / 32;
+    sell_width_kernel<<<(ns + 7) / 8, 256, 0, st>>>(rowptr, n, nnz, width);
+    sell_scan_kernel<<<1, 1024, 0, st>>>(width, ns, off);
+}
+
+void launch_sell_fill_f64(const int* rowptr, const int* colind, const double* val, int n, int nnz,
+                          const int* off, int* col, double* v, cudaStream_t st) {
+    const int ns = (n + 31) / 32;
+    sell_fill_kernel<double><<<(ns + 7) / 8, 256, 0, st>>>(rowptr, colind, val, n, nnz, off, col, v);
+}
+
+void launch_sell_fill_f32(const int* rowptr, const int* colind, const float* val, int n, int nnz,
+                          const int* off, int* col, float* v, cudaStream_t st) {
+    const int ns = (n + 31) / 32;
+    sell_fill_kernel<float><<<(ns + 7) / 8, 256, 0, st>>>(rowptr, colind, val, n, nnz, off, col, v);
+}
+
+// ---------------------------------------------------------------------------
 // Mixed precision: r = b - A64 x in FP64, beta = ||r||, rhs32 = (float) r.
 __global__ void __launch_bounds__(kStreamBlock, 1)
 refine_residual_kernel(const DevArgs* __restrict__ a, KState* ks, float* rhs32, double* partial) {

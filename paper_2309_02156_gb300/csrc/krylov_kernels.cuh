@@ -171,6 +171,51 @@ __device__ __forceinline__ void block_columns(T (&part)[K], int nk, T* wsum /* k
 constexpr int kSpmvBlock = 768;
 constexpr int kSpmvWarps = kSpmvBlock / 32;
 
+// SELL-32 product: warp per 32-row slice (lane = row), the slice's entries
+// stored column-major and padded to its widest row (padding has column -1).
+// All index and value loads of a slice are independent and coalesced, and
+// each row is summed in CSR order with one fused multiply-add per entry.
+// Two slices per warp and iteration keep more loads in flight.
+template <typename T>
+__device__ __forceinline__ void sell_spmv_rows(const int* __restrict__ off,
+                                               const int* __restrict__ col,
+                                               const T* __restrict__ val,
+                                               const T* __restrict__ x, int n, int lo, int hi,
+                                               T scale, T* __restrict__ y, int nwarps, int* bad) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s_lo = lo >> 5, s_hi = (hi + 31) >> 5;
+    int flag = 0;
+    for (int s = s_lo + warp; s < s_hi; s += 2 * nwarps) {
+        const int s2 = s + nwarps;
+        const bool two = s2 < s_hi;
+        const int o1 = __ldg(off + s), w1 = (__ldg(off + s + 1) - o1) >> 5;
+        const int o2 = two ? __ldg(off + s2) : 0;
+        const int w2 = two ? ((__ldg(off + s2 + 1) - o2) >> 5) : 0;
+        T a1 = 0, a2 = 0;
+        const int wm = max(w1, w2);
+        for (int k = 0; k < wm; ++k) {
+            if (k < w1) {
+                const int c = __ldg(col + o1 + k * 32 + lane);
+                if (c >= 0) {
+                    if (c < n) a1 = fma(__ldg(val + o1 + k * 32 + lane), x[c], a1);
+                    else flag = 1;
+                }
+            }
+            if (k < w2) {
+                const int c = __ldg(col + o2 + k * 32 + lane);
+                if (c >= 0) {
+                    if (c < n) a2 = fma(__ldg(val + o2 + k * 32 + lane), x[c], a2);
+                    else flag = 1;
+                }
+            }
+        }
+        const int r1 = s * 32 + lane, r2 = s2 * 32 + lane;
+        if (r1 < hi) y[r1] = a1 * scale;
+        if (two && r2 < hi) y[r2] = a2 * scale;
+    }
+    if (flag) atomicOr(bad, 1);
+}
+
 template <class Sys>
 __global__ void __launch_bounds__(kSpmvBlock, 1)
 arnoldi_spmv_kernel(const DevArgs* __restrict__ a, const KState* __restrict__ ks,
@@ -187,6 +232,11 @@ arnoldi_spmv_kernel(const DevArgs* __restrict__ a, const KState* __restrict__ ks
     const T* val = Sys::val(a);
     int lo, hi;
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    if (a->sell_off) {
+        sell_spmv_rows<T>(a->sell_off, a->sell_col, reinterpret_cast<const T*>(a->sell_val), vj, n,
+                          lo, hi, sig, w, kSpmvWarps, const_cast<int*>(&ks->bad_index));
+        return;
+    }
     const int step = kSpmvWarps * 32;
     int r0 = lo + warp * 32;
     TileRows ta = tile_rows(a->rowptr, n, nnz, r0, hi);
