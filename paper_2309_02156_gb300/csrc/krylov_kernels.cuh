@@ -173,9 +173,47 @@ constexpr int kSpmvWarps = kSpmvBlock / 32;
 
 // SELL-32 product: warp per 32-row slice (lane = row), the slice's entries
 // stored column-major and padded to its widest row (padding has column -1).
-// All index and value loads of a slice are independent and coalesced, and
-// each row is summed in CSR order with one fused multiply-add per entry.
-// Two slices per warp and iteration keep more loads in flight.
+// Two slices per warp and iteration: all index and value loads of both are
+// issued first (coalesced, independent), then all gathers, then each row is
+// summed in CSR order with exactly one fused multiply-add per stored entry
+// (the FMA chain is unrolled for the slice's exact width, so padding costs
+// no FP64 instruction).  Slices wider than kSellW use a plain loop.
+constexpr int kSellW = 6;
+
+template <typename T, int W>
+__device__ __forceinline__ T sell_dot(const T (&v)[kSellW], const T (&xv)[kSellW]) {
+    T a = 0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) a = fma(v[k], xv[k], a);
+    return a;
+}
+
+template <typename T>
+__device__ __forceinline__ T sell_dot_w(int w, const T (&v)[kSellW], const T (&xv)[kSellW]) {
+    switch (w) {
+        case 1: return sell_dot<T, 1>(v, xv);
+        case 2: return sell_dot<T, 2>(v, xv);
+        case 3: return sell_dot<T, 3>(v, xv);
+        case 4: return sell_dot<T, 4>(v, xv);
+        case 5: return sell_dot<T, 5>(v, xv);
+        case 6: return sell_dot<T, 6>(v, xv);
+        default: return (T)0;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T sell_row_loop(const int* __restrict__ col, const T* __restrict__ val,
+                                           const T* __restrict__ x, int n, int o, int w, int& flag) {
+    const int lane = threadIdx.x & 31;
+    T a = 0;
+    for (int k = 0; k < w; ++k) {
+        const int c = __ldg(col + o + k * 32 + lane);
+        if ((unsigned)c < (unsigned)n) a = fma(__ldg(val + o + k * 32 + lane), x[c], a);
+        else if (c >= 0) flag = 1;
+    }
+    return a;
+}
+
 template <typename T>
 __device__ __forceinline__ void sell_spmv_rows(const int* __restrict__ off,
                                                const int* __restrict__ col,
@@ -191,23 +229,31 @@ __device__ __forceinline__ void sell_spmv_rows(const int* __restrict__ off,
         const int o1 = __ldg(off + s), w1 = (__ldg(off + s + 1) - o1) >> 5;
         const int o2 = two ? __ldg(off + s2) : 0;
         const int w2 = two ? ((__ldg(off + s2 + 1) - o2) >> 5) : 0;
-        T a1 = 0, a2 = 0;
-        const int wm = max(w1, w2);
-        for (int k = 0; k < wm; ++k) {
-            if (k < w1) {
-                const int c = __ldg(col + o1 + k * 32 + lane);
-                if (c >= 0) {
-                    if (c < n) a1 = fma(__ldg(val + o1 + k * 32 + lane), x[c], a1);
-                    else flag = 1;
-                }
+        T a1, a2 = 0;
+        if (w1 <= kSellW && w2 <= kSellW) {
+            int c1[kSellW], c2[kSellW];
+            T v1[kSellW], v2[kSellW], x1[kSellW], x2[kSellW];
+#pragma unroll
+            for (int k = 0; k < kSellW; ++k) {
+                c1[k] = k < w1 ? __ldg(col + o1 + k * 32 + lane) : -1;
+                c2[k] = k < w2 ? __ldg(col + o2 + k * 32 + lane) : -1;
             }
-            if (k < w2) {
-                const int c = __ldg(col + o2 + k * 32 + lane);
-                if (c >= 0) {
-                    if (c < n) a2 = fma(__ldg(val + o2 + k * 32 + lane), x[c], a2);
-                    else flag = 1;
-                }
+#pragma unroll
+            for (int k = 0; k < kSellW; ++k) {
+                v1[k] = k < w1 ? __ldg(val + o1 + k * 32 + lane) : (T)0;
+                v2[k] = k < w2 ? __ldg(val + o2 + k * 32 + lane) : (T)0;
             }
+#pragma unroll
+            for (int k = 0; k < kSellW; ++k) {
+                x1[k] = (unsigned)c1[k] < (unsigned)n ? x[c1[k]] : (T)0;
+                x2[k] = (unsigned)c2[k] < (unsigned)n ? x[c2[k]] : (T)0;
+                if (c1[k] >= n || c2[k] >= n) flag = 1;
+            }
+            a1 = sell_dot_w<T>(w1, v1, x1);
+            if (two) a2 = sell_dot_w<T>(w2, v2, x2);
+        } else {
+            a1 = sell_row_loop<T>(col, val, x, n, o1, w1, flag);
+            if (two) a2 = sell_row_loop<T>(col, val, x, n, o2, w2, flag);
         }
         const int r1 = s * 32 + lane, r2 = s2 * 32 + lane;
         if (r1 < hi) y[r1] = a1 * scale;
