@@ -197,6 +197,32 @@ int seq_kernel_stats(seq_ctx* ctx, seq_kernel_stat* out, int reset);
  * arithmetic roof of the FP64 kernels.  Synchronises. */
 int seq_probe_fp64_peak(void* cuda_stream, double* tflops);
 
+/* The sketched block W = S [A X | b] computed without allocating any device
+ * memory.  The paper has no counterpart: this is a deployment variant of the
+ * sketch step for callers that cannot call cudaMalloc where they need W --
+ * code recorded into a CUDA graph by stream capture (allocation is not
+ * capturable), host callbacks and real-time loops that must not block in the
+ * allocator, and hosts that fix the library's memory budget up front.
+ *
+ * Inputs (device): CSR A (n rows, nnz entries), X (n x M, row i at
+ * X[i * ldx .. i * ldx + M - 1], column k is the k-th history vector), b (n).
+ * Output (device): W_dev, s x (M + 1) row-major, column k < M = S A X[:, k],
+ * column M = S b, with the same sparse-sign S (n, s, zeta, seed) as the rest
+ * of the library (entries +-1/sqrt(zeta)).
+ * Limits: s * (M + 1) <= 4096, M <= 31, zeta <= min(s, 16); larger sizes
+ * return SEQ_EINVAL before any GPU work.  Column indices outside [0, n) give
+ * SEQ_EINVAL after the call.
+ * Scratch: a fixed device array of about 5 MB defined in the library, held by
+ * every GPU that loads the library until the process exits.  All calls share
+ * it and it keeps the last call's contents; calls that overlap on the GPU
+ * race on it.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture.  Synchronises cuda_stream before returning. */
+int seq_sketch_block_noalloc(int32_t n, int32_t nnz, const int32_t* rowptr, const int32_t* colind,
+                             const double* values, const double* X, int32_t ldx, int32_t M,
+                             const double* b, int32_t s, int32_t zeta, uint64_t seed,
+                             double* W_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

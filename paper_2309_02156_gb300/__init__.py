@@ -12,7 +12,7 @@ reduced least-squares problem row-sketched by a sparse-sign S, followed by
 CG or GMRES from that guess.
 """
 from ._binding import (CSR, Sequence, SeqError, lib_path, load, probe_fp64_peak,
-                       sketch_columns, STATUS)
+                       sketch_block_noalloc, sketch_columns, STATUS)
 
 __all__ = ["CSR", "Sequence", "SeqError", "lib_path", "load", "probe_fp64_peak",
-           "sketch_columns", "STATUS"]
+           "sketch_block_noalloc", "sketch_columns", "STATUS"]

@@ -76,6 +76,11 @@ _SIGS = {
                                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p]),
     "seq_probe_fp64_peak": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "seq_sketch_block_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                                ctypes.c_void_p, ctypes.c_void_p]),
     "seq_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "seq_kernel_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
 }
@@ -238,3 +243,23 @@ def probe_fp64_peak() -> float:
     if rc != 0:
         raise SeqError(rc, "seq_probe_fp64_peak failed")
     return out.value
+
+
+def sketch_block_noalloc(A: CSR, X: torch.Tensor, b: torch.Tensor, s: int, zeta: int, seed: int,
+                         W: torch.Tensor) -> None:
+    """W <- S [A X | b] into the caller's (s, M+1) float64 tensor, without any
+    allocation inside the library (seq_sketch_block_noalloc).  X is (n, M)
+    float64, row-major, each column one history vector."""
+    lib = load()
+    n, M = X.shape
+    if W.shape != (s, M + 1):
+        raise ValueError(f"W must have shape ({s}, {M + 1})")
+    rc = lib.seq_sketch_block_noalloc(n, A.nnz, _ptr(A.rowptr, torch.int32, n + 1),
+                                      _ptr(A.colind, torch.int32, A.nnz),
+                                      _ptr(A.values, torch.float64, A.nnz),
+                                      _ptr(X, torch.float64, n * M), X.stride(0), M,
+                                      _ptr(b, torch.float64, n), s, zeta, seed,
+                                      _ptr(W, torch.float64, s * (M + 1)),
+                                      ctypes.c_void_p(_stream()))
+    if rc != 0:
+        raise SeqError(rc, "seq_sketch_block_noalloc failed")
