@@ -54,9 +54,11 @@ typedef enum {
 } seq_status;
 
 typedef enum {
-    SEQ_F64 = 0,      /* FP64 everywhere                                                */
-    SEQ_MIXED = 1     /* FP32 values, history, sketch and inner Krylov; FP64 QR,
-                         refinement residual b - A x and convergence test             */
+    SEQ_F64 = 0,          /* FP64 everywhere                                            */
+    SEQ_MIXED = 1,        /* FP32 values, history, sketch and inner Krylov; FP64 QR,
+                             refinement residual b - A x and convergence test         */
+    SEQ_MIXED_KRYLOV = 2  /* FP64 history, sketch, QR and guess; FP32 inner Krylov
+                             inside FP64 iterative refinement                         */
 } seq_precision;
 
 typedef enum {
@@ -74,8 +76,9 @@ typedef struct {
     const int32_t* rowptr;     /* device, n+1, rowptr[0] = 0, non-decreasing      */
     const int32_t* colind;     /* device, nnz                                     */
     const double* values;      /* device, nnz, FP64                               */
-    const float* values_f32;   /* device, nnz, FP32 copy used by SEQ_MIXED inner
-                                  solves; NULL: the library rounds `values`        */
+    const float* values_f32;   /* device, nnz, FP32 copy used by the FP32 inner
+                                  solves (and the FP32 sketch of SEQ_MIXED); NULL:
+                                  the library rounds `values`                      */
 } seq_csr;
 
 typedef struct {
@@ -89,16 +92,16 @@ typedef struct {
     int32_t krylov;       /* seq_krylov                                            */
     int32_t restart;      /* GMRES restart length, 1..64                           */
     int32_t max_iters;    /* Krylov iteration cap per solve (inner iterations in
-                             SEQ_MIXED)                                            */
-    double inner_tol;     /* SEQ_MIXED: floor of the inner relative tolerance;
+                             the mixed modes)                                      */
+    double inner_tol;     /* mixed modes: floor of the inner relative tolerance;
                              0 selects 1e-2                                        */
-    double rank_tol;      /* QR truncation tau; 0 selects 1e-12 (SEQ_F64) or 1e-5
-                             (SEQ_MIXED)                                           */
+    double rank_tol;      /* QR truncation tau; 0 selects 1e-12 for an FP64 sketch
+                             or 1e-5 for an FP32 sketch (SEQ_MIXED)                */
 } seq_config;
 
 typedef struct {
-    int32_t iters;          /* Krylov iterations (inner iterations summed in SEQ_MIXED) */
-    int32_t refinements;    /* FP64 refinement steps (SEQ_MIXED)                       */
+    int32_t iters;          /* Krylov iterations (inner iterations summed, mixed modes) */
+    int32_t refinements;    /* FP64 refinement steps (mixed modes)                      */
     int32_t history_cols;   /* history columns the guess used                          */
     int32_t rank;           /* columns kept by the pivoted QR                           */
     double guess_relres;    /* ||b - A x0|| / ||b|| of the starting vector              */

@@ -112,3 +112,32 @@ def solve_step(A, b, hist: History, S, tol: float, krylov_kind: str,
     return {"x": x, "x0": x0, "guess_relres": r0, "iters": it, "relres": rel,
             "status": st, "rank": g.rank if g else 0, "rho_s": g.rho_s if g else 0.0,
             "y": g.y if g else None}
+
+
+def sketched_guess_mixed(A32, b, X32: np.ndarray, S, tau: float = RANK_TOL_F32) -> Guess:
+    """Mixed-precision guess: W = S [A32 X32 | b] formed in float32 arithmetic
+    (float32 products and sums), the reduced least squares in FP64, and
+    x0 = X32 y accumulated in FP64 (the history is stored in float32)."""
+    n, m = X32.shape
+    if m == 0:
+        return Guess(np.zeros(n), np.zeros(0), np.zeros((S.shape[0], 1)), 0,
+                     float(np.linalg.norm(S @ b)))
+    S32 = S.astype(np.float32)
+    Y = np.column_stack([A32 @ X32, b.astype(np.float32)])
+    W = np.asarray(S32 @ Y).astype(np.float64)
+    y, rank, rho, _, _ = lsq.pivoted_qr_lstsq(W[:, :m], W[:, m], tau)
+    return Guess(X32.astype(np.float64) @ y, y, W, rank, rho)
+
+
+def solve_step_mixed(A64, A32, b, hist: History, S, tol: float, krylov_kind: str,
+                     restart: int = 30, max_iters: int = 30000, inner_tol: float = 1e-2):
+    """One system in mixed precision: float32 history, float32 sketch, FP64
+    least squares and FP64 refinement around float32 inner solves."""
+    X32 = hist.matrix().astype(np.float32)
+    g = sketched_guess_mixed(A32, b, X32, S)
+    r0 = relres(A64, b, g.x0)
+    x, it, nref, rel, st = krylov.mixed_refine(A64, A32, b, g.x0, tol, krylov_kind, restart,
+                                               max_iters, inner_tol=inner_tol)
+    hist.push(x.astype(np.float32).astype(np.float64))
+    return {"x": x, "x0": g.x0, "guess_relres": r0, "iters": it, "refinements": nref,
+            "relres": rel, "status": st, "rank": g.rank, "rho_s": g.rho_s, "y": g.y}

@@ -14,7 +14,7 @@ from . import build as _build
 STATUS = {0: "SEQ_OK", 1: "SEQ_NOT_CONVERGED", 2: "SEQ_FALLBACK_USED", -1: "SEQ_EINVAL",
           -2: "SEQ_ENOMEM", -3: "SEQ_ECUDA", -4: "SEQ_EBREAKDOWN", -5: "SEQ_ENONFINITE",
           -6: "SEQ_ETIMEOUT"}
-PRECISION = {"f64": 0, "mixed": 1}
+PRECISION = {"f64": 0, "mixed": 1, "mixed_krylov": 2}
 GUESS = {"zero": 0, "prev": 1, "sketch": 2, "learned": 3}
 KRYLOV = {"cg": 0, "gmres": 1}
 

@@ -22,7 +22,8 @@ struct seq_ctx {
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;      // private stream used only for graph capture
     int dev = 0;
-    bool mixed = false;
+    bool mixed = false;              // FP32 inner Krylov inside FP64 refinement
+    bool hist32 = false;             // FP32 history and sketch (SEQ_MIXED)
     int ldx = 0;
     void* X = nullptr;               // history ring, n x ldx (double or float)
     int pushes = 0;
@@ -309,7 +310,7 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
     const seq_config& c = *cfg;
     if (c.n <= 0 || c.M < 1 || c.M > kMaxM || c.s < c.M + 1 || c.s > kMaxS || c.zeta < 1 ||
         c.zeta > c.s || c.zeta > kMaxZeta || c.restart < 1 || c.restart > kMaxRestart ||
-        c.max_iters < 0 || (c.precision != SEQ_F64 && c.precision != SEQ_MIXED) ||
+        c.max_iters < 0 || (c.precision < SEQ_F64 || c.precision > SEQ_MIXED_KRYLOV) ||
         c.guess < SEQ_GUESS_ZERO || c.guess > SEQ_GUESS_LEARNED ||
         (c.krylov != SEQ_CG && c.krylov != SEQ_GMRES))
         return SEQ_EINVAL;
@@ -318,18 +319,20 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
     ctx->cfg = c;
     if (ctx->cfg.inner_tol <= 0) ctx->cfg.inner_tol = 1e-2;
     if (ctx->cfg.rank_tol <= 0) ctx->cfg.rank_tol = c.precision == SEQ_MIXED ? 1e-5 : 1e-12;
-    ctx->mixed = c.precision == SEQ_MIXED;
+    ctx->mixed = c.precision != SEQ_F64;
+    ctx->hist32 = c.precision == SEQ_MIXED;
     ctx->stream = (cudaStream_t)cuda_stream;
     const int n = c.n, M = c.M, s = c.s;
-    const size_t el = ctx->mixed ? sizeof(float) : sizeof(double);
-    ctx->ldx = ctx->mixed ? round_up(M, 8) : round_up(M, 4);
+    const size_t el = ctx->mixed ? sizeof(float) : sizeof(double);     // Krylov vectors
+    const size_t elh = ctx->hist32 ? sizeof(float) : sizeof(double);  // history and sketch
+    ctx->ldx = ctx->hist32 ? round_up(M, 8) : round_up(M, 4);
     bool ok = cudaGetDevice(&ctx->dev) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) == cudaSuccess;
-    ok = ok && cudaMalloc(&ctx->X, el * (size_t)n * ctx->ldx) == cudaSuccess;
-    ok = ok && cudaMemsetAsync(ctx->X, 0, el * (size_t)n * ctx->ldx, ctx->stream) == cudaSuccess;
+    ok = ok && cudaMalloc(&ctx->X, elh * (size_t)n * ctx->ldx) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(ctx->X, 0, elh * (size_t)n * ctx->ldx, ctx->stream) == cudaSuccess;
     ok = ok && cudaMalloc(&ctx->sk, sizeof(uint16_t) * (size_t)n * c.zeta) == cudaSuccess;
     ctx->sk_nblk = sketch_grid(n);
-    ok = ok && cudaMalloc(&ctx->sk_partial, el * (size_t)ctx->sk_nblk * (s * (M + 1) + 1)) == cudaSuccess;
+    ok = ok && cudaMalloc(&ctx->sk_partial, elh * (size_t)ctx->sk_nblk * (s * (M + 1) + 1)) == cudaSuccess;
     ok = ok && cudaMalloc(&ctx->W, sizeof(double) * (s * (M + 1) + 1)) == cudaSuccess;
     ok = ok && cudaMalloc(&ctx->lsq, sizeof(LsqOut)) == cudaSuccess;
     ok = ok && cudaMallocHost(&ctx->lsq_host, sizeof(LsqOut)) == cudaSuccess;
@@ -399,7 +402,7 @@ int seq_destroy(seq_ctx* ctx) {
 int seq_push_solution(seq_ctx* ctx, const double* x_dev) {
     if (!ctx || !x_dev) return fail(ctx, SEQ_EINVAL, "NULL argument");
     const int slot = ctx->pushes % ctx->cfg.M;
-    if (ctx->mixed)
+    if (ctx->hist32)
         launch_push_f32(x_dev, ctx->cfg.n, (float*)ctx->X, ctx->ldx, slot, ctx->stream);
     else
         launch_push_f64(x_dev, ctx->cfg.n, (double*)ctx->X, ctx->ldx, slot, ctx->stream);
@@ -435,14 +438,14 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
         CK(cudaMemsetAsync(x0_dev, 0, sizeof(double) * (size_t)n, ctx->stream));
     } else if (mode == SEQ_GUESS_PREV) {
         const int slot = (ctx->pushes - 1) % M;
-        if (ctx->mixed)
+        if (ctx->hist32)
             launch_copy_slot_f32((const float*)ctx->X, ctx->ldx, n, slot, x0_dev, ctx->stream);
         else
             launch_copy_slot_f64((const double*)ctx->X, ctx->ldx, n, slot, x0_dev, ctx->stream);
         ctx->launches += 1;
     } else {
         int* bad = &ctx->ks->bad_index;
-        if (ctx->mixed) {
+        if (ctx->hist32) {
             rc = ensure_val32(ctx, A);
             if (rc) return rc;
             const float* v32 = A->values_f32 ? A->values_f32 : ctx->val32;
@@ -456,7 +459,7 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
         }
         const int oldest = (ctx->pushes - m) % M;
         launch_lsq(ctx->W, c.s, M, m, oldest, c.rank_tol, ctx->lsq, ctx->stream);
-        if (ctx->mixed)
+        if (ctx->hist32)
             launch_expand_f32((const float*)ctx->X, ctx->ldx, n, M, ctx->lsq, x0_dev, ctx->stream);
         else
             launch_expand_f64((const double*)ctx->X, ctx->ldx, n, M, ctx->lsq, x0_dev, ctx->stream);

@@ -1,0 +1,111 @@
+"""Mixed precision on the GPU against the oracle.
+
+SEQ_MIXED_KRYLOV: FP64 history, sketch and guess; FP32 inner Krylov inside
+FP64 iterative refinement.  SEQ_MIXED: also the history and the sketch in
+FP32 (the least squares stays FP64).  Both must reach the FP64 tolerance on
+the true residual; inner iteration counts follow the oracle's float32
+emulation loosely (float32 rounding order differs between the two), and the
+number of refinement steps agrees within one.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import krylov, method, sketch
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_02156_gb300 as sa
+    sa.load()
+
+
+def _dev(rowptr, colind, vals, b):
+    import paper_2309_02156_gb300 as sa
+    A = sa.CSR(torch.from_numpy(rowptr).to(DEV), torch.from_numpy(colind).to(DEV),
+               torch.from_numpy(vals).to(DEV))
+    return A, torch.from_numpy(b).to(DEV)
+
+
+def _t(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(DEV)
+
+
+@pytest.mark.parametrize("kind,N,tol", [("gmres", 48, 1e-8), ("gmres", 33, 1e-10), ("cg", 40, 1e-10)])
+def test_mixed_krylov_from_oracle_history(kind, N, tol):
+    import paper_2309_02156_gb300 as sa
+    p = workloads.plain_nonsym(N) if kind == "gmres" else workloads.plain_spd(N)
+    M, s = 10, 40
+    S = sketch.sparse_sign_matrix(p.n, s, 8, 99)
+    hist = method.History(p.n, M)
+    seq = sa.Sequence(p.n, M, s, seed=99, precision="mixed_krylov", krylov=kind,
+                      max_iters=60000)
+    for i in range(M + 3):
+        rowptr, colind, vals, b = workloads.csr_system(p, i)
+        A = krylov.csr(rowptr, colind, vals, p.n)
+        g = method.sketched_guess(A, b, hist.matrix(), S)
+        x_ref, it_ref, nref_ref, rel_ref, st_ref = krylov.mixed_refine(
+            A, A.astype(np.float32), b, g.x0, tol, kind, 30, 60000)
+        Ad, bd = _dev(rowptr, colind, vals, b)
+        x = torch.empty(p.n, dtype=torch.float64, device=DEV)
+        gi = seq.guess(Ad, bd, x)
+        assert gi["guess_relres"] == pytest.approx(method.relres(A, b, g.x0), rel=1e-3, abs=1e-14)
+        info = seq.solve(Ad, bd, tol, x)
+        assert info["status"] == 0 and st_ref == 0
+        assert method.relres(A, b, x.cpu().numpy()) <= tol * (1 + 1e-9)
+        assert abs(info["refinements"] - nref_ref) <= 1
+        assert info["iters"] <= 1.5 * it_ref + 10 and it_ref <= 1.5 * info["iters"] + 10
+        hist.push(x_ref)
+        seq.push(_t(x_ref))
+    seq.close()
+
+
+def test_mixed_fp32_history_sketch_and_refinement():
+    import paper_2309_02156_gb300 as sa
+    p = workloads.plain_nonsym(40)
+    M, s = 12, 48
+    rng = np.random.default_rng(3)
+    cols = [rng.standard_normal(p.n) for _ in range(M)]
+    rowptr, colind, vals, b = workloads.csr_system(p, 6)
+    A = krylov.csr(rowptr, colind, vals, p.n)
+    seq = sa.Sequence(p.n, M, s, seed=5, precision="mixed", krylov="gmres", max_iters=60000)
+    for c in cols:
+        seq.push(_t(c))
+    Ad, bd = _dev(rowptr, colind, vals, b)
+    x = torch.empty(p.n, dtype=torch.float64, device=DEV)
+    seq.guess(Ad, bd, x)
+    W, _ = seq.last_sketch()
+    W = W[: s * (M + 1)].reshape(s, M + 1)
+    S = sketch.sparse_sign_matrix(p.n, s, 8, 5)
+    X32 = np.stack(cols, axis=1).astype(np.float32)
+    ref = method.sketched_guess_mixed(A.astype(np.float32), b, X32, S)
+    # float32 sums of ~n zeta / s terms in different orders.
+    assert np.all(np.abs(W - ref.W) <= 2e-5 * np.linalg.norm(ref.W, axis=0))
+    info = seq.solve(Ad, bd, 1e-10, x)
+    assert info["status"] == 0 and info["refinements"] >= 1
+    assert method.relres(A, b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-9)
+    seq.close()
+
+
+def test_mixed_sequence_reaches_tolerance_every_step():
+    """A short mixed sequence run end to end on the GPU (its own history)."""
+    import paper_2309_02156_gb300 as sa
+    p = workloads.plain_nonsym(64)
+    seq = sa.Sequence(p.n, 20, 80, precision="mixed", krylov="gmres", max_iters=60000)
+    for i in range(8):
+        rowptr, colind, vals, b = workloads.csr_system(p, i)
+        A = krylov.csr(rowptr, colind, vals, p.n)
+        Ad, bd = _dev(rowptr, colind, vals, b)
+        x = torch.empty(p.n, dtype=torch.float64, device=DEV)
+        seq.guess(Ad, bd, x)
+        info = seq.solve(Ad, bd, 1e-10, x)
+        assert info["status"] == 0
+        assert method.relres(A, b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-9)
+        seq.push(x)
+    seq.close()
