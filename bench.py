@@ -110,11 +110,13 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def profile_traffic(kind):
-    """Per-launch DRAM traffic of `kind` from the committed ncu summary, if it was
-    taken on the current kernel source (null otherwise)."""
+def profile_traffic(kind, algorithmic_bytes):
+    """Per-launch DRAM traffic of `kind`: the DRAM/algorithmic byte ratio that the
+    committed ncu summary measured (one full-set capture at Arnoldi step 15)
+    times this launch's algorithmic bytes; null when the summary was taken on
+    a different kernel source."""
     path = os.path.join(ROOT, "profiles", "arnoldi_kernels_nonsym1024.txt")
-    src = os.path.join(ROOT, "paper_2309_02156_gb300", "csrc", "krylov.cu")
+    src = os.path.join(ROOT, "paper_2309_02156_gb300", "csrc", "krylov_kernels.cuh")
     if not os.path.exists(path):
         return None
     digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -122,11 +124,11 @@ def profile_traffic(kind):
     for line in open(path):
         if line.startswith("source_sha256_16:"):
             vals["sha"] = line.split(":", 1)[1].strip()
-        if line.startswith(f"traffic_bytes_per_launch[{kind}]:"):
-            vals["traffic"] = float(line.split(":", 1)[1].split()[0])
-    if vals.get("sha") != digest:
+        if line.startswith(f"traffic_ratio[{kind}]:"):
+            vals["ratio"] = float(line.split(":", 1)[1].split()[0])
+    if vals.get("sha") != digest or "ratio" not in vals:
         return None
-    return vals.get("traffic")
+    return vals["ratio"] * algorithmic_bytes
 
 
 def cpu_baseline_worker(iters_per_system: float, gmres_iters: int) -> None:
@@ -365,7 +367,7 @@ def main():
         roof = {"bound": "hbm", "achieved": bytes_l / t_launch / 1e9, "peak": hbm_peak,
                 "unit": "GB/s", "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = profile_traffic(dom)
+    roof["traffic"] = profile_traffic(dom, bytes_l)
     roof["kernel"] = dom
     roof["algorithmic_bytes_per_launch"] = bytes_l
     roof["algorithmic_flops_per_launch"] = flops_l

@@ -241,10 +241,14 @@ void add_stat(seq_ctx* ctx, int kind, int ev0, double bytes, double flops) {
 void account_cycle(seq_ctx* ctx, bool f32, int jd, bool updated, int nnz) {
     const double n = ctx->cfg.n, E = f32 ? 4.0 : 8.0, R = ctx->cfg.restart;
     const double csr = 4.0 * (n + 1) + (4.0 + E) * nnz;
+    // The cycle's products read the SELL-32 copy when it exists (padded index
+    // and value arrays plus the slice offsets), the CSR arrays otherwise.
+    const double ns = (ctx->cfg.n + 31) / 32;
+    const double spmv_mat = ctx->sell_ok ? 4.0 * (ns + 1) + (4.0 + E) * (double)*ctx->h_int : csr;
     const int S = kKernelsPerStep;
     for (int j = 0; j < jd; ++j) {
         const double nk = j + 1;
-        add_stat(ctx, SEQ_K_SPMV, S * j, csr + 2.0 * E * n, 2.0 * nnz + n);
+        add_stat(ctx, SEQ_K_SPMV, S * j, spmv_mat + 2.0 * E * n, 2.0 * nnz + n);
         add_stat(ctx, SEQ_K_CGS_DOT, S * j + 1, E * n * (nk + 1), 2.0 * n * nk);
         add_stat(ctx, SEQ_K_CGS_PASS2, S * j + 2, E * n * (nk + 2), 4.0 * n * nk);
         add_stat(ctx, SEQ_K_CGS_PASS3, S * j + 3, E * n * (nk + 2), 2.0 * n * nk + 2.0 * n);
