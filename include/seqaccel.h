@@ -200,6 +200,53 @@ int seq_kernel_stats(seq_ctx* ctx, seq_kernel_stat* out, int reset);
  * arithmetic roof of the FP64 kernels.  Synchronises. */
 int seq_probe_fp64_peak(void* cuda_stream, double* tflops);
 
+/* ---- Batched form: many independent sequences, one persistent launch per step ----
+ *
+ * Each sequence k has its own history (M columns, FP64), sketch (seed + k)
+ * and fixed sparsity pattern; every step, for every sequence: the sketched
+ * guess (Algorithm 1, steps 1-3), then FP64 iterative refinement around FP32
+ * CG (the sequences are SPD) to ||b - A x|| <= tol ||b|| (step 4), then the
+ * push.  One thread block processes one sequence at a time, taking sequences
+ * from a device queue; the step is a single kernel launch captured in a CUDA
+ * graph.  Limits: M <= 16, s <= 64, zeta <= min(s, 16). */
+typedef struct seq_batch seq_batch;
+
+/* patterns (host array of count seq_csr; device rowptr/colind, values ignored)
+ * stay borrowed for the life of the batch.  Allocates per sequence the
+ * history (n x M FP64), an FP32 copy of the values and four FP32 vectors.
+ * The default schedule is 512 threads, one block per SM, largest first. */
+int seq_batch_create(int32_t count, const seq_csr* patterns, int32_t M, int32_t s, int32_t zeta,
+                     uint64_t seed, int32_t max_iters, double inner_tol, void* cuda_stream,
+                     seq_batch** out);
+int seq_batch_destroy(seq_batch* batch);
+
+/* One time step.  values, b, x: host arrays of count device pointers (the
+ * step's matrix values in the pattern's CSR order, right-hand side, solution
+ * output).  infos (host array of count, or NULL) receives per-sequence
+ * results.  Returns the worst status.  Synchronises the stream. */
+int seq_batch_step(seq_batch* batch, const double* const* values, const double* const* b,
+                   double* const* x, double tol, seq_info* infos);
+
+/* Autotuner: times one non-committing step (no history update) for every
+ * schedule (threads per block 256/512/1024, one or two blocks per SM,
+ * largest-first or given queue order) on these inputs and keeps the fastest;
+ * chosen (3 ints, may be NULL) receives it. */
+int seq_batch_autotune(seq_batch* batch, const double* const* values, const double* const* b,
+                       double* const* x, double tol, int32_t* chosen);
+
+/* Append x_dev (device, n_k FP64 values) to sequence k's history, as
+ * seq_push_solution does for one sequence (steps push automatically; this
+ * primes a history from solutions computed elsewhere).  Stream-ordered. */
+int seq_batch_push(seq_batch* batch, int32_t k, const double* x_dev);
+
+/* on = 0: seq_batch_step leaves the histories unchanged (the caller pushes
+ * with seq_batch_push); on = 1 (default): every step pushes its solutions. */
+int seq_batch_set_autopush(seq_batch* batch, int32_t on);
+
+/* Fix the schedule explicitly (e.g. one the autotuner picked earlier). */
+int seq_batch_set_schedule(seq_batch* batch, int32_t threads, int32_t blocks_per_sm,
+                           int32_t order_kind);
+
 /* The sketched block W = S [A X | b] computed without allocating any device
  * memory.  The paper has no counterpart: this is a deployment variant of the
  * sketch step for callers that cannot call cudaMalloc where they need W --

@@ -141,3 +141,21 @@ def solve_step_mixed(A64, A32, b, hist: History, S, tol: float, krylov_kind: str
     hist.push(x.astype(np.float32).astype(np.float64))
     return {"x": x, "x0": g.x0, "guess_relres": r0, "iters": it, "refinements": nref,
             "relres": rel, "status": st, "rank": g.rank, "rho_s": g.rho_s, "y": g.y}
+
+
+def batched_step(systems, hists, sketches, tol: float, max_iters: int = 100000,
+                 inner_tol: float = 1e-2):
+    """One time step of independent SPD sequences: for each sequence, the
+    sketched guess from its own history (FP64), then FP64 refinement around
+    float32 CG, then the push.  systems: list of (A, b); hists: list of History;
+    sketches: list of S.  Returns per-sequence dicts."""
+    out = []
+    for (A, b), h, S in zip(systems, hists, sketches):
+        g = sketched_guess(A, b, h.matrix(), S)
+        x, it, nref, rel, st = krylov.mixed_refine(A, A.astype(np.float32), b, g.x0, tol, "cg",
+                                                   30, max_iters, inner_tol=inner_tol)
+        h.push(x)
+        out.append({"x": x, "x0": g.x0, "iters": it, "refinements": nref, "relres": rel,
+                    "status": st, "guess_relres": relres(A, b, g.x0), "rank": g.rank,
+                    "rho_s": g.rho_s})
+    return out

@@ -81,6 +81,19 @@ _SIGS = {
                                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
+    "seq_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                        ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "seq_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "seq_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
+    "seq_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
+    "seq_batch_push": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "seq_batch_set_autopush": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "seq_batch_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32]),
     "seq_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "seq_kernel_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
 }
@@ -263,3 +276,79 @@ def sketch_block_noalloc(A: CSR, X: torch.Tensor, b: torch.Tensor, s: int, zeta:
                                       ctypes.c_void_p(_stream()))
     if rc != 0:
         raise SeqError(rc, "seq_sketch_block_noalloc failed")
+
+
+class Batch:
+    """Many independent SPD sequences advanced one time step per call
+    (seq_batch_create / seq_batch_step / seq_batch_autotune)."""
+
+    def __init__(self, patterns, M: int, s: int, zeta: int = 8, seed: int = 0x5EEDBA5E,
+                 max_iters: int = 100000, inner_tol: float = 0.0):
+        """patterns: list of (rowptr, colind) int32 CUDA tensors (kept alive here)."""
+        self._lib = load()
+        self._patterns = [(rp, ci) for rp, ci in patterns]
+        arr = (_Csr * len(patterns))()
+        for k, (rp, ci) in enumerate(self._patterns):
+            n = rp.numel() - 1
+            arr[k] = _Csr(n, ci.numel(), _ptr(rp, torch.int32, n + 1), _ptr(ci, torch.int32), 0, 0)
+        h = ctypes.c_void_p()
+        rc = self._lib.seq_batch_create(len(patterns), ctypes.byref(arr), M, s, zeta, seed,
+                                        max_iters, inner_tol, ctypes.c_void_p(_stream()),
+                                        ctypes.byref(h))
+        if rc != 0:
+            raise SeqError(rc, "seq_batch_create failed")
+        self._h = h
+        self.count = len(patterns)
+        self.sizes = [rp.numel() - 1 for rp, _ in self._patterns]
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.seq_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _arrays(self, values, b, x):
+        P = ctypes.c_void_p * self.count
+        va = P(*[_ptr(v, torch.float64) for v in values])
+        ba = P(*[_ptr(t, torch.float64, nn) for t, nn in zip(b, self.sizes)])
+        xa = P(*[_ptr(t, torch.float64, nn) for t, nn in zip(x, self.sizes)])
+        return va, ba, xa
+
+    def step(self, values, b, x, tol: float, allow=(0, 1)):
+        """values, b, x: lists of CUDA float64 tensors (one per sequence).
+        Returns the list of per-sequence info dicts."""
+        va, ba, xa = self._arrays(values, b, x)
+        infos = (SeqInfo * self.count)()
+        rc = self._lib.seq_batch_step(self._h, va, ba, xa, ctypes.c_double(tol), infos)
+        if rc not in allow:
+            raise SeqError(rc, "seq_batch_step failed")
+        return [infos[k].as_dict() for k in range(self.count)]
+
+    def autotune(self, values, b, x, tol: float):
+        va, ba, xa = self._arrays(values, b, x)
+        chosen = (ctypes.c_int32 * 3)()
+        rc = self._lib.seq_batch_autotune(self._h, va, ba, xa, ctypes.c_double(tol), chosen)
+        if rc != 0:
+            raise SeqError(rc, "seq_batch_autotune failed")
+        return {"threads": chosen[0], "blocks_per_sm": chosen[1],
+                "order": "largest first" if chosen[2] == 0 else "given"}
+
+    def set_autopush(self, on: bool) -> None:
+        rc = self._lib.seq_batch_set_autopush(self._h, int(bool(on)))
+        if rc != 0:
+            raise SeqError(rc, "seq_batch_set_autopush failed")
+
+    def push(self, k: int, x: torch.Tensor) -> None:
+        rc = self._lib.seq_batch_push(self._h, k, _ptr(x, torch.float64, self.sizes[k]))
+        if rc != 0:
+            raise SeqError(rc, "seq_batch_push failed")
+
+    def set_schedule(self, threads: int, blocks_per_sm: int, order: int) -> None:
+        rc = self._lib.seq_batch_set_schedule(self._h, threads, blocks_per_sm, order)
+        if rc != 0:
+            raise SeqError(rc, "seq_batch_set_schedule failed")

@@ -1,0 +1,802 @@
+// Batched form: many independent sequences advance one time step in a single
+// persistent launch (captured in a CUDA graph; one graph launch per step).
+//
+// Each thread block pulls sequences from a device work queue (largest first
+// by default, the order the autotuner picked otherwise) and runs the whole
+// step of one sequence with block barriers only -- there is no grid-wide
+// wait anywhere, so blocks never spin on one another:
+//   1. guess (Algorithm 1, steps 1-3): W = S [A X | b] accumulated in shared
+//      memory (the sparse-sign S generated on the fly from its counters),
+//      the column-scaled pivoted Householder least squares in shared memory,
+//      x0 = X y with FP64 accumulation;
+//   2. FP64 iterative refinement around FP32 CG (step 4): r = b - A x in FP64,
+//      inner CG on A32 d = r to a relative tolerance
+//      max(inner_tol, theta tol ||b|| / ||r||), x += d, until ||r|| <= tol ||b||;
+//   3. push x into the sequence's history ring (FP64).
+// Inputs per step are device arrays owned by the caller; the per-sequence
+// descriptors live in a device array refreshed by seq_batch_step.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/seqaccel.h"
+#include "common.cuh"
+
+namespace sa {
+namespace {
+
+constexpr int kBatchMaxM = 16;
+constexpr int kBatchMaxS = 64;
+constexpr int kSketchWarps = 8;           // warps with a private copy of W
+constexpr double kTheta = 0.5;
+constexpr int kOk = 0;
+
+struct BatchSeq {
+    // fixed for the life of the batch
+    int n, nnz, M, s, zeta, ldx;
+    uint64_t seed;
+    const int* rowptr;
+    const int* colind;
+    double* X;                             // history ring, n x ldx (FP64)
+    float* val32;                          // FP32 copy of this step's values
+    float *r, *p, *q, *d;                  // FP32 CG vectors
+    // per step
+    const double* val;
+    const double* b;
+    double* x;
+    // state and outputs
+    int pushes;
+    int iters, refinements, status, history_cols, rank;
+    double guess_relres, sketch_resid, final_relres;
+};
+
+struct BatchParams {
+    double tol;
+    double inner_tol;
+    int max_iters;
+    int commit;          // 1: push the solution into the history and keep the state
+};
+
+template <typename T>
+__device__ __forceinline__ T btotal(T v, T* sred) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sred[warp] = v;
+    __syncthreads();
+    T t = 0;
+    for (int w = 0; w < nw; ++w) t += sred[w];
+    return t;
+}
+
+template <typename VT, typename XT, typename Acc>
+__device__ __forceinline__ Acc row_dot(const int* __restrict__ rowptr, const int* __restrict__ colind,
+                                       const VT* __restrict__ val, const XT* x, int i, int n,
+                                       int nnz, int& bad) {
+    const int rs = max(0, min(rowptr[i], nnz));
+    const int re = max(rs, min(rowptr[i + 1], nnz));
+    Acc acc = 0;
+    for (int e = rs; e < re; ++e) {
+        const int c = colind[e];
+        if ((unsigned)c < (unsigned)n)
+            acc = fma((Acc)val[e], (Acc)x[c], acc);
+        else
+            bad = 1;
+    }
+    return acc;
+}
+
+__device__ void sketch_column_b(int j, int s, int zeta, uint64_t seed, uint16_t* out) {
+    int rows[kMaxZeta];
+    int cnt = 0;
+    for (int c = 0; c < 256 && cnt < zeta; ++c) {
+        const uint64_t h = mix64(seed + ((uint64_t)j * 256ull + (uint64_t)(c + 1)) *
+                                            0x9E3779B97F4A7C15ull);
+        const int q = (int)(((h >> 32) * (uint64_t)s) >> 32);
+        bool dup = false;
+        for (int k = 0; k < cnt; ++k) dup |= rows[k] == q;
+        if (!dup) {
+            rows[cnt] = q;
+            out[cnt] = (uint16_t)(q | ((h & 1ull) ? 0x8000 : 0));
+            ++cnt;
+        }
+    }
+    for (int q = 0; cnt < zeta && q < s; ++q) {
+        bool used = false;
+        for (int k = 0; k < cnt; ++k) used |= rows[k] == q;
+        if (!used) {
+            rows[cnt] = q;
+            out[cnt] = (uint16_t)q;
+            ++cnt;
+        }
+    }
+}
+
+// The sketched block W (s x (M+1), physical history slots, b last) of one
+// sequence, summed into Wsum (shared).  Warps 0..kSketchWarps-1 keep private
+// copies; rows are taken in batches of 32 per warp, lane l building the
+// sketch column of row base + l; the copies are added in warp order.
+__device__ void block_sketch(const BatchSeq& q, double* Wpriv, uint16_t* sks, double* Wsum,
+                             int& bad) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncol = q.M + 1, wsz = q.s * ncol;
+    const int nsw = min(kSketchWarps, (int)(blockDim.x >> 5));
+    for (int i = threadIdx.x; i < nsw * wsz; i += blockDim.x) Wpriv[i] = 0.0;
+    __syncthreads();
+    if (warp < nsw) {
+        double* Ww = Wpriv + warp * wsz;
+        uint16_t* sk = sks + warp * 32 * kMaxZeta;
+        for (int base = warp * 32; base < q.n; base += nsw * 32) {
+            if (base + lane < q.n) sketch_column_b(base + lane, q.s, q.zeta, q.seed, sk + lane * kMaxZeta);
+            __syncwarp();
+            const int cnt = min(32, q.n - base);
+            for (int u = 0; u < cnt; ++u) {
+                const int r = base + u;
+                double y = 0.0;
+                if (lane < q.M) {
+                    const int rs = max(0, min(q.rowptr[r], q.nnz));
+                    const int re = max(rs, min(q.rowptr[r + 1], q.nnz));
+                    for (int e = rs; e < re; ++e) {
+                        const int c = q.colind[e];
+                        if ((unsigned)c < (unsigned)q.n)
+                            y = fma(q.val[e], q.X[(size_t)c * q.ldx + lane], y);
+                        else
+                            bad = 1;
+                    }
+                } else if (lane == q.M) {
+                    y = q.b[r];
+                }
+                if (lane < ncol) {
+                    for (int k = 0; k < q.zeta; ++k) {
+                        const unsigned e = sk[u * kMaxZeta + k];
+                        double* dst = Ww + (e & 0x7fff) * ncol + lane;
+                        *dst = (e & 0x8000) ? *dst - y : *dst + y;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    const double inv = 1.0 / sqrt((double)q.zeta);
+    for (int i = threadIdx.x; i < wsz; i += blockDim.x) {
+        double acc = Wpriv[i];
+        for (int w = 1; w < nsw; ++w) acc += Wpriv[w * wsz + i];
+        Wsum[i] = acc * inv;
+    }
+    __syncthreads();
+}
+
+// Column-scaled, pivoted Householder least squares of the s x m block (the
+// same steps as the single-sequence kernel), all in shared memory.  Returns
+// y per physical slot in yphys (zeros for unused or truncated slots).
+__device__ void block_lsq(const double* Wsum, int s, int M, int m, int oldest, double tau,
+                          double* ws, double* yphys, int* rank_out, double* rho_out) {
+    double* B = ws;               // s*m
+    double* Wo = B + s * m;       // s*m
+    double* c = Wo + s * m;       // s
+    double* cb = c + s;           // s
+    double* v = cb + s;           // s
+    double* d = v + s;            // m
+    double* nrm = d + m;          // m
+    double* rdiag = nrm + m;      // m
+    double* z = rdiag + m;        // m
+    double* ylog = z + m;         // m
+    __shared__ int perm[kBatchMaxM], live[kBatchMaxM];
+    __shared__ double sh_normx, sh_vtv, sh_rho[32];
+    __shared__ int sh_p, sh_rank;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int bd = blockDim.x, ncol = M + 1;
+    for (int i = tid; i < s * m; i += bd) {
+        const int l = i / s, qq = i - l * s;
+        Wo[i] = Wsum[qq * ncol + (oldest + l) % M];
+    }
+    for (int qq = tid; qq < s; qq += bd) c[qq] = cb[qq] = Wsum[qq * ncol + M];
+    __syncthreads();
+    for (int l = warp; l < m; l += nw) {
+        double a = 0.0;
+        for (int qq = lane; qq < s; qq += 32) a += Wo[l * s + qq] * Wo[l * s + qq];
+        a = warp_sum(a);
+        if (lane == 0) d[l] = sqrt(a);
+    }
+    __syncthreads();
+    for (int i = tid; i < s * m; i += bd) {
+        const int l = i / s;
+        B[i] = d[l] > 0.0 ? Wo[i] / d[l] : 0.0;
+    }
+    if (tid < m) {
+        perm[tid] = tid;
+        live[tid] = d[tid] > 0.0;
+    }
+    __syncthreads();
+    const int steps = min(s, m);
+    int kdone = 0;
+    for (int k = 0; k < steps; ++k) {
+        for (int l = k + warp; l < m; l += nw) {
+            double a = 0.0;
+            for (int qq = k + lane; qq < s; qq += 32) a += B[l * s + qq] * B[l * s + qq];
+            a = warp_sum(a);
+            if (lane == 0) nrm[l] = live[perm[l]] ? sqrt(a) : -1.0;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int p = k;
+            double best = nrm[k];
+            for (int l = k + 1; l < m; ++l)
+                if (nrm[l] > best) { best = nrm[l]; p = l; }
+            sh_p = p;
+        }
+        __syncthreads();
+        const int p = sh_p;
+        if (p != k) {
+            for (int qq = tid; qq < s; qq += bd) {
+                const double t = B[k * s + qq];
+                B[k * s + qq] = B[p * s + qq];
+                B[p * s + qq] = t;
+            }
+            if (tid == 0) {
+                const int t = perm[k];
+                perm[k] = perm[p];
+                perm[p] = t;
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double a = 0.0;
+            for (int qq = k + lane; qq < s; qq += 32) a += B[k * s + qq] * B[k * s + qq];
+            a = warp_sum(a);
+            if (lane == 0) sh_normx = sqrt(a);
+        }
+        __syncthreads();
+        const double normx = sh_normx;
+        if (normx == 0.0 || !live[perm[k]]) break;
+        const double alpha = B[k * s + k] >= 0.0 ? -normx : normx;
+        for (int qq = k + tid; qq < s; qq += bd) v[qq] = B[k * s + qq] - (qq == k ? alpha : 0.0);
+        __syncthreads();
+        if (warp == 0) {
+            double a = 0.0;
+            for (int qq = k + lane; qq < s; qq += 32) a += v[qq] * v[qq];
+            a = warp_sum(a);
+            if (lane == 0) sh_vtv = a;
+        }
+        __syncthreads();
+        const double vtv = sh_vtv;
+        if (vtv > 0.0) {
+            for (int l = k + 1 + warp; l <= m; l += nw) {
+                double* col = (l < m) ? B + l * s : c;
+                double a = 0.0;
+                for (int qq = k + lane; qq < s; qq += 32) a += v[qq] * col[qq];
+                a = warp_sum(a);
+                const double t = (2.0 / vtv) * a;
+                for (int qq = k + lane; qq < s; qq += 32) col[qq] -= v[qq] * t;
+            }
+        }
+        __syncthreads();
+        for (int qq = k + tid; qq < s; qq += bd) B[k * s + qq] = (qq == k) ? alpha : 0.0;
+        if (tid == 0) rdiag[k] = alpha;
+        kdone = k + 1;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        int r = 0;
+        if (kdone > 0 && rdiag[0] != 0.0) {
+            const double lim = tau * fabs(rdiag[0]);
+            while (r < kdone && fabs(rdiag[r]) > lim) ++r;
+        }
+        for (int i = r - 1; i >= 0; --i) {
+            double acc = 0.0;
+            for (int j = i + 1; j < r; ++j) acc += B[j * s + i] * z[j];
+            z[i] = (c[i] - acc) / B[i * s + i];
+        }
+        for (int l = 0; l < m; ++l) ylog[l] = 0.0;
+        for (int i = 0; i < r; ++i) {
+            const int l = perm[i];
+            ylog[l] = live[l] ? z[i] / d[l] : 0.0;
+        }
+        sh_rank = r;
+    }
+    __syncthreads();
+    double part = 0.0;
+    for (int qq = tid; qq < s; qq += bd) {
+        double acc = 0.0;
+        for (int l = 0; l < m; ++l) acc += Wo[l * s + qq] * ylog[l];
+        const double e = acc - cb[qq];
+        part += e * e;
+    }
+    part = warp_sum(part);
+    if (lane == 0) sh_rho[warp] = part;
+    __syncthreads();
+    if (tid < M) yphys[tid] = 0.0;
+    __syncthreads();
+    for (int l = tid; l < m; l += bd) yphys[(oldest + l) % M] = ylog[l];
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += sh_rho[w];
+        *rho_out = sqrt(t);
+        *rank_out = sh_rank;
+    }
+    __syncthreads();
+}
+
+// FP32 CG on A32 d = rhs (d from 0) to ||rhs - A32 d|| <= itol ||rhs||, in
+// one block; returns iterations (negative status on breakdown).
+__device__ int block_cg32(const BatchSeq& q, double itol, int max_iters, float* sred, int& bad,
+                          int& status) {
+    const int n = q.n, tid = threadIdx.x, bd = blockDim.x;
+    float rr_l = 0.f;
+    for (int i = tid; i < n; i += bd) {
+        const float ri = q.r[i];
+        q.d[i] = 0.f;
+        q.p[i] = ri;
+        rr_l = fmaf(ri, ri, rr_l);
+    }
+    float rr = btotal(rr_l, sred);
+    const double target = itol * sqrt((double)rr);
+    int it = 0;
+    status = kOk;
+    if (!(rr > 0.f)) return 0;
+    while (sqrt((double)rr) > target) {
+        if (it >= max_iters) {
+            status = 1;
+            break;
+        }
+        __syncthreads();
+        float pq_l = 0.f;
+        for (int i = tid; i < n; i += bd) {
+            const float qi = row_dot<float, float, float>(q.rowptr, q.colind, q.val32, q.p, i, n,
+                                                          q.nnz, bad);
+            q.q[i] = qi;
+            pq_l = fmaf(q.p[i], qi, pq_l);
+        }
+        const float pq = btotal(pq_l, sred);
+        if (!(pq > 0.f)) {
+            status = isfinite(pq) ? -4 : -5;
+            break;
+        }
+        const float alpha = rr / pq;
+        float rn_l = 0.f;
+        for (int i = tid; i < n; i += bd) {
+            q.d[i] = fmaf(alpha, q.p[i], q.d[i]);
+            const float ri = fmaf(-alpha, q.q[i], q.r[i]);
+            q.r[i] = ri;
+            rn_l = fmaf(ri, ri, rn_l);
+        }
+        const float rr_new = btotal(rn_l, sred);
+        ++it;
+        const float beta = rr_new / rr;
+        rr = rr_new;
+        for (int i = tid; i < n; i += bd) q.p[i] = fmaf(beta, q.p[i], q.r[i]);
+    }
+    __syncthreads();
+    return it;
+}
+
+// Shared-memory bytes of one block for sequences with at most s rows of
+// sketch and M history columns.
+size_t batch_smem_bytes(int s, int M) {
+    const int ncol = M + 1, wsz = s * ncol;
+    size_t d = (size_t)kSketchWarps * wsz + wsz + (2 * s * M + 3 * s + 5 * M) + kBatchMaxM;
+    return d * sizeof(double) + (size_t)kSketchWarps * 32 * kMaxZeta * sizeof(uint16_t);
+}
+
+// One time step of every sequence.  Blocks take sequences from the queue
+// until it is empty; each sequence is processed by one block from start to
+// end (no inter-block waiting).
+__global__ void batched_step_kernel(BatchSeq* seqs, const int* __restrict__ order, int count,
+                                    int* queue, const BatchParams* __restrict__ prm) {
+    extern __shared__ double smem[];
+    __shared__ int sidx;
+    __shared__ double dred[32];
+    __shared__ float fred[32];
+    __shared__ int sbad;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    const BatchParams P = *prm;
+    for (;;) {
+        if (tid == 0) {
+            sidx = atomicAdd(queue, 1);
+            sbad = 0;
+        }
+        __syncthreads();
+        const int idx = sidx;
+        if (idx >= count) break;
+        BatchSeq& gq = seqs[order[idx]];
+        const BatchSeq q = gq;
+        const int n = q.n, M = q.M, s = q.s;
+        const int m = min(q.pushes, M);
+        int bad = 0, rank = 0;
+        double rho = 0.0;
+        // 1. guess
+        double* Wpriv = smem;
+        double* Wsum = Wpriv + kSketchWarps * s * (M + 1);
+        double* ws = Wsum + s * (M + 1);
+        double* yphys = ws + (2 * s * M + 3 * s + 5 * M);
+        uint16_t* sks = reinterpret_cast<uint16_t*>(yphys + kBatchMaxM);
+        if (m == 0) {
+            for (int i = tid; i < n; i += bd) q.x[i] = 0.0;
+        } else {
+            block_sketch(q, Wpriv, sks, Wsum, bad);
+            block_lsq(Wsum, s, M, m, (q.pushes - m) % M, 1e-12, ws, yphys, &rank, &rho);
+            for (int i = tid; i < n; i += bd) {
+                const double* row = q.X + (size_t)i * q.ldx;
+                double acc = 0.0;
+                for (int k = 0; k < M; ++k) acc = fma(row[k], yphys[k], acc);
+                q.x[i] = acc;
+            }
+        }
+        for (int e = tid; e < q.nnz; e += bd) q.val32[e] = (float)q.val[e];
+        __syncthreads();
+        // 2. FP64 refinement around FP32 CG
+        double bb_l = 0.0;
+        for (int i = tid; i < n; i += bd) bb_l = fma(q.b[i], q.b[i], bb_l);
+        const double bnorm = sqrt(btotal(bb_l, dred));
+        const double target = P.tol * bnorm;
+        int total = 0, nref = 0, status = kOk;
+        double rn = 0.0, first = 0.0;
+        for (int pass = 0;; ++pass) {
+            double rr_l = 0.0;
+            for (int i = tid; i < n; i += bd) {
+                const double ri = q.b[i] - row_dot<double, double, double>(q.rowptr, q.colind, q.val,
+                                                                           q.x, i, n, q.nnz, bad);
+                q.r[i] = (float)ri;
+                rr_l = fma(ri, ri, rr_l);
+            }
+            rn = sqrt(btotal(rr_l, dred));
+            if (pass == 0) first = bnorm > 0.0 ? rn / bnorm : rn;
+            if (!isfinite(rn)) {
+                status = -5;
+                break;
+            }
+            if (rn <= target) break;
+            if (total >= P.max_iters || nref >= 100) {
+                status = 1;
+                break;
+            }
+            const double itol = fmax(P.inner_tol, kTheta * target / rn);
+            int st = kOk;
+            total += block_cg32(q, itol, P.max_iters - total, fred, bad, st);
+            ++nref;
+            if (st < 0) {
+                status = st;
+                break;
+            }
+            for (int i = tid; i < n; i += bd) q.x[i] += (double)q.d[i];
+            __syncthreads();
+        }
+        // 3. push
+        if (P.commit && status >= 0) {
+            const int slot = q.pushes % M;
+            for (int i = tid; i < n; i += bd) q.X[(size_t)i * q.ldx + slot] = q.x[i];
+        }
+        if (bad) atomicOr(&sbad, 1);
+        __syncthreads();
+        if (tid == 0) {
+            if (P.commit && status >= 0) gq.pushes = q.pushes + 1;
+            gq.iters = total;
+            gq.refinements = nref;
+            gq.status = sbad ? -1 : status;
+            gq.history_cols = m;
+            gq.rank = rank;
+            gq.guess_relres = first;
+            gq.sketch_resid = rho;
+            gq.final_relres = bnorm > 0.0 ? rn / bnorm : rn;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void batch_push_kernel(const double* __restrict__ x, int n, double* X, int ldx, int slot) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        X[(size_t)i * ldx + slot] = x[i];
+}
+
+}  // namespace
+}  // namespace sa
+
+using namespace sa;
+
+struct seq_batch {
+    int count = 0, M = 0, s = 0, zeta = 0;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    std::vector<BatchSeq> host;           // mirror of the device descriptors
+    BatchSeq* h_pinned = nullptr;
+    BatchSeq* d_seqs = nullptr;
+    BatchParams* h_prm = nullptr;
+    BatchParams* d_prm = nullptr;
+    int* d_order = nullptr;
+    int* d_queue = nullptr;
+    std::vector<void*> allocs;
+    int threads = 512, blocks_per_sm = 1, order_kind = 0;  // 0: largest first, 1: given order
+    int autopush = 1;
+    cudaGraphExec_t graph = nullptr;
+    size_t smem = 0;
+    int sms = 0;
+};
+
+namespace {
+
+int batch_alloc(seq_batch* bt, void** p, size_t bytes) {
+    if (cudaMalloc(p, bytes ? bytes : 1) != cudaSuccess) {
+        cudaGetLastError();
+        return SEQ_ENOMEM;
+    }
+    bt->allocs.push_back(*p);
+    return SEQ_OK;
+}
+
+int batch_order(seq_batch* bt) {
+    std::vector<int> ord(bt->count);
+    for (int k = 0; k < bt->count; ++k) ord[k] = k;
+    if (bt->order_kind == 0)
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+            return (long long)bt->host[a].nnz > (long long)bt->host[b].nnz;
+        });
+    if (cudaMemcpyAsync(bt->d_order, ord.data(), sizeof(int) * bt->count, cudaMemcpyHostToDevice,
+                        bt->stream) != cudaSuccess)
+        return SEQ_ECUDA;
+    return cudaStreamSynchronize(bt->stream) == cudaSuccess ? SEQ_OK : SEQ_ECUDA;
+}
+
+int batch_capture(seq_batch* bt) {
+    if (bt->graph) {
+        cudaGraphExecDestroy(bt->graph);
+        bt->graph = nullptr;
+    }
+    if (cudaFuncSetAttribute(batched_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bt->smem) != cudaSuccess) {
+        cudaGetLastError();
+        return SEQ_ECUDA;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return SEQ_ECUDA;
+    cudaMemsetAsync(bt->d_queue, 0, sizeof(int), bt->cap);
+    batched_step_kernel<<<bt->sms * bt->blocks_per_sm, bt->threads, bt->smem, bt->cap>>>(
+        bt->d_seqs, bt->d_order, bt->count, bt->d_queue, bt->d_prm);
+    if (cudaStreamEndCapture(bt->cap, &g) != cudaSuccess) {
+        cudaGetLastError();
+        return SEQ_ECUDA;
+    }
+    cudaError_t e = cudaGraphInstantiate(&bt->graph, g, 0);
+    cudaGraphDestroy(g);
+    return e == cudaSuccess ? SEQ_OK : SEQ_ECUDA;
+}
+
+// Upload descriptors and parameters, launch the captured step, read back.
+int batch_run(seq_batch* bt, const double* const* values, const double* const* b,
+              double* const* x, double tol, int commit) {
+    for (int k = 0; k < bt->count; ++k) {
+        if (!values[k] || !b[k] || !x[k]) return SEQ_EINVAL;
+        bt->host[k].val = values[k];
+        bt->host[k].b = b[k];
+        bt->host[k].x = x[k];
+    }
+    memcpy(bt->h_pinned, bt->host.data(), sizeof(BatchSeq) * bt->count);
+    bt->h_prm->tol = tol;
+    bt->h_prm->commit = commit;
+    cudaMemcpyAsync(bt->d_seqs, bt->h_pinned, sizeof(BatchSeq) * bt->count,
+                    cudaMemcpyHostToDevice, bt->stream);
+    cudaMemcpyAsync(bt->d_prm, bt->h_prm, sizeof(BatchParams), cudaMemcpyHostToDevice, bt->stream);
+    if (cudaGraphLaunch(bt->graph, bt->stream) != cudaSuccess) return SEQ_ECUDA;
+    cudaMemcpyAsync(bt->h_pinned, bt->d_seqs, sizeof(BatchSeq) * bt->count,
+                    cudaMemcpyDeviceToHost, bt->stream);
+    if (cudaStreamSynchronize(bt->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return SEQ_ECUDA;
+    memcpy(bt->host.data(), bt->h_pinned, sizeof(BatchSeq) * bt->count);
+    return SEQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int seq_batch_create(int32_t count, const seq_csr* patterns, int32_t M, int32_t s, int32_t zeta,
+                     uint64_t seed, int32_t max_iters, double inner_tol, void* cuda_stream,
+                     seq_batch** out) {
+    if (!out) return SEQ_EINVAL;
+    *out = nullptr;
+    if (count <= 0 || !patterns || M < 1 || M > kBatchMaxM || s < M + 1 || s > kBatchMaxS ||
+        zeta < 1 || zeta > s || zeta > kMaxZeta || max_iters < 0)
+        return SEQ_EINVAL;
+    for (int k = 0; k < count; ++k)
+        if (patterns[k].n <= 0 || patterns[k].nnz < 0 || !patterns[k].rowptr ||
+            (patterns[k].nnz > 0 && !patterns[k].colind))
+            return SEQ_EINVAL;
+    seq_batch* bt = new seq_batch();
+    bt->count = count;
+    bt->M = M;
+    bt->s = s;
+    bt->zeta = zeta;
+    bt->stream = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&bt->sms, cudaDevAttrMultiProcessorCount, dev);
+    bt->smem = batch_smem_bytes(s, M);
+    bt->host.resize(count);
+    int rc = SEQ_OK;
+    const int ldx = (M + 1) & ~1;
+    for (int k = 0; k < count && rc == SEQ_OK; ++k) {
+        BatchSeq& q = bt->host[k];
+        memset(&q, 0, sizeof(q));
+        q.n = patterns[k].n;
+        q.nnz = patterns[k].nnz;
+        q.M = M;
+        q.s = s;
+        q.zeta = zeta;
+        q.ldx = ldx;
+        q.seed = seed + (uint64_t)k;
+        q.rowptr = patterns[k].rowptr;
+        q.colind = patterns[k].colind;
+        void* p = nullptr;
+        rc = batch_alloc(bt, &p, sizeof(double) * (size_t)q.n * ldx);
+        if (rc) break;
+        q.X = (double*)p;
+        cudaMemsetAsync(q.X, 0, sizeof(double) * (size_t)q.n * ldx, bt->stream);
+        rc = batch_alloc(bt, &p, sizeof(float) * (size_t)q.nnz);
+        if (rc) break;
+        q.val32 = (float*)p;
+        rc = batch_alloc(bt, &p, sizeof(float) * 4 * (size_t)q.n);
+        if (rc) break;
+        q.r = (float*)p;
+        q.p = q.r + q.n;
+        q.q = q.p + q.n;
+        q.d = q.q + q.n;
+    }
+    void* p = nullptr;
+    if (rc == SEQ_OK) rc = batch_alloc(bt, &p, sizeof(BatchSeq) * count), bt->d_seqs = (BatchSeq*)p;
+    if (rc == SEQ_OK) rc = batch_alloc(bt, &p, sizeof(BatchParams)), bt->d_prm = (BatchParams*)p;
+    if (rc == SEQ_OK) rc = batch_alloc(bt, &p, sizeof(int) * count), bt->d_order = (int*)p;
+    if (rc == SEQ_OK) rc = batch_alloc(bt, &p, sizeof(int)), bt->d_queue = (int*)p;
+    if (rc == SEQ_OK && (cudaMallocHost(&bt->h_pinned, sizeof(BatchSeq) * count) != cudaSuccess ||
+                         cudaMallocHost(&bt->h_prm, sizeof(BatchParams)) != cudaSuccess))
+        rc = SEQ_ENOMEM;
+    if (rc == SEQ_OK && cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking) != cudaSuccess)
+        rc = SEQ_ECUDA;
+    if (rc == SEQ_OK) {
+        bt->h_prm->tol = 1e-8;
+        bt->h_prm->inner_tol = inner_tol > 0 ? inner_tol : 1e-2;
+        bt->h_prm->max_iters = max_iters;
+        bt->h_prm->commit = 1;
+        rc = batch_order(bt);
+    }
+    if (rc == SEQ_OK) rc = batch_capture(bt);
+    if (rc != SEQ_OK) {
+        cudaGetLastError();
+        seq_batch_destroy(bt);
+        return rc;
+    }
+    *out = bt;
+    return SEQ_OK;
+}
+
+int seq_batch_destroy(seq_batch* bt) {
+    if (!bt) return SEQ_OK;
+    cudaStreamSynchronize(bt->stream);
+    if (bt->graph) cudaGraphExecDestroy(bt->graph);
+    for (void* p : bt->allocs) cudaFree(p);
+    if (bt->h_pinned) cudaFreeHost(bt->h_pinned);
+    if (bt->h_prm) cudaFreeHost(bt->h_prm);
+    if (bt->cap) cudaStreamDestroy(bt->cap);
+    delete bt;
+    return SEQ_OK;
+}
+
+int seq_batch_step(seq_batch* bt, const double* const* values, const double* const* b,
+                   double* const* x, double tol, seq_info* infos) {
+    if (!bt || !values || !b || !x || !(tol > 0)) return SEQ_EINVAL;
+    int rc = batch_run(bt, values, b, x, tol, bt->autopush);
+    if (rc) return rc;
+    int worst = SEQ_OK;
+    for (int k = 0; k < bt->count; ++k) {
+        const BatchSeq& q = bt->host[k];
+        if (infos) {
+            seq_info& in = infos[k];
+            memset(&in, 0, sizeof(in));
+            in.iters = q.iters;
+            in.refinements = q.refinements;
+            in.history_cols = q.history_cols;
+            in.rank = q.rank;
+            in.guess_relres = q.guess_relres;
+            in.sketch_resid = q.sketch_resid;
+            in.final_relres = q.final_relres;
+            in.status = q.status;
+            in.launches = (k == 0) ? 1 : 0;
+        }
+        if (q.status < 0) worst = q.status;
+        else if (q.status > 0 && worst == SEQ_OK) worst = q.status;
+    }
+    return worst;
+}
+
+int seq_batch_autotune(seq_batch* bt, const double* const* values, const double* const* b,
+                       double* const* x, double tol, int32_t* chosen) {
+    if (!bt || !values || !b || !x || !(tol > 0)) return SEQ_EINVAL;
+    const int thr[3] = {256, 512, 1024};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bt_thr = bt->threads, bt_bps = bt->blocks_per_sm, bt_ord = bt->order_kind;
+    for (int oi = 0; oi < 2; ++oi) {
+        for (int ti = 0; ti < 3; ++ti) {
+            for (int bps = 1; bps <= 2; ++bps) {
+                if ((size_t)bps * bt->smem > 220 * 1024) continue;
+                int nb = 0;
+                bt->threads = thr[ti];
+                bt->blocks_per_sm = bps;
+                bt->order_kind = oi;
+                if (cudaFuncSetAttribute(batched_step_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bt->smem) != cudaSuccess ||
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_step_kernel, thr[ti],
+                                                                  bt->smem) != cudaSuccess ||
+                    nb < bps) {
+                    cudaGetLastError();
+                    continue;
+                }
+                if (batch_order(bt) || batch_capture(bt)) continue;
+                cudaEventRecord(e0, bt->stream);
+                const int rc = batch_run(bt, values, b, x, tol, 0);
+                cudaEventRecord(e1, bt->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rc == SEQ_OK && ms < best) {
+                    best = ms;
+                    bt_thr = thr[ti];
+                    bt_bps = bps;
+                    bt_ord = oi;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bt->threads = bt_thr;
+    bt->blocks_per_sm = bt_bps;
+    bt->order_kind = bt_ord;
+    int rc = batch_order(bt);
+    if (!rc) rc = batch_capture(bt);
+    if (chosen) {
+        chosen[0] = bt->threads;
+        chosen[1] = bt->blocks_per_sm;
+        chosen[2] = bt->order_kind;
+    }
+    return rc;
+}
+
+int seq_batch_set_autopush(seq_batch* bt, int32_t on) {
+    if (!bt) return SEQ_EINVAL;
+    bt->autopush = on ? 1 : 0;
+    return SEQ_OK;
+}
+
+int seq_batch_push(seq_batch* bt, int32_t k, const double* x_dev) {
+    if (!bt || k < 0 || k >= bt->count || !x_dev) return SEQ_EINVAL;
+    BatchSeq& q = bt->host[k];
+    const int slot = q.pushes % q.M;
+    int blocks = (q.n + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    batch_push_kernel<<<blocks, 256, 0, bt->stream>>>(x_dev, q.n, q.X, q.ldx, slot);
+    if (cudaGetLastError() != cudaSuccess) return SEQ_ECUDA;
+    q.pushes += 1;
+    return SEQ_OK;
+}
+
+int seq_batch_set_schedule(seq_batch* bt, int32_t threads, int32_t blocks_per_sm,
+                           int32_t order_kind) {
+    if (!bt || (threads != 256 && threads != 512 && threads != 1024) || blocks_per_sm < 1 ||
+        blocks_per_sm > 2 || order_kind < 0 || order_kind > 1)
+        return SEQ_EINVAL;
+    bt->threads = threads;
+    bt->blocks_per_sm = blocks_per_sm;
+    bt->order_kind = order_kind;
+    int rc = batch_order(bt);
+    if (!rc) rc = batch_capture(bt);
+    return rc;
+}
+
+}  // extern "C"

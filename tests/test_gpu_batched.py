@@ -1,0 +1,133 @@
+"""Batched form (one persistent launch per time step) against the oracle.
+
+Each sequence is an SPD diffusion-reaction sequence with its own grid size,
+phase and source radius.  With histories primed from the oracle's solutions
+the GPU guess of every sequence matches the oracle's; every solve reaches the
+FP64 tolerance on the true residual (FP32 CG inside FP64 refinement)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import krylov, method, sketch
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_02156_gb300 as sa
+    sa.load()
+
+
+def _params():
+    ps = workloads.batched_params(7, 0xBA7C, nmin=6, nmax=40)
+    ps.append(workloads.PDEParams(N=1, a=0.5, phi=0.3, rc=0.2, v0=0.0, dt=0.01))   # 1 x 1 system
+    return ps
+
+
+def _batch(ps, M, s, seed):
+    import paper_2309_02156_gb300 as sa
+    pats = []
+    for p in ps:
+        rowptr, colind, _ = workloads.pattern(p.N)
+        pats.append((torch.from_numpy(rowptr).to(DEV), torch.from_numpy(colind).to(DEV)))
+    return sa.Batch(pats, M=M, s=s, zeta=8, seed=seed, max_iters=100000)
+
+
+def _inputs(ps, i):
+    vals, bs, As, bnp = [], [], [], []
+    for p in ps:
+        rowptr, colind, v, b = workloads.csr_system(p, i)
+        vals.append(torch.from_numpy(v).to(DEV))
+        bs.append(torch.from_numpy(b).to(DEV))
+        As.append(krylov.csr(rowptr, colind, v, p.n))
+        bnp.append(b)
+    return vals, bs, As, bnp
+
+
+def test_batched_matches_oracle_with_shared_history():
+    ps = _params()
+    M, s, seed, tol = 6, 24, 77, 1e-8
+    bt = _batch(ps, M, s, seed)
+    bt.set_autopush(False)
+    S = [sketch.sparse_sign_matrix(p.n, s, 8, seed + k) for k, p in enumerate(ps)]
+    hists = [method.History(p.n, M) for p in ps]
+    for i in range(M + 3):
+        vals, bs, As, bnp = _inputs(ps, i)
+        xs = [torch.empty(p.n, dtype=torch.float64, device=DEV) for p in ps]
+        ref = method.batched_step(list(zip(As, bnp)), hists, S, tol)
+        infos = bt.step(vals, bs, xs, tol)
+        for k, (p, info, r) in enumerate(zip(ps, infos, ref)):
+            assert info["status"] == 0 and r["status"] == 0
+            assert method.relres(As[k], bnp[k], xs[k].cpu().numpy()) <= tol * (1 + 1e-9)
+            assert info["history_cols"] == min(i, M)
+            assert info["guess_relres"] == pytest.approx(r["guess_relres"], rel=2e-3, abs=1e-13)
+            assert abs(info["refinements"] - r["refinements"]) <= 1
+            assert info["iters"] <= 1.5 * r["iters"] + 10 and r["iters"] <= 1.5 * info["iters"] + 10
+        for k, r in enumerate(ref):       # both histories receive the oracle's solutions
+            bt.push(k, torch.from_numpy(r["x"]).to(DEV))
+    bt.close()
+
+
+def test_batched_primed_guess_parity():
+    ps = _params()
+    M, s, seed = 5, 20, 3
+    bt = _batch(ps, M, s, seed)
+    S = [sketch.sparse_sign_matrix(p.n, s, 8, seed + k) for k, p in enumerate(ps)]
+    rng = np.random.default_rng(0)
+    hists = []
+    for k, p in enumerate(ps):
+        h = method.History(p.n, M)
+        for _ in range(M + 2):           # wraps the ring
+            c = rng.standard_normal(p.n)
+            h.push(c)
+            bt.push(k, torch.from_numpy(c).to(DEV))
+        hists.append(h)
+    vals, bs, As, bnp = _inputs(ps, 9)
+    xs = [torch.empty(p.n, dtype=torch.float64, device=DEV) for p in ps]
+    infos = bt.step(vals, bs, xs, 1e-8)
+    for k, p in enumerate(ps):
+        g = method.sketched_guess(As[k], bnp[k], hists[k].matrix(), S[k])
+        assert infos[k]["rank"] == g.rank
+        assert infos[k]["sketch_resid"] == pytest.approx(g.rho_s, rel=1e-9, abs=1e-14)
+        assert infos[k]["guess_relres"] == pytest.approx(method.relres(As[k], bnp[k], g.x0), rel=1e-9)
+        assert method.relres(As[k], bnp[k], xs[k].cpu().numpy()) <= 1e-8 * (1 + 1e-9)
+    bt.close()
+
+
+def test_batched_autotune_and_schedules():
+    ps = _params()
+    bt = _batch(ps, 4, 16, 5)
+    vals, bs, As, bnp = _inputs(ps, 0)
+    xs = [torch.empty(p.n, dtype=torch.float64, device=DEV) for p in ps]
+    chosen = bt.autotune(vals, bs, xs, 1e-8)
+    assert chosen["threads"] in (256, 512, 1024) and chosen["blocks_per_sm"] in (1, 2)
+    for sched in [(256, 1, 1), (256, 2, 0), (512, 1, 0)]:
+        bt.set_schedule(*sched)
+        infos = bt.step(vals, bs, xs, 1e-8)
+        for k in range(len(ps)):
+            assert infos[k]["status"] == 0
+            assert method.relres(As[k], bnp[k], xs[k].cpu().numpy()) <= 1e-8 * (1 + 1e-9)
+    bt.close()
+
+
+def test_batched_reports_bad_column_index():
+    import paper_2309_02156_gb300 as sa
+    ps = _params()[:3]
+    pats = []
+    for j, p in enumerate(ps):
+        rowptr, colind, _ = workloads.pattern(p.N)
+        if j == 1:
+            colind = colind.copy()
+            colind[3] = p.n + 7
+        pats.append((torch.from_numpy(rowptr).to(DEV), torch.from_numpy(colind).to(DEV)))
+    bt = sa.Batch(pats, M=4, s=16)
+    vals, bs, As, bnp = _inputs(ps, 0)
+    xs = [torch.empty(p.n, dtype=torch.float64, device=DEV) for p in ps]
+    with pytest.raises(sa.SeqError):
+        bt.step(vals, bs, xs, 1e-8)
+    bt.close()
