@@ -324,9 +324,10 @@ __device__ void block_lsq(const double* Wsum, int s, int M, int m, int oldest, d
 
 // FP32 CG on A32 d = rhs (d from 0) to ||rhs - A32 d|| <= itol ||rhs||, in
 // one block; returns iterations (negative status on breakdown).
-__device__ int block_cg32(const BatchSeq& q, double itol, int max_iters, float* sred, int& bad,
-                          int& status) {
+__device__ int block_cg32(const BatchSeq& q, double itol, int max_iters, float* sred, float* stage,
+                          int* sbad, int& status) {
     const int n = q.n, tid = threadIdx.x, bd = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
     float rr_l = 0.f;
     for (int i = tid; i < n; i += bd) {
         const float ri = q.r[i];
@@ -346,11 +347,14 @@ __device__ int block_cg32(const BatchSeq& q, double itol, int max_iters, float* 
         }
         __syncthreads();
         float pq_l = 0.f;
-        for (int i = tid; i < n; i += bd) {
-            const float qi = row_dot<float, float, float>(q.rowptr, q.colind, q.val32, q.p, i, n,
-                                                          q.nnz, bad);
-            q.q[i] = qi;
-            pq_l = fmaf(q.p[i], qi, pq_l);
+        for (int r0 = warp * 32; r0 < n; r0 += nw * 32) {
+            const float qi = warp_tile_spmv<float>(q.rowptr, q.colind, q.val32, q.p, n, q.nnz, r0,
+                                                   stage + warp * kTileChunks * 32, sbad);
+            const int i = r0 + lane;
+            if (i < n) {
+                q.q[i] = qi;
+                pq_l = fmaf(q.p[i], qi, pq_l);
+            }
         }
         const float pq = btotal(pq_l, sred);
         if (!(pq > 0.f)) {
@@ -380,14 +384,17 @@ __device__ int block_cg32(const BatchSeq& q, double itol, int max_iters, float* 
 size_t batch_smem_bytes(int s, int M) {
     const int ncol = M + 1, wsz = s * ncol;
     size_t d = (size_t)kSketchWarps * wsz + wsz + (2 * s * M + 3 * s + 5 * M) + kBatchMaxM;
-    return d * sizeof(double) + (size_t)kSketchWarps * 32 * kMaxZeta * sizeof(uint16_t);
+    const size_t guess = d * sizeof(double) + (size_t)kSketchWarps * 32 * kMaxZeta * sizeof(uint16_t);
+    const size_t stage = sizeof(double) * 32 * (size_t)kTileChunks * 32;   // up to 32 warps
+    return guess > stage ? guess : stage;
 }
 
 // One time step of every sequence.  Blocks take sequences from the queue
 // until it is empty; each sequence is processed by one block from start to
 // end (no inter-block waiting).
-__global__ void batched_step_kernel(BatchSeq* seqs, const int* __restrict__ order, int count,
-                                    int* queue, const BatchParams* __restrict__ prm) {
+__global__ void __launch_bounds__(1024, 1)
+batched_step_kernel(BatchSeq* seqs, const int* __restrict__ order, int count, int* queue,
+                    const BatchParams* __restrict__ prm) {
     extern __shared__ double smem[];
     __shared__ int sidx;
     __shared__ double dred[32];
@@ -429,6 +436,10 @@ __global__ void batched_step_kernel(BatchSeq* seqs, const int* __restrict__ orde
         }
         for (int e = tid; e < q.nnz; e += bd) q.val32[e] = (float)q.val[e];
         __syncthreads();
+        // Warp-tile staging for the products (aliases the guess workspace).
+        double* stage_d = smem;
+        float* stage_f = reinterpret_cast<float*>(smem);
+        const int lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
         // 2. FP64 refinement around FP32 CG
         double bb_l = 0.0;
         for (int i = tid; i < n; i += bd) bb_l = fma(q.b[i], q.b[i], bb_l);
@@ -438,11 +449,15 @@ __global__ void batched_step_kernel(BatchSeq* seqs, const int* __restrict__ orde
         double rn = 0.0, first = 0.0;
         for (int pass = 0;; ++pass) {
             double rr_l = 0.0;
-            for (int i = tid; i < n; i += bd) {
-                const double ri = q.b[i] - row_dot<double, double, double>(q.rowptr, q.colind, q.val,
-                                                                           q.x, i, n, q.nnz, bad);
-                q.r[i] = (float)ri;
-                rr_l = fma(ri, ri, rr_l);
+            for (int r0 = warp * 32; r0 < n; r0 += nw * 32) {
+                const double ax = warp_tile_spmv<double>(q.rowptr, q.colind, q.val, q.x, n, q.nnz, r0,
+                                                         stage_d + warp * kTileChunks * 32, &sbad);
+                const int i = r0 + lane;
+                if (i < n) {
+                    const double ri = q.b[i] - ax;
+                    q.r[i] = (float)ri;
+                    rr_l = fma(ri, ri, rr_l);
+                }
             }
             rn = sqrt(btotal(rr_l, dred));
             if (pass == 0) first = bnorm > 0.0 ? rn / bnorm : rn;
@@ -457,7 +472,7 @@ __global__ void batched_step_kernel(BatchSeq* seqs, const int* __restrict__ orde
             }
             const double itol = fmax(P.inner_tol, kTheta * target / rn);
             int st = kOk;
-            total += block_cg32(q, itol, P.max_iters - total, fred, bad, st);
+            total += block_cg32(q, itol, P.max_iters - total, fred, stage_f, &sbad, st);
             ++nref;
             if (st < 0) {
                 status = st;
