@@ -322,6 +322,129 @@ def batched_form(K, W, hbm_peak):
     }
 
 
+def _gen_learned(job):
+    import workloads
+    from workloads.pde import PDEParams
+    a, N, i = job
+    p = PDEParams(N=N, a=a, phi=0.0, rc=0.2, v0=20.0, dt=0.005)
+    t = workloads.time_grid(p, i)
+    return workloads.assemble(p, t), workloads.rhs(p, t)
+
+
+def learned_ablation(args):
+    """Learned coefficient predictor against sketched least squares.
+
+    Workload: advection-diffusion sequences as in the main line on a 512 x 512
+    grid (n = 262,144), one per k amplitude a ~ U[0.2, 0.8] (seeded), M = 20,
+    s = 80, GMRES(30) to 1e-8 (FP64).  The predictor (160 -> 256 -> 256 -> 20,
+    BF16 weights) is trained on the GPU on the samples of steps 0..T-1 and
+    evaluated on steps T..T+E-1.  Two contexts see identical histories (the
+    least-squares path's solution is pushed into both); each evaluation system
+    is solved from both guesses.  Prints one JSON line."""
+    import numpy as np
+    T, E, N, nseq = args.learned_train, args.learned_eval, args.learned_grid, args.learned_seqs
+    amps = __import__("workloads").learned_amplitudes(nseq, SEED)
+    pool = mp.get_context("spawn").Pool(8)
+    import torch
+    import paper_2309_02156_gb300 as sa
+    import workloads
+    dev = torch.device("cuda", 0)
+    rowptr, colind, _ = workloads.pattern(N)
+    rp = torch.from_numpy(rowptr).to(dev)
+    ci = torch.from_numpy(colind).to(dev)
+    n = N * N
+    net = sa.MLP(M_HIST, S_ROWS, hidden=256, max_batch=64, seed=SEED)
+    stride = net.stride
+
+    def systems(a, lo, hi, chunk=32):
+        nxt = pool.map_async(_gen_learned, [(a, N, i) for i in range(lo, min(lo + chunk, hi))])
+        for c0 in range(lo, hi, chunk):
+            got = nxt.get()
+            c1 = c0 + chunk
+            if c1 < hi:
+                nxt = pool.map_async(_gen_learned, [(a, N, i) for i in range(c1, min(c1 + chunk, hi))])
+            for k, (v, b) in enumerate(got):
+                yield c0 + k, torch.from_numpy(v).to(dev), torch.from_numpy(b).to(dev)
+
+    mk = lambda: sa.Sequence(n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, guess="learned",
+                             krylov="gmres", restart=RESTART, max_iters=60000)
+    ctxs, samples, train_iters = [], [], []
+    t0 = time.time()
+    for a in amps:
+        c_ls, c_net = mk(), mk()
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        y = torch.empty(n, dtype=torch.float64, device=dev)
+        for i, v, b in systems(a, 0, T):
+            A = sa.CSR(rp, ci, v)
+            c_ls.guess(A, b, x)
+            c_net.guess(A, b, y)
+            buf = torch.empty(stride, dtype=torch.float32, device=dev)
+            try:
+                c_ls.last_sample(buf)
+                samples.append(buf)
+            except sa.SeqError:
+                pass
+            info = c_ls.solve(A, b, TOL, x)
+            train_iters.append(info["iters"])
+            c_ls.push(x)
+            c_net.push(x)
+        ctxs.append((a, c_ls, c_net))
+    gen_s = time.time() - t0
+    St = torch.stack(samples)
+    net.fit_normalization(St)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    losses = net.train(St, epochs=args.learned_epochs, batch=32, lr=1e-3, seed=SEED)
+    torch.cuda.synchronize()
+    train_s = time.time() - t1
+    rec = {"ls_guess": [], "net_guess": [], "ls_iters": [], "net_iters": [], "fallback": [],
+           "ls_rho": [], "net_rho": []}
+    for a, c_ls, c_net in ctxs:
+        c_net.set_learned(net)
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        y = torch.empty(n, dtype=torch.float64, device=dev)
+        for i, v, b in systems(a, T, T + E):
+            A = sa.CSR(rp, ci, v)
+            g1 = c_ls.guess(A, b, x)
+            g2 = c_net.guess(A, b, y)
+            i1 = c_ls.solve(A, b, TOL, x)
+            i2 = c_net.solve(A, b, TOL, y)
+            rec["ls_guess"].append(g1["guess_relres"])
+            rec["net_guess"].append(g2["guess_relres"])
+            rec["ls_rho"].append(g1["sketch_resid"])
+            rec["net_rho"].append(g2["sketch_resid"])
+            rec["ls_iters"].append(i1["iters"])
+            rec["net_iters"].append(i2["iters"])
+            rec["fallback"].append(bool(g2["fallback"]))
+            c_ls.push(x)
+            c_net.push(x)
+        c_ls.close()
+        c_net.close()
+    pool.close()
+    gm = lambda v: float(np.exp(np.mean(np.log(np.asarray(v, dtype=np.float64)))))
+    used = [not f for f in rec["fallback"]]
+    out = {
+        "learned_ablation": True,
+        "workload": "advection-diffusion %dx%d (n=%d), a ~ U[0.2,0.8] x %d sequences, M=20, s=80, "
+                    "GMRES(30) to 1e-8; train steps 0..%d, evaluate %d..%d"
+                    % (N, N, n, nseq, T - 1, T, T + E - 1),
+        "amplitudes": amps, "samples": int(St.shape[0]), "epochs": args.learned_epochs,
+        "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1]),
+        "train_seconds": train_s, "data_seconds": gen_s,
+        "train_iters_mean": float(np.mean(train_iters)),
+        "eval_systems": len(rec["ls_iters"]),
+        "ls": {"guess_relres_geomean": gm(rec["ls_guess"]), "iters_mean": float(np.mean(rec["ls_iters"])),
+               "sketch_resid_geomean": gm(rec["ls_rho"])},
+        "net": {"guess_relres_geomean": gm(rec["net_guess"]),
+                "iters_mean": float(np.mean(rec["net_iters"])),
+                "sketch_resid_geomean": gm(rec["net_rho"]),
+                "used_fraction": float(np.mean(used))},
+        "net_over_ls_guess_relres_geomean": gm(np.asarray(rec["net_guess"]) / np.asarray(rec["ls_guess"])),
+    }
+    print(json.dumps(out), flush=True)
+    net.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -336,7 +459,16 @@ def main():
     ap.add_argument("--iters-per-system", type=float, default=0.0)
     ap.add_argument("--gmres-iters", type=int, default=120)
     ap.add_argument("--profile-run", type=int, default=0, metavar="ITERS")
+    ap.add_argument("--learned-ablation", action="store_true")
+    ap.add_argument("--learned-train", type=int, default=400)
+    ap.add_argument("--learned-eval", type=int, default=400)
+    ap.add_argument("--learned-grid", type=int, default=512)
+    ap.add_argument("--learned-seqs", type=int, default=1)
+    ap.add_argument("--learned-epochs", type=int, default=300)
     args = ap.parse_args()
+    if args.learned_ablation:
+        learned_ablation(args)
+        return
     if args.profile_run:
         profile_run(args.profile_run)
         return

@@ -200,6 +200,56 @@ int seq_kernel_stats(seq_ctx* ctx, seq_kernel_stat* out, int reset);
  * arithmetic roof of the FP64 kernels.  Synchronises. */
 int seq_probe_fp64_peak(void* cuda_stream, double* tflops);
 
+/* ---- Learned coefficient predictor (SEQ_GUESS_LEARNED) ----
+ *
+ * Not in the paper (Algorithm 1 solves for y every step).  A small MLP,
+ * 4M+s -> H -> H -> M with GELU, bfloat16 weights and FP32 accumulation,
+ * predicts y from the previous four coefficient vectors (shifted into the
+ * current window) and the sketched residual of the linear extrapolation
+ * 2 x(t_{i-1}) - x(t_{i-2}); y_hat = shift(y_{i-1}) + sigma_out * net.  In
+ * SEQ_GUESS_LEARNED, seq_guess uses y_hat unless its sketched residual
+ * exceeds 1.5 times that of the least-squares y, in which case it falls back
+ * to least squares and returns SEQ_FALLBACK_USED.
+ *
+ * Training data: after every seq_guess with a full history and four previous
+ * guesses, seq_last_sample writes the sample of that guess, FP32, stride
+ * (4M+s) + M + M*M + 1: [features | least-squares y | W1^T W1 | ||S b||].
+ * Loss of a sample: (y_hat - y)^T W1^T W1 (y_hat - y) / ||S b||^2 (the
+ * excess sketched residual).  Training runs on the GPU (hand-written forward
+ * and backward kernels, Adam). */
+typedef struct seq_mlp seq_mlp;
+
+/* He-uniform weights from SplitMix64 counters (seed), zero biases, identity
+ * normalisation.  max_batch bounds the batch of train / loss_grad / predict. */
+int seq_mlp_create(int32_t M, int32_t s, int32_t hidden, int32_t max_batch, uint64_t seed,
+                   void* cuda_stream, seq_mlp** out);
+int seq_mlp_destroy(seq_mlp* mlp);
+/* Number of FP32 parameters: W1 (H x (4M+s)), b1, W2 (H x H), b2, W3 (M x H), b3. */
+int seq_mlp_param_count(const seq_mlp* mlp);
+/* Host copies of the parameters (param_count floats, layout above) and of the
+ * normalisation (feature mean, feature std, output scale: 2(4M+s) + M floats);
+ * either pointer may be NULL.  set also resets the Adam state. */
+int seq_mlp_get_params(seq_mlp* mlp, float* params_host, float* norm_host);
+int seq_mlp_set_params(seq_mlp* mlp, const float* params_host, const float* norm_host);
+/* Feature mean/std and output scale from count samples (device). */
+int seq_mlp_fit_normalization(seq_mlp* mlp, const float* samples_dev, int32_t count);
+/* Batch-mean loss and its gradient (host, param_count floats) on B samples,
+ * without updating. */
+int seq_mlp_loss_grad(seq_mlp* mlp, const float* samples_dev, int32_t B, float* loss_host,
+                      float* grads_host);
+/* epochs of Adam (lr) over count samples in shuffled batches (SplitMix64 seed);
+ * losses_host (epochs floats, may be NULL) receives the mean loss per epoch. */
+int seq_mlp_train(seq_mlp* mlp, const float* samples_dev, int32_t count, int32_t epochs,
+                  int32_t batch, float lr, uint64_t seed, float* losses_host);
+/* y_hat (B x M, device) for B samples (device, sample stride; only the
+ * features part is read). */
+int seq_mlp_predict(seq_mlp* mlp, const float* samples_dev, int32_t B, float* y_dev);
+/* Attach (or detach with NULL) a predictor to a context. */
+int seq_set_learned(seq_ctx* ctx, seq_mlp* mlp);
+/* Sample of the last seq_guess into sample_dev (device); SEQ_EINVAL if that
+ * guess had no full history or fewer than four previous guesses. */
+int seq_last_sample(seq_ctx* ctx, float* sample_dev);
+
 /* ---- Batched form: many independent sequences, one persistent launch per step ----
  *
  * Each sequence k has its own history (M columns, FP64), sketch (seed + k)

@@ -39,7 +39,7 @@ import math
 
 import numpy as np
 
-IN, HID, OUT = 160, 256, 20
+IN, HID, OUT = 160, 256, 20     # the sizes used with M = 20, s = 80 (any M, s work)
 
 
 def bf16_round(a: np.ndarray) -> np.ndarray:
@@ -104,7 +104,7 @@ def forward(p: Params, F: np.ndarray, dtype=np.float32, round_bf16=True):
     a2 = h1 @ W2.T + p.b2.astype(dtype)
     h2 = gelu(a2).astype(dtype)
     d = h2 @ W3.T + p.b3.astype(dtype)
-    base = F[:, :OUT].astype(dtype)
+    base = F[:, :p.W3.shape[0]].astype(dtype)     # shift(y_{i-1}): the first M features
     y = base + p.sig.astype(dtype) * d
     return y, (z, a1, h1, a2, h2, W1, W2, W3)
 

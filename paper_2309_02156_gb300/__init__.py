@@ -11,8 +11,8 @@ the guess of Algorithm 1 over span(X) of the last M solutions, here with the
 reduced least-squares problem row-sketched by a sparse-sign S, followed by
 CG or GMRES from that guess.
 """
-from ._binding import (Batch, CSR, Sequence, SeqError, lib_path, load, probe_fp64_peak,
+from ._binding import (Batch, CSR, MLP, Sequence, SeqError, lib_path, load, probe_fp64_peak,
                        sketch_block_noalloc, sketch_columns, STATUS)
 
-__all__ = ["Batch", "CSR", "Sequence", "SeqError", "lib_path", "load", "probe_fp64_peak",
+__all__ = ["Batch", "CSR", "MLP", "Sequence", "SeqError", "lib_path", "load", "probe_fp64_peak",
            "sketch_block_noalloc", "sketch_columns", "STATUS"]

@@ -94,6 +94,20 @@ _SIGS = {
     "seq_batch_set_autopush": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "seq_batch_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_int32]),
+    "seq_mlp_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "seq_mlp_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "seq_mlp_param_count": (ctypes.c_int, [ctypes.c_void_p]),
+    "seq_mlp_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "seq_mlp_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "seq_mlp_fit_normalization": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "seq_mlp_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "seq_mlp_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, ctypes.c_void_p]),
+    "seq_mlp_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "seq_set_learned": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "seq_last_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "seq_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "seq_kernel_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
 }
@@ -201,8 +215,10 @@ class Sequence:
         info = SeqInfo()
         rc = self._lib.seq_guess(self._h, ctypes.byref(A._c()), _ptr(b, torch.float64, self.n),
                                  _ptr(x0, torch.float64, self.n), ctypes.byref(info))
-        self._check(rc, info)
-        return info.as_dict()
+        self._check(rc, info, allow=(0, 2))
+        d = info.as_dict()
+        d["fallback"] = rc == 2
+        return d
 
     def solve(self, A: CSR, b: torch.Tensor, tol: float, x: torch.Tensor,
               allow=(0, 1)) -> dict:
@@ -224,6 +240,14 @@ class Sequence:
         self._check(self._lib.seq_kernel_stats(self._h, ctypes.byref(arr), int(reset)))
         return {k: {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes,
                     "flops": arr[i].flops} for i, k in enumerate(KERNEL_KINDS)}
+
+    def set_learned(self, mlp) -> None:
+        self._check(self._lib.seq_set_learned(self._h, mlp._h if mlp is not None else None))
+        self._mlp = mlp
+
+    def last_sample(self, out: torch.Tensor) -> None:
+        """Write the training sample of the last guess into out (CUDA float32)."""
+        self._check(self._lib.seq_last_sample(self._h, _ptr(out, torch.float32)), allow=(0,))
 
     def last_sketch(self):
         """(W, y) of the last guess as float64 CPU tensors, oldest history column first."""
@@ -352,3 +376,75 @@ class Batch:
         rc = self._lib.seq_batch_set_schedule(self._h, threads, blocks_per_sm, order)
         if rc != 0:
             raise SeqError(rc, "seq_batch_set_schedule failed")
+
+
+class MLP:
+    """The learned coefficient predictor (seq_mlp_*)."""
+
+    def __init__(self, M: int, s: int, hidden: int = 256, max_batch: int = 256, seed: int = 1):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        rc = self._lib.seq_mlp_create(M, s, hidden, max_batch, seed, ctypes.c_void_p(_stream()),
+                                      ctypes.byref(h))
+        if rc != 0:
+            raise SeqError(rc, "seq_mlp_create failed")
+        self._h = h
+        self.M, self.s, self.hidden = M, s, hidden
+        self.inp = 4 * M + s
+        self.stride = self.inp + M + M * M + 1
+        self.nparams = self._lib.seq_mlp_param_count(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.seq_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _rc(self, rc, what):
+        if rc != 0:
+            raise SeqError(rc, what)
+
+    def get_params(self):
+        import numpy as np
+        p = np.zeros(self.nparams, np.float32)
+        nrm = np.zeros(2 * self.inp + self.M, np.float32)
+        self._rc(self._lib.seq_mlp_get_params(self._h, p.ctypes.data, nrm.ctypes.data), "get_params")
+        return p, nrm
+
+    def set_params(self, params, norm=None):
+        import numpy as np
+        p = np.ascontiguousarray(params, np.float32)
+        nrm = None if norm is None else np.ascontiguousarray(norm, np.float32)
+        self._rc(self._lib.seq_mlp_set_params(self._h, p.ctypes.data,
+                                              None if nrm is None else nrm.ctypes.data), "set_params")
+
+    def fit_normalization(self, samples: torch.Tensor) -> None:
+        self._rc(self._lib.seq_mlp_fit_normalization(self._h, _ptr(samples, torch.float32),
+                                                     samples.shape[0]), "fit_normalization")
+
+    def loss_grad(self, samples: torch.Tensor):
+        import numpy as np
+        g = np.zeros(self.nparams, np.float32)
+        loss = ctypes.c_float()
+        self._rc(self._lib.seq_mlp_loss_grad(self._h, _ptr(samples, torch.float32), samples.shape[0],
+                                             ctypes.byref(loss), g.ctypes.data), "loss_grad")
+        return loss.value, g
+
+    def train(self, samples: torch.Tensor, epochs: int, batch: int, lr: float = 1e-3, seed: int = 7):
+        import numpy as np
+        losses = np.zeros(max(epochs, 1), np.float32)
+        self._rc(self._lib.seq_mlp_train(self._h, _ptr(samples, torch.float32), samples.shape[0],
+                                         epochs, batch, ctypes.c_float(lr), seed, losses.ctypes.data),
+                 "train")
+        return losses[:epochs]
+
+    def predict(self, samples: torch.Tensor) -> torch.Tensor:
+        y = torch.empty((samples.shape[0], self.M), dtype=torch.float32, device=samples.device)
+        self._rc(self._lib.seq_mlp_predict(self._h, _ptr(samples, torch.float32), samples.shape[0],
+                                           _ptr(y, torch.float32)), "predict")
+        return y

@@ -14,6 +14,7 @@
 #include "../../include/seqaccel.h"
 #include "common.cuh"
 #include "internal.h"
+#include "mlp_internal.h"
 
 using namespace sa;
 
@@ -59,6 +60,15 @@ struct seq_ctx {
     size_t sell_cap = 0;             // entries allocated
     int* h_int = nullptr;            // pinned scratch word
     bool sell_ok = false;
+    double* yring = nullptr;         // last four coefficient vectors (newest first)
+    int yring_valid = 0;             // consecutive full-history guesses in the ring
+    long long yring_pushes = -1;     // pushes at the newest ring entry
+    seq_mlp* mlp = nullptr;          // learned predictor (SEQ_GUESS_LEARNED)
+    float* sample = nullptr;         // features / target of the last full guess
+    float* yhat = nullptr;
+    int* used_net = nullptr;
+    int* h_used = nullptr;
+    bool sample_ready = false;
     cudaGraphExec_t cycle = nullptr;
     cudaGraphExec_t cycle_prof = nullptr;   // same cycle with timing events between kernels
     std::vector<cudaEvent_t> ev;
@@ -361,6 +371,15 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
         ok = ok && cudaMalloc(&ctx->sell_off, sizeof(int) * (size_t)(ns + 1)) == cudaSuccess;
     }
     ok = ok && cudaMallocHost(&ctx->h_int, sizeof(int)) == cudaSuccess;
+    {
+        const int in = 4 * M + s, stride = in + M + M * M + 1;
+        ok = ok && cudaMalloc(&ctx->yring, sizeof(double) * 4 * kMaxM) == cudaSuccess;
+        ok = ok && cudaMemsetAsync(ctx->yring, 0, sizeof(double) * 4 * kMaxM, ctx->stream) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->sample, sizeof(float) * stride) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->yhat, sizeof(float) * kMaxM) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->used_net, sizeof(int)) == cudaSuccess;
+        ok = ok && cudaMallocHost(&ctx->h_used, sizeof(int)) == cudaSuccess;
+    }
     ok = ok && cudaMalloc(&ctx->d_args, sizeof(DevArgs)) == cudaSuccess;
     ok = ok && cudaMallocHost(&ctx->h_args, sizeof(DevArgs)) == cudaSuccess;
     ok = ok && cudaMalloc(&ctx->d_args_in, sizeof(DevArgs)) == cudaSuccess;
@@ -392,10 +411,12 @@ int seq_destroy(seq_ctx* ctx) {
     void* dev_ptrs[] = {ctx->X, ctx->sk, ctx->sk_partial, ctx->W, ctx->lsq, ctx->kpartial,
                         ctx->V, ctx->w, ctx->r, ctx->p, ctx->q, ctx->val32, ctx->rhs32, ctx->d,
                         ctx->d_args, ctx->d_args_in, ctx->ks, ctx->ks_in, ctx->sell_width,
-                        ctx->sell_off, ctx->sell_col, ctx->sell_val};
+                        ctx->sell_off, ctx->sell_col, ctx->sell_val, ctx->yring, ctx->sample,
+                        ctx->yhat, ctx->used_net};
     for (void* p : dev_ptrs)
         if (p) cudaFree(p);
-    void* host_ptrs[] = {ctx->lsq_host, ctx->h_args, ctx->h_args_in, ctx->h_ks, ctx->h_int};
+    void* host_ptrs[] = {ctx->lsq_host, ctx->h_args, ctx->h_args_in, ctx->h_ks, ctx->h_int,
+                         ctx->h_used};
     for (void* p : host_ptrs)
         if (p) cudaFreeHost(p);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
@@ -432,7 +453,10 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
     const int n = c.n, M = c.M;
     const int m = seq_history_size(ctx);
     int mode = c.guess;
-    if (mode == SEQ_GUESS_LEARNED) mode = SEQ_GUESS_SKETCH;
+    const bool learned = mode == SEQ_GUESS_LEARNED;
+    if (learned) mode = SEQ_GUESS_SKETCH;
+    bool fallback = false;
+    ctx->sample_ready = false;
     ctx->sell_ok = false;            // the SELL copy belongs to the last seq_solve's matrix
     if (m == 0 && mode != SEQ_GUESS_ZERO) mode = SEQ_GUESS_ZERO;
     CK(cudaMemsetAsync(ctx->ks, 0, sizeof(KState), ctx->stream));
@@ -463,11 +487,40 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
         }
         const int oldest = (ctx->pushes - m) % M;
         launch_lsq(ctx->W, c.s, M, m, oldest, c.rank_tol, ctx->lsq, ctx->stream);
+        ctx->launches += 1;
+        if (ctx->pushes != ctx->yring_pushes + 1) ctx->yring_valid = 0;   // window moved by != 1
+        if (m == M && ctx->yring_valid >= 4 && M >= 2) {
+            // Features and target of this guess (training sample), and the
+            // learned prediction with its fallback to least squares.
+            launch_learned_sample(ctx->lsq, c.s, M, ctx->yring, ctx->sample, ctx->stream);
+            ctx->sample_ready = true;
+            ctx->launches += 1;
+        }
+        // The ring keeps the least-squares coefficients (the training
+        // targets), pushed before the network's choice can replace them.
+        if (m == M) {
+            launch_yring_push(ctx->yring, ctx->lsq, M, ctx->stream);
+            ctx->yring_valid += 1;
+            ctx->yring_pushes = ctx->pushes;
+            ctx->launches += 1;
+        } else {
+            ctx->yring_valid = 0;
+        }
+        if (ctx->sample_ready) {
+            if (learned && ctx->mlp && mlp_dims_ok(ctx->mlp, M, c.s)) {
+                mlp_predict_dev(ctx->mlp, ctx->sample, 1, ctx->yhat, ctx->stream);
+                launch_learned_select(ctx->lsq, c.s, M, oldest, ctx->yhat, ctx->used_net, ctx->stream);
+                CK(cudaMemcpyAsync(ctx->h_used, ctx->used_net, sizeof(int), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+                ctx->launches += 6;
+                fallback = true;   // decided after the synchronisation below
+            }
+        }
         if (ctx->hist32)
             launch_expand_f32((const float*)ctx->X, ctx->ldx, n, M, ctx->lsq, x0_dev, ctx->stream);
         else
             launch_expand_f64((const double*)ctx->X, ctx->ldx, n, M, ctx->lsq, x0_dev, ctx->stream);
-        ctx->launches += 4;
+        ctx->launches += 3;
         CK(cudaMemcpyAsync(ctx->lsq_host, ctx->lsq, offsetof(LsqOut, W_logical),
                            cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaMemcpyAsync(&ctx->lsq_host->rho, &ctx->lsq->rho,
@@ -495,6 +548,7 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
         info->launches = ctx->launches;
     }
     ctx->lsq_host->m = (mode == SEQ_GUESS_SKETCH) ? m : 0;
+    if (fallback) fallback = *ctx->h_used == 0;     // the network's guess was rejected
     if (ctx->h_ks->bad_index) {
         if (info) info->status = SEQ_EINVAL;
         return fail(ctx, SEQ_EINVAL, "CSR column index outside [0, n)");
@@ -503,6 +557,28 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
         if (info) info->status = SEQ_ENONFINITE;
         return fail(ctx, SEQ_ENONFINITE, "non-finite residual of the guess");
     }
+    if (fallback) {
+        if (info) info->status = SEQ_FALLBACK_USED;
+        return SEQ_FALLBACK_USED;
+    }
+    return SEQ_OK;
+}
+
+int seq_set_learned(seq_ctx* ctx, seq_mlp* mlp) {
+    if (!ctx) return SEQ_EINVAL;
+    if (mlp && !mlp_dims_ok(mlp, ctx->cfg.M, ctx->cfg.s))
+        return fail(ctx, SEQ_EINVAL, "predictor dimensions differ from the context's M and s");
+    ctx->mlp = mlp;
+    return SEQ_OK;
+}
+
+int seq_last_sample(seq_ctx* ctx, float* sample_dev) {
+    if (!ctx || !sample_dev) return SEQ_EINVAL;
+    if (!ctx->sample_ready) return fail(ctx, SEQ_EINVAL, "no sample: the last guess lacked a full history");
+    const int M = ctx->cfg.M, stride = 4 * M + ctx->cfg.s + M + M * M + 1;
+    CK(cudaMemcpyAsync(sample_dev, ctx->sample, sizeof(float) * stride, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return SEQ_OK;
 }
 
