@@ -398,7 +398,7 @@ def learned_ablation(args):
     torch.cuda.synchronize()
     train_s = time.time() - t1
     rec = {"ls_guess": [], "net_guess": [], "ls_iters": [], "net_iters": [], "fallback": [],
-           "ls_rho": [], "net_rho": []}
+           "ls_rho": [], "net_rho": [], "ratio": [], "fp32_floor": [], "ymax": []}
     for a, c_ls, c_net in ctxs:
         c_net.set_learned(net)
         x = torch.empty(n, dtype=torch.float64, device=dev)
@@ -416,6 +416,18 @@ def learned_ablation(args):
             rec["ls_iters"].append(i1["iters"])
             rec["net_iters"].append(i2["iters"])
             rec["fallback"].append(bool(g2["fallback"]))
+            if g2["net_resid"] > 0 and g1["sketch_resid"] > 0:
+                rec["ratio"].append(g2["net_resid"] / g1["sketch_resid"])
+            # Floor of any FP32-output predictor: the least-squares y itself
+            # rounded to FP32, judged in FP64 on the same sketched block.
+            Wf, yf = c_ls.last_sketch()
+            Wf = Wf.reshape(S_ROWS, M_HIST + 1)
+            r64 = np.linalg.norm(Wf[:, :M_HIST] @ yf - Wf[:, M_HIST])
+            r32 = np.linalg.norm(Wf[:, :M_HIST] @ yf.astype(np.float32).astype(np.float64)
+                                 - Wf[:, M_HIST])
+            if r64 > 0:
+                rec["fp32_floor"].append(r32 / r64)
+                rec["ymax"].append(float(np.abs(yf).max()))
             c_ls.push(x)
             c_net.push(x)
         c_ls.close()
@@ -438,11 +450,96 @@ def learned_ablation(args):
         "net": {"guess_relres_geomean": gm(rec["net_guess"]),
                 "iters_mean": float(np.mean(rec["net_iters"])),
                 "sketch_resid_geomean": gm(rec["net_rho"]),
-                "used_fraction": float(np.mean(used))},
+                "used_fraction": float(np.mean(used)),
+                "net_over_ls_sketch_resid_geomean": gm(rec["ratio"]) if rec["ratio"] else None,
+                "net_over_ls_sketch_resid_min": float(min(rec["ratio"])) if rec["ratio"] else None},
+        "fp32_rounded_ls_y_over_ls_sketch_resid_geomean": gm(rec["fp32_floor"]),
+        "fp32_rounded_ls_y_rejected_fraction": float(np.mean(np.asarray(rec["fp32_floor"]) > 1.5)),
+        "ls_y_absmax_geomean": gm(rec["ymax"]),
         "net_over_ls_guess_relres_geomean": gm(np.asarray(rec["net_guess"]) / np.asarray(rec["ls_guess"])),
     }
     print(json.dumps(out), flush=True)
     net.close()
+
+
+def _gen_nonsym(job):
+    import workloads
+    N, i = job
+    p = workloads.plain_nonsym(N)
+    t = workloads.time_grid(p, i)
+    return workloads.assemble(p, t), workloads.rhs(p, t)
+
+
+def precision_form(args):
+    """Precision form on the 2048 x 2048 advection-diffusion sequence
+    (n = 4,194,304, nnz = 20,963,328): FP32 CSR values, FP32 history and sketch
+    of A X, FP32 GMRES(30) inner solves inside FP64 residual refinement to
+    ||b - A x|| <= 1e-10 ||b||, FP64 least squares (M = 20, s = 80).  The first
+    `prime` systems fill the history (untimed, same method), then W warm-up and
+    K timed steps (seq_guess + seq_solve + seq_push_solution).  Prints one JSON
+    line; the per-step FP64 residuals are computed on the device by the library."""
+    import numpy as np
+    import torch
+    import paper_2309_02156_gb300 as sa
+    import workloads
+    N, tol = args.precision_grid, 1e-10
+    P, W, K = args.precision_prime, args.precision_warmup, args.precision_steps
+    pool = mp.get_context("spawn").Pool(8)
+    dev = torch.device("cuda", 0)
+    rowptr, colind, _ = workloads.pattern(N)
+    rp = torch.from_numpy(rowptr).to(dev)
+    ci = torch.from_numpy(colind).to(dev)
+    n = N * N
+    seq = sa.Sequence(n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, precision=args.precision_kind,
+                      krylov="gmres", restart=RESTART, max_iters=400000)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    total = P + W + K
+    nxt = pool.map_async(_gen_nonsym, [(N, i) for i in range(0, min(4, total))])
+    rows, timed_ms = [], []
+    stream = torch.cuda.current_stream()
+    for c0 in range(0, total, 4):
+        got = nxt.get()
+        if c0 + 4 < total:
+            nxt = pool.map_async(_gen_nonsym, [(N, i) for i in range(c0 + 4, min(c0 + 8, total))])
+        for k, (v, b) in enumerate(got):
+            i = c0 + k
+            vd = torch.from_numpy(v).to(dev)
+            bd = torch.from_numpy(b).to(dev)
+            A = sa.CSR(rp, ci, vd)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            w0 = time.time()
+            e0.record(stream)
+            g = seq.guess(A, bd, x)
+            info = seq.solve(A, bd, tol, x)
+            seq.push(x)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            rows.append({"i": i, "guess_relres": g["guess_relres"], "iters": info["iters"],
+                         "refinements": info["refinements"], "final_relres": info["final_relres"],
+                         "status": info["status"], "ms": ms, "wall_s": time.time() - w0})
+            if i >= P + W:
+                timed_ms.append(ms)
+            print(json.dumps({"precision_step": rows[-1]}), file=sys.stderr, flush=True)
+    pool.close()
+    seq.close()
+    timed = rows[P + W:]
+    out = {
+        "precision_form": True,
+        "workload": "nonsym advection-diffusion %dx%d (n=%d), M=20, s=80, %s: FP32 values/history/"
+                    "inner GMRES(30), FP64 refinement to rel-res 1e-10" % (N, N, n, args.precision_kind),
+        "value": 1e3 * K / sum(timed_ms), "unit": "systems/s", "ms_per_step": sum(timed_ms) / K,
+        "steps": K, "warmup": W, "prime": P,
+        "iters_mean": float(np.mean([r["iters"] for r in timed])),
+        "refinements_mean": float(np.mean([r["refinements"] for r in timed])),
+        "guess_relres_geomean": float(np.exp(np.mean(np.log([r["guess_relres"] for r in timed])))),
+        "final_relres_max": max(r["final_relres"] for r in timed),
+        "all_converged": all(r["status"] == 0 for r in rows),
+        "per_step": rows,
+    }
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -459,6 +556,12 @@ def main():
     ap.add_argument("--iters-per-system", type=float, default=0.0)
     ap.add_argument("--gmres-iters", type=int, default=120)
     ap.add_argument("--profile-run", type=int, default=0, metavar="ITERS")
+    ap.add_argument("--precision-form", action="store_true")
+    ap.add_argument("--precision-kind", default="mixed", choices=["mixed", "mixed_krylov", "f64"])
+    ap.add_argument("--precision-grid", type=int, default=2048)
+    ap.add_argument("--precision-prime", type=int, default=20)
+    ap.add_argument("--precision-warmup", type=int, default=1)
+    ap.add_argument("--precision-steps", type=int, default=5)
     ap.add_argument("--learned-ablation", action="store_true")
     ap.add_argument("--learned-train", type=int, default=400)
     ap.add_argument("--learned-eval", type=int, default=400)
@@ -468,6 +571,9 @@ def main():
     args = ap.parse_args()
     if args.learned_ablation:
         learned_ablation(args)
+        return
+    if args.precision_form:
+        precision_form(args)
         return
     if args.profile_run:
         profile_run(args.profile_run)

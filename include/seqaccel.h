@@ -109,6 +109,9 @@ typedef struct {
     double final_relres;    /* true ||b - A x|| / ||b|| at exit (seq_solve)             */
     int32_t status;         /* seq_status of the call                                   */
     int32_t launches;       /* kernels this call launched (graph nodes included)        */
+    double net_resid;       /* SEQ_GUESS_LEARNED: sketched residual ||W1 y_net - S b|| of
+                               the network's y, whether used or rejected; -1 when no
+                               prediction was made (history not full)               */
 } seq_info;
 
 /* Create a context for one sequence (Section 2: one history X per sequence).

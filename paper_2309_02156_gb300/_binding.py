@@ -45,7 +45,7 @@ class SeqInfo(ctypes.Structure):
                 ("history_cols", ctypes.c_int32), ("rank", ctypes.c_int32),
                 ("guess_relres", ctypes.c_double), ("sketch_resid", ctypes.c_double),
                 ("final_relres", ctypes.c_double), ("status", ctypes.c_int32),
-                ("launches", ctypes.c_int32)]
+                ("launches", ctypes.c_int32), ("net_resid", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -377,8 +377,8 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
         ok = ok && cudaMemsetAsync(ctx->yring, 0, sizeof(double) * 4 * kMaxM, ctx->stream) == cudaSuccess;
         ok = ok && cudaMalloc(&ctx->sample, sizeof(float) * stride) == cudaSuccess;
         ok = ok && cudaMalloc(&ctx->yhat, sizeof(float) * kMaxM) == cudaSuccess;
-        ok = ok && cudaMalloc(&ctx->used_net, sizeof(int)) == cudaSuccess;
-        ok = ok && cudaMallocHost(&ctx->h_used, sizeof(int)) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->used_net, 16) == cudaSuccess;     // int flag | double rho
+        ok = ok && cudaMallocHost(&ctx->h_used, 16) == cudaSuccess;
     }
     ok = ok && cudaMalloc(&ctx->d_args, sizeof(DevArgs)) == cudaSuccess;
     ok = ok && cudaMallocHost(&ctx->h_args, sizeof(DevArgs)) == cudaSuccess;
@@ -455,7 +455,7 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
     int mode = c.guess;
     const bool learned = mode == SEQ_GUESS_LEARNED;
     if (learned) mode = SEQ_GUESS_SKETCH;
-    bool fallback = false;
+    bool predicted = false;          // the network's y was computed (and judged)
     ctx->sample_ready = false;
     ctx->sell_ok = false;            // the SELL copy belongs to the last seq_solve's matrix
     if (m == 0 && mode != SEQ_GUESS_ZERO) mode = SEQ_GUESS_ZERO;
@@ -509,11 +509,12 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
         if (ctx->sample_ready) {
             if (learned && ctx->mlp && mlp_dims_ok(ctx->mlp, M, c.s)) {
                 mlp_predict_dev(ctx->mlp, ctx->sample, 1, ctx->yhat, ctx->stream);
-                launch_learned_select(ctx->lsq, c.s, M, oldest, ctx->yhat, ctx->used_net, ctx->stream);
-                CK(cudaMemcpyAsync(ctx->h_used, ctx->used_net, sizeof(int), cudaMemcpyDeviceToHost,
+                launch_learned_select(ctx->lsq, c.s, M, oldest, ctx->yhat, ctx->used_net,
+                                      (double*)(ctx->used_net + 2), ctx->stream);
+                CK(cudaMemcpyAsync(ctx->h_used, ctx->used_net, 16, cudaMemcpyDeviceToHost,
                                    ctx->stream));
                 ctx->launches += 6;
-                fallback = true;   // decided after the synchronisation below
+                predicted = true;   // used or rejected: read after the synchronisation
             }
         }
         if (ctx->hist32)
@@ -546,9 +547,10 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
         info->guess_relres = ctx->h_ks->first_relres;
         info->final_relres = ctx->h_ks->first_relres;
         info->launches = ctx->launches;
+        info->net_resid = predicted ? *(const double*)(ctx->h_used + 2) : -1.0;
     }
     ctx->lsq_host->m = (mode == SEQ_GUESS_SKETCH) ? m : 0;
-    if (fallback) fallback = *ctx->h_used == 0;     // the network's guess was rejected
+    const bool fallback = predicted && *ctx->h_used == 0;   // the network's y was rejected
     if (ctx->h_ks->bad_index) {
         if (info) info->status = SEQ_EINVAL;
         return fail(ctx, SEQ_EINVAL, "CSR column index outside [0, n)");
@@ -592,7 +594,10 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
     if (!b_dev || !x_dev) return fail(ctx, SEQ_EINVAL, "NULL vector");
     if (!(tol > 0.0)) return fail(ctx, SEQ_EINVAL, "tol must be > 0");
     const seq_config& c = ctx->cfg;
-    if (info) memset(info, 0, sizeof(seq_info));
+    if (info) {
+        memset(info, 0, sizeof(seq_info));
+        info->net_resid = -1.0;
+    }
     CK(cudaMemsetAsync(ctx->ks, 0, sizeof(KState), ctx->stream));
     CK(cudaMemsetAsync(ctx->ks_in, 0, sizeof(KState), ctx->stream));
     rc = ensure_val32(ctx, A);

@@ -719,6 +719,7 @@ int seq_batch_step(seq_batch* bt, const double* const* values, const double* con
             in.final_relres = q.final_relres;
             in.status = q.status;
             in.launches = (k == 0) ? 1 : 0;
+            in.net_resid = -1.0;
         }
         if (q.status < 0) worst = q.status;
         else if (q.status > 0 && worst == SEQ_OK) worst = q.status;

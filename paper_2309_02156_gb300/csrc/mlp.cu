@@ -254,7 +254,7 @@ __global__ void learned_sample_kernel(const LsqOut* __restrict__ lo, int s, int 
 // the network's y is used unless its sketched residual exceeds 1.5 times the
 // least-squares one.  Writes the chosen y into lo (logical and physical).
 __global__ void learned_select_kernel(LsqOut* lo, int s, int M, int oldest, const float* __restrict__ yhat,
-                                      int* used_net) {
+                                      int* used_net, double* rho_net_out) {
     __shared__ double part[32];
     const int ncol = M + 1, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double acc = 0;
@@ -272,6 +272,7 @@ __global__ void learned_select_kernel(LsqOut* lo, int s, int M, int oldest, cons
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
         const double rho_net = sqrt(t);
         use = rho_net <= 1.5 * lo->rho;
+        *rho_net_out = rho_net;
         if (use) lo->rho = rho_net;
         *used_net = use;
     }
@@ -298,8 +299,8 @@ void launch_learned_sample(const LsqOut* lo, int s, int M, const double* yring, 
     learned_sample_kernel<<<1, 256, 0, st>>>(lo, s, M, yring, sample);
 }
 void launch_learned_select(LsqOut* lo, int s, int M, int oldest, const float* yhat, int* used,
-                           cudaStream_t st) {
-    learned_select_kernel<<<1, 128, 0, st>>>(lo, s, M, oldest, yhat, used);
+                           double* rho_net, cudaStream_t st) {
+    learned_select_kernel<<<1, 128, 0, st>>>(lo, s, M, oldest, yhat, used, rho_net);
 }
 void launch_yring_push(double* yring, const LsqOut* lo, int M, cudaStream_t st) {
     yring_push_kernel<<<1, 32, 0, st>>>(yring, lo, M);

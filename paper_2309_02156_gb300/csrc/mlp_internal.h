@@ -11,7 +11,7 @@ namespace sa {
 void launch_learned_sample(const LsqOut* lo, int s, int M, const double* yring, float* sample,
                            cudaStream_t st);
 void launch_learned_select(LsqOut* lo, int s, int M, int oldest, const float* yhat, int* used,
-                           cudaStream_t st);
+                           double* rho_net, cudaStream_t st);
 void launch_yring_push(double* yring, const LsqOut* lo, int M, cudaStream_t st);
 void mlp_predict_dev(seq_mlp* m, const float* features, int B, float* y, cudaStream_t st);
 int mlp_stride(const seq_mlp* m);

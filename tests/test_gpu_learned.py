@@ -229,12 +229,13 @@ def test_learned_selection_and_fallback():
             assert abs(rho_net / (1.5 * ref.rho_s) - 1) > 1e-6
             assert use == want_net
             assert info["fallback"] == (not use)
+            assert info["net_resid"] == pytest.approx(rho_net, rel=1e-6)
             x_want = X @ yhat if use else ref.x0
             assert np.linalg.norm(x0 - x_want) <= 1e-6 * np.linalg.norm(x_want)
             assert info["guess_relres"] == pytest.approx(method.relres(A_ref, b, x_want), rel=1e-5)
             outcomes.append(use)
         else:
-            assert not info["fallback"]
+            assert not info["fallback"] and info["net_resid"] == -1.0
             assert np.linalg.norm(x0 - ref.x0) <= 1e-10 * np.linalg.norm(ref.x0)
         ys.append(ref.y)
         seq.push(_tensor(cols[k + M]))
