@@ -65,7 +65,12 @@ typedef enum {
     SEQ_GUESS_ZERO = 0,     /* x0 = 0                                                  */
     SEQ_GUESS_PREV = 1,     /* x0 = x(t_{i-1}), the paper's baseline (Sections 4-5)    */
     SEQ_GUESS_SKETCH = 2,   /* x0 = X y, y from the sketched least squares (Alg. 1)    */
-    SEQ_GUESS_LEARNED = 3   /* y predicted by the coefficient MLP, sketched LS fallback */
+    SEQ_GUESS_LEARNED = 3,  /* y predicted by the coefficient MLP, sketched LS fallback */
+    SEQ_GUESS_POD = 4,      /* Algorithm 1 over span(Q_POD), Q_POD = the basis_m leading
+                               left singular vectors of X (Algorithm 2)               */
+    SEQ_GUESS_RAND = 5      /* Algorithm 1 over span(Omega), Omega = X Z with a Gaussian
+                               Z (n x basis_m), updated progressively at every push and
+                               recomputed every `refresh` updates (Algorithm 4)       */
 } seq_guess_mode;
 
 typedef enum { SEQ_CG = 0, SEQ_GMRES = 1 } seq_krylov;
@@ -97,6 +102,10 @@ typedef struct {
                              0 selects 1e-2                                        */
     double rank_tol;      /* QR truncation tau; 0 selects 1e-12 for an FP64 sketch
                              or 1e-5 for an FP32 sketch (SEQ_MIXED)                */
+    int32_t basis_m;      /* SEQ_GUESS_POD / SEQ_GUESS_RAND: basis size m, 1..M
+                             (ignored by the other modes)                          */
+    int32_t refresh;      /* SEQ_GUESS_RAND: progressive updates between from-scratch
+                             computations of Omega; 0 selects 50 (Section 4)       */
 } seq_config;
 
 typedef struct {
@@ -156,9 +165,26 @@ const char* seq_last_error(const seq_ctx* ctx);
 
 /* The sketched block and coefficients of the last seq_guess, in logical
  * history order (oldest column first): W_host (s x (m+1), row-major, b last)
- * and y_host (m), where m = info.history_cols of that call.  Either pointer
- * may be NULL.  Diagnostic; synchronises. */
+ * and y_host (m), where m = info.history_cols of that call.  In the POD and
+ * RAND modes they are the reduced problem's block [S A B | S b] and its
+ * coefficients c over the basis B (X V_k, resp. Omega), m = basis columns.
+ * Either pointer may be NULL.  Diagnostic; synchronises. */
 int seq_last_sketch(seq_ctx* ctx, double* W_host, double* y_host);
+
+/* Algorithm 4 state of a SEQ_GUESS_RAND context (diagnostic; synchronises):
+ * omega_host (n x basis_m, row-major), Z_host (history_size x basis_m, oldest
+ * history column first), the number of Gaussian values drawn so far and the
+ * progressive updates since the last from-scratch Omega.  Any pointer may be
+ * NULL.  SEQ_EINVAL if the context is not in RAND mode or Omega was never
+ * formed. */
+int seq_rand_state(seq_ctx* ctx, double* omega_host, double* Z_host, uint64_t* draws,
+                   int32_t* updates);
+
+/* Algorithm 2 state of the last SEQ_GUESS_POD guess (diagnostic; synchronises):
+ * V_host (m_i x k, column-major: the k leading eigenvectors of X^T X over the
+ * m_i history columns, oldest first), lam_host (m_i eigenvalues, descending),
+ * dims[0] = m_i, dims[1] = k, dims[2] = Jacobi sweeps.  Pointers may be NULL. */
+int seq_pod_state(seq_ctx* ctx, double* V_host, double* lam_host, int32_t* dims);
 
 /* Materialise the sparse-sign sketch used by every context with the same
  * (n, s, zeta, seed): for column j, rows_dev[j*zeta + k] and signs_dev[j*zeta + k]

@@ -15,7 +15,7 @@ STATUS = {0: "SEQ_OK", 1: "SEQ_NOT_CONVERGED", 2: "SEQ_FALLBACK_USED", -1: "SEQ_
           -2: "SEQ_ENOMEM", -3: "SEQ_ECUDA", -4: "SEQ_EBREAKDOWN", -5: "SEQ_ENONFINITE",
           -6: "SEQ_ETIMEOUT"}
 PRECISION = {"f64": 0, "mixed": 1, "mixed_krylov": 2}
-GUESS = {"zero": 0, "prev": 1, "sketch": 2, "learned": 3}
+GUESS = {"zero": 0, "prev": 1, "sketch": 2, "learned": 3, "pod": 4, "rand": 5}
 KRYLOV = {"cg": 0, "gmres": 1}
 
 
@@ -37,7 +37,8 @@ class _Config(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("guess", ctypes.c_int32),
                 ("krylov", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_iters", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("rank_tol", ctypes.c_double)]
+                ("rank_tol", ctypes.c_double), ("basis_m", ctypes.c_int32),
+                ("refresh", ctypes.c_int32)]
 
 
 class SeqInfo(ctypes.Structure):
@@ -108,6 +109,10 @@ _SIGS = {
     "seq_mlp_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "seq_set_learned": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "seq_last_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "seq_rand_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "seq_pod_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
     "seq_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "seq_kernel_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
 }
@@ -178,16 +183,16 @@ class Sequence:
     def __init__(self, n: int, M: int, s: int, zeta: int = 8, seed: int = 0x5EEDBA5E,
                  precision: str = "f64", guess: str = "sketch", krylov: str = "gmres",
                  restart: int = 30, max_iters: int = 30000, inner_tol: float = 0.0,
-                 rank_tol: float = 0.0):
+                 rank_tol: float = 0.0, basis_m: int = 0, refresh: int = 0):
         self._lib = load()
         cfg = _Config(n, M, s, zeta, seed, PRECISION[precision], GUESS[guess], KRYLOV[krylov],
-                      restart, max_iters, inner_tol, rank_tol)
+                      restart, max_iters, inner_tol, rank_tol, basis_m, refresh)
         h = ctypes.c_void_p()
         rc = self._lib.seq_create(ctypes.byref(cfg), ctypes.c_void_p(_stream()), ctypes.byref(h))
         if rc != 0:
             raise SeqError(rc, "seq_create failed")
         self._h = h
-        self.n, self.M, self.s = n, M, s
+        self.n, self.M, self.s, self.basis_m = n, M, s, basis_m
 
     def close(self) -> None:
         if getattr(self, "_h", None):
@@ -248,6 +253,28 @@ class Sequence:
     def last_sample(self, out: torch.Tensor) -> None:
         """Write the training sample of the last guess into out (CUDA float32)."""
         self._check(self._lib.seq_last_sample(self._h, _ptr(out, torch.float32)), allow=(0,))
+
+    def rand_state(self):
+        """(Omega n x m, Z history_size x m, draws, updates) of Algorithm 4 (host arrays)."""
+        import numpy as np
+        om = np.zeros((self.n, self.basis_m))
+        Z = np.zeros((self.history_size(), self.basis_m))
+        draws = ctypes.c_uint64()
+        upd = ctypes.c_int32()
+        self._check(self._lib.seq_rand_state(self._h, om.ctypes.data, Z.ctypes.data,
+                                             ctypes.byref(draws), ctypes.byref(upd)), allow=(0,))
+        return om, Z, draws.value, upd.value
+
+    def pod_state(self):
+        """(V_k m_i x k, eigenvalues m_i, sweeps) of the last POD guess."""
+        import numpy as np
+        dims = (ctypes.c_int32 * 3)()
+        self._check(self._lib.seq_pod_state(self._h, None, None, dims), allow=(0,))
+        mi, kk = dims[0], dims[1]
+        V = np.zeros(max(mi * kk, 1))
+        lam = np.zeros(max(mi, 1))
+        self._check(self._lib.seq_pod_state(self._h, V.ctypes.data, lam.ctypes.data, dims), allow=(0,))
+        return V[:mi * kk].reshape(kk, mi).T.copy(), lam[:mi].copy(), dims[2]
 
     def last_sketch(self):
         """(W, y) of the last guess as float64 CPU tensors, oldest history column first."""

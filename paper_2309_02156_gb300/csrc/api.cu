@@ -69,6 +69,22 @@ struct seq_ctx {
     int* used_net = nullptr;
     int* h_used = nullptr;
     bool sample_ready = false;
+    double* Om = nullptr;            // RAND: Omega, n x ldo row-major
+    int ldo = 0;
+    double* Zs = nullptr;            // RAND: Z row of every ring slot (M x basis_m)
+    uint64_t gseed = 0;
+    uint64_t gdraws = 0;             // Gaussian values drawn so far
+    bool om_valid = false;
+    int om_updates = 0;
+    double* gpart = nullptr;         // POD: Gram partials, Gram, eigenvectors, eigenvalues
+    unsigned* gcount = nullptr;
+    double* G = nullptr;
+    double* Vk = nullptr;
+    double* lam = nullptr;
+    int* sweeps = nullptr;
+    double* Wp = nullptr;            // POD: reduced block [W1 V_k | wb]
+    LsqOut* lsq_red = nullptr;
+    int pod_mi = 0, pod_kk = 0;
     cudaGraphExec_t cycle = nullptr;
     cudaGraphExec_t cycle_prof = nullptr;   // same cycle with timing events between kernels
     std::vector<cudaEvent_t> ev;
@@ -325,14 +341,18 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
     if (c.n <= 0 || c.M < 1 || c.M > kMaxM || c.s < c.M + 1 || c.s > kMaxS || c.zeta < 1 ||
         c.zeta > c.s || c.zeta > kMaxZeta || c.restart < 1 || c.restart > kMaxRestart ||
         c.max_iters < 0 || (c.precision < SEQ_F64 || c.precision > SEQ_MIXED_KRYLOV) ||
-        c.guess < SEQ_GUESS_ZERO || c.guess > SEQ_GUESS_LEARNED ||
+        c.guess < SEQ_GUESS_ZERO || c.guess > SEQ_GUESS_RAND ||
         (c.krylov != SEQ_CG && c.krylov != SEQ_GMRES))
+        return SEQ_EINVAL;
+    const bool compressed = c.guess == SEQ_GUESS_POD || c.guess == SEQ_GUESS_RAND;
+    if (compressed && (c.basis_m < 1 || c.basis_m > c.M || c.refresh < 0 || c.precision == SEQ_MIXED))
         return SEQ_EINVAL;
     seq_ctx* ctx = new seq_ctx();
     memset(ctx->stats, 0, sizeof(ctx->stats));
     ctx->cfg = c;
     if (ctx->cfg.inner_tol <= 0) ctx->cfg.inner_tol = 1e-2;
     if (ctx->cfg.rank_tol <= 0) ctx->cfg.rank_tol = c.precision == SEQ_MIXED ? 1e-5 : 1e-12;
+    if (ctx->cfg.refresh <= 0) ctx->cfg.refresh = 50;
     ctx->mixed = c.precision != SEQ_F64;
     ctx->hist32 = c.precision == SEQ_MIXED;
     ctx->stream = (cudaStream_t)cuda_stream;
@@ -380,6 +400,24 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
         ok = ok && cudaMalloc(&ctx->used_net, 16) == cudaSuccess;     // int flag | double rho
         ok = ok && cudaMallocHost(&ctx->h_used, 16) == cudaSuccess;
     }
+    if (c.guess == SEQ_GUESS_RAND) {
+        ctx->ldo = round_up(c.basis_m, 4);
+        ctx->gseed = c.seed ^ 0x52414E44ull;
+        ok = ok && cudaMalloc(&ctx->Om, sizeof(double) * (size_t)n * ctx->ldo) == cudaSuccess;
+        ok = ok && cudaMemsetAsync(ctx->Om, 0, sizeof(double) * (size_t)n * ctx->ldo, ctx->stream) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->Zs, sizeof(double) * M * c.basis_m) == cudaSuccess;
+    }
+    if (c.guess == SEQ_GUESS_POD) {
+        ok = ok && cudaMalloc(&ctx->gpart, sizeof(double) * gram_partial_doubles()) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->gcount, sizeof(unsigned)) == cudaSuccess;
+        ok = ok && cudaMemsetAsync(ctx->gcount, 0, sizeof(unsigned), ctx->stream) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->G, sizeof(double) * kMaxM * kMaxM) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->Vk, sizeof(double) * kMaxM * kMaxM) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->lam, sizeof(double) * kMaxM) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->sweeps, sizeof(int)) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->Wp, sizeof(double) * s * (kMaxM + 1)) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->lsq_red, sizeof(LsqOut)) == cudaSuccess;
+    }
     ok = ok && cudaMalloc(&ctx->d_args, sizeof(DevArgs)) == cudaSuccess;
     ok = ok && cudaMallocHost(&ctx->h_args, sizeof(DevArgs)) == cudaSuccess;
     ok = ok && cudaMalloc(&ctx->d_args_in, sizeof(DevArgs)) == cudaSuccess;
@@ -412,7 +450,8 @@ int seq_destroy(seq_ctx* ctx) {
                         ctx->V, ctx->w, ctx->r, ctx->p, ctx->q, ctx->val32, ctx->rhs32, ctx->d,
                         ctx->d_args, ctx->d_args_in, ctx->ks, ctx->ks_in, ctx->sell_width,
                         ctx->sell_off, ctx->sell_col, ctx->sell_val, ctx->yring, ctx->sample,
-                        ctx->yhat, ctx->used_net};
+                        ctx->yhat, ctx->used_net, ctx->Om, ctx->Zs, ctx->gpart, ctx->gcount,
+                        ctx->G, ctx->Vk, ctx->lam, ctx->sweeps, ctx->Wp, ctx->lsq_red};
     for (void* p : dev_ptrs)
         if (p) cudaFree(p);
     void* host_ptrs[] = {ctx->lsq_host, ctx->h_args, ctx->h_args_in, ctx->h_ks, ctx->h_int,
@@ -427,6 +466,19 @@ int seq_destroy(seq_ctx* ctx) {
 int seq_push_solution(seq_ctx* ctx, const double* x_dev) {
     if (!ctx || !x_dev) return fail(ctx, SEQ_EINVAL, "NULL argument");
     const int slot = ctx->pushes % ctx->cfg.M;
+    if (ctx->cfg.guess == SEQ_GUESS_RAND && ctx->om_valid) {
+        // Algorithm 4, steps 6-9, fused with the push.
+        const int mb = ctx->cfg.basis_m;
+        launch_rand_push(x_dev, ctx->cfg.n, (double*)ctx->X, ctx->ldx, slot,
+                         ctx->pushes >= ctx->cfg.M, ctx->Zs, mb, ctx->gseed, ctx->gdraws, ctx->Om,
+                         ctx->ldo, ctx->stream);
+        CK(cudaGetLastError());
+        ctx->gdraws += (uint64_t)mb;
+        ctx->om_updates += 1;
+        ctx->pushes += 1;
+        ctx->launches = 2;
+        return SEQ_OK;
+    }
     if (ctx->hist32)
         launch_push_f32(x_dev, ctx->cfg.n, (float*)ctx->X, ctx->ldx, slot, ctx->stream);
     else
@@ -462,6 +514,7 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
     CK(cudaMemsetAsync(ctx->ks, 0, sizeof(KState), ctx->stream));
     int rank = 0;
     double rho = 0.0;
+    int basis_cols = m;              // columns of the reduced problem
     if (mode == SEQ_GUESS_ZERO) {
         CK(cudaMemsetAsync(x0_dev, 0, sizeof(double) * (size_t)n, ctx->stream));
     } else if (mode == SEQ_GUESS_PREV) {
@@ -471,6 +524,51 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
         else
             launch_copy_slot_f64((const double*)ctx->X, ctx->ldx, n, slot, x0_dev, ctx->stream);
         ctx->launches += 1;
+    } else if (mode == SEQ_GUESS_POD || mode == SEQ_GUESS_RAND) {
+        int* bad = &ctx->ks->bad_index;
+        const int oldest = (ctx->pushes - m) % M;
+        const int mb = c.basis_m;
+        const double* X = (const double*)ctx->X;
+        if (mode == SEQ_GUESS_POD) {
+            // Algorithm 2 in snapshot form; the reduced problem from W = S[AX|b].
+            const int kk = mb < m ? mb : m;
+            launch_sketch_f64(A->rowptr, A->colind, A->values, X, ctx->ldx, b_dev, ctx->sk, n,
+                              A->nnz, M, c.s, c.zeta, (double*)ctx->sk_partial, ctx->sk_nblk,
+                              ctx->W, bad, ctx->stream);
+            launch_pod_basis(X, ctx->ldx, n, M, m, oldest, kk, ctx->gpart, ctx->gcount, ctx->G,
+                             ctx->Vk, ctx->lam, ctx->sweeps, ctx->stream);
+            launch_pod_reduce(ctx->W, c.s, M, m, oldest, ctx->Vk, kk, ctx->Wp, ctx->stream);
+            launch_lsq(ctx->Wp, c.s, kk, kk, 0, c.rank_tol, ctx->lsq_red, ctx->stream);
+            launch_pod_coeff(ctx->lsq_red, ctx->Vk, m, kk, M, oldest, ctx->lsq, ctx->stream);
+            launch_expand_f64(X, ctx->ldx, n, M, ctx->lsq, x0_dev, ctx->stream);
+            ctx->launches += 8;
+            ctx->pod_mi = m;
+            ctx->pod_kk = kk;
+            basis_cols = kk;
+        } else {
+            // Algorithm 4: Omega from scratch when due, then the reduced problem
+            // over span(Omega).
+            if (!ctx->om_valid || ctx->om_updates >= c.refresh) {
+                launch_rand_scratch(X, ctx->ldx, n, M, m, oldest, ctx->Zs, mb, ctx->gseed,
+                                    ctx->gdraws, ctx->Om, ctx->ldo, ctx->stream);
+                ctx->gdraws += (uint64_t)m * mb;
+                ctx->om_valid = true;
+                ctx->om_updates = 0;
+                ctx->launches += 2;
+            }
+            launch_sketch_f64(A->rowptr, A->colind, A->values, ctx->Om, ctx->ldo, b_dev, ctx->sk,
+                              n, A->nnz, mb, c.s, c.zeta, (double*)ctx->sk_partial, ctx->sk_nblk,
+                              ctx->W, bad, ctx->stream);
+            launch_lsq(ctx->W, c.s, mb, mb, 0, c.rank_tol, ctx->lsq, ctx->stream);
+            launch_expand_f64(ctx->Om, ctx->ldo, n, mb, ctx->lsq, x0_dev, ctx->stream);
+            ctx->launches += 4;
+            basis_cols = mb;
+        }
+        CK(cudaMemcpyAsync(ctx->lsq_host, ctx->lsq, offsetof(LsqOut, W_logical),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(&ctx->lsq_host->rho, &ctx->lsq->rho,
+                           sizeof(LsqOut) - offsetof(LsqOut, rho), cudaMemcpyDeviceToHost,
+                           ctx->stream));
     } else {
         int* bad = &ctx->ks->bad_index;
         if (ctx->hist32) {
@@ -535,7 +633,8 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
     CK(cudaGetLastError());
     rc = read_tail(ctx, ctx->ks);
     if (rc) return rc;
-    if (mode == SEQ_GUESS_SKETCH) {
+    const bool reduced = mode == SEQ_GUESS_SKETCH || mode == SEQ_GUESS_POD || mode == SEQ_GUESS_RAND;
+    if (reduced) {
         rank = ctx->lsq_host->rank;
         rho = ctx->lsq_host->rho;
     }
@@ -549,7 +648,7 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
         info->launches = ctx->launches;
         info->net_resid = predicted ? *(const double*)(ctx->h_used + 2) : -1.0;
     }
-    ctx->lsq_host->m = (mode == SEQ_GUESS_SKETCH) ? m : 0;
+    ctx->lsq_host->m = reduced ? basis_cols : 0;
     const bool fallback = predicted && *ctx->h_used == 0;   // the network's y was rejected
     if (ctx->h_ks->bad_index) {
         if (info) info->status = SEQ_EINVAL;
@@ -724,6 +823,46 @@ int seq_last_sketch(seq_ctx* ctx, double* W_host, double* y_host) {
                       cudaMemcpyDeviceToHost));
     if (y_host && m > 0)
         CK(cudaMemcpy(y_host, ctx->lsq->y_logical, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    return SEQ_OK;
+}
+
+int seq_rand_state(seq_ctx* ctx, double* omega_host, double* Z_host, uint64_t* draws,
+                   int32_t* updates) {
+    if (!ctx) return SEQ_EINVAL;
+    if (ctx->cfg.guess != SEQ_GUESS_RAND || !ctx->om_valid)
+        return fail(ctx, SEQ_EINVAL, "no Omega: not in RAND mode or no guess yet");
+    const int n = ctx->cfg.n, M = ctx->cfg.M, mb = ctx->cfg.basis_m;
+    const int mi = seq_history_size(ctx), oldest = (ctx->pushes - mi) % M;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (omega_host)
+        CK(cudaMemcpy2D(omega_host, sizeof(double) * mb, ctx->Om, sizeof(double) * ctx->ldo,
+                        sizeof(double) * mb, n, cudaMemcpyDeviceToHost));
+    if (Z_host) {
+        std::vector<double> z((size_t)M * mb);
+        CK(cudaMemcpy(z.data(), ctx->Zs, sizeof(double) * z.size(), cudaMemcpyDeviceToHost));
+        for (int l = 0; l < mi; ++l)
+            memcpy(Z_host + (size_t)l * mb, z.data() + (size_t)((oldest + l) % M) * mb, sizeof(double) * mb);
+    }
+    if (draws) *draws = ctx->gdraws;
+    if (updates) *updates = ctx->om_updates;
+    return SEQ_OK;
+}
+
+int seq_pod_state(seq_ctx* ctx, double* V_host, double* lam_host, int32_t* dims) {
+    if (!ctx) return SEQ_EINVAL;
+    if (ctx->cfg.guess != SEQ_GUESS_POD) return fail(ctx, SEQ_EINVAL, "not in POD mode");
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int mi = ctx->pod_mi, kk = ctx->pod_kk;
+    if (V_host && mi > 0)
+        CK(cudaMemcpy(V_host, ctx->Vk, sizeof(double) * mi * kk, cudaMemcpyDeviceToHost));
+    if (lam_host && mi > 0)
+        CK(cudaMemcpy(lam_host, ctx->lam, sizeof(double) * mi, cudaMemcpyDeviceToHost));
+    if (dims) {
+        dims[0] = mi;
+        dims[1] = kk;
+        dims[2] = 0;
+        if (mi > 0) CK(cudaMemcpy(&dims[2], ctx->sweeps, sizeof(int), cudaMemcpyDeviceToHost));
+    }
     return SEQ_OK;
 }
 

@@ -39,6 +39,21 @@ void launch_copy_slot_f32(const float* X, int ldx, int n, int slot, double* x0, 
 void launch_push_f64(const double* x, int n, double* X, int ldx, int slot, cudaStream_t st);
 void launch_push_f32(const double* x, int n, float* X, int ldx, int slot, cudaStream_t st);
 
+// basis.cu: POD (Algorithm 2) and randomised range finder (Algorithm 4)
+int gram_grid();
+size_t gram_partial_doubles();
+void launch_rand_scratch(const double* X, int ldx, int n, int M, int mi, int oldest, double* Zs, int m,
+                         uint64_t gseed, uint64_t start, double* Om, int ldo, cudaStream_t st);
+void launch_rand_push(const double* x, int n, double* X, int ldx, int slot, int remove, double* Zs,
+                      int m, uint64_t gseed, uint64_t start, double* Om, int ldo, cudaStream_t st);
+void launch_pod_basis(const double* X, int ldx, int n, int M, int mi, int oldest, int kk,
+                      double* partial, unsigned* counter, double* G, double* Vk, double* lam,
+                      int* sweeps, cudaStream_t st);
+void launch_pod_reduce(const double* W, int s, int M, int mi, int oldest, const double* Vk, int kk,
+                       double* Wp, cudaStream_t st);
+void launch_pod_coeff(const LsqOut* red, const double* Vk, int mi, int kk, int M, int oldest,
+                      LsqOut* out, cudaStream_t st);
+
 // krylov.cu
 int stream_grid(int n);
 // ||b - A x|| and ||b|| of FP64 vectors; results in st->beta, st->bnorm and

@@ -1,0 +1,199 @@
+"""POD (Algorithm 2) and randomised range finder (Algorithm 4) guesses on the
+GPU against oracle/basis.py.
+
+Tolerances:
+* Gaussian draws: the same counter-based Box-Muller definition on both sides;
+  log and cos may differ in the last bit, so Z agrees to 1e-14 absolute.
+* Omega after progressive updates: the same operations in the same order (the
+  GPU fuses the down- and up-date into two FMAs), relative 1e-12.
+* Guesses on well-conditioned histories (Gaussian columns, or prescribed
+  well-separated singular values): x0 and the sketched residual to 1e-9
+  (least-squares perturbation theory with cond ~1e2 on top of the 1e-11
+  agreement of the sketched block).
+* POD eigenpairs: the eigenvalues of X^T X to 1e-13 of the largest (Weyl's
+  bound for a Gram matrix rounded at ~u ||G||); the eigenvector subspace (gap
+  ratio >= 2) to 1e-10.
+* On solution histories (ill-conditioned, Theorem 1) the comparison is on the
+  true guess residual, relative 1e-3, as for the whole-span guess.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import basis, krylov, method, sketch
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+SEED = 0x5EEDBA5E
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_02156_gb300 as sa
+    sa.load()
+    yield
+
+
+def _sa():
+    import paper_2309_02156_gb300 as sa
+    return sa
+
+
+def _t(x, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device=DEV, dtype=dtype)
+
+
+def _gpu_system(p, i):
+    rowptr, colind, vals, b = workloads.csr_system(p, i)
+    A = _sa().CSR(_t(rowptr, torch.int32), _t(colind, torch.int32), _t(vals))
+    return A, _t(b), krylov.csr(rowptr, colind, vals, p.n), b
+
+
+@pytest.mark.parametrize("M,m,refresh,steps", [(6, 4, 3, 14), (5, 5, 50, 9), (8, 3, 2, 12)])
+def test_rand_matches_oracle_through_updates_and_refreshes(M, m, refresh, steps):
+    p = workloads.plain_nonsym(24)
+    rng = np.random.default_rng(M * 10 + m)
+    cols = [rng.standard_normal(p.n) for _ in range(steps)]
+    seq = _sa().Sequence(p.n, M, 40, zeta=8, seed=SEED, guess="rand", basis_m=m, refresh=refresh)
+    S = sketch.sparse_sign_matrix(p.n, 40, 8, SEED)
+    rrf = basis.RandRangeFinder(m, refresh, SEED)
+    hist = method.History(p.n, M)
+    for k, c in enumerate(cols):
+        leaving = hist.cols[0] if len(hist.cols) == M else None
+        rrf.on_push(c, leaving)
+        hist.push(c)
+        seq.push(_t(c))
+        A, bd, A_ref, b = _gpu_system(p, 3 + k)
+        x0 = torch.empty(p.n, dtype=torch.float64, device=DEV)
+        info = seq.guess(A, bd, x0)
+        ref = basis.rand_guess(A_ref, b, rrf, hist.matrix(), S)
+        om, Z, draws, updates = seq.rand_state()
+        assert draws == rrf.counter and updates == rrf.updates
+        assert np.abs(Z - rrf.Zmat()).max() <= 1e-14 * max(1.0, np.abs(Z).max())
+        assert np.linalg.norm(om - rrf.omega) <= 1e-12 * np.linalg.norm(rrf.omega)
+        assert info["history_cols"] == len(hist.cols) and info["rank"] == ref.rank
+        x0 = x0.cpu().numpy()
+        assert np.linalg.norm(x0 - ref.x0) <= 1e-9 * np.linalg.norm(ref.x0)
+        assert info["sketch_resid"] == pytest.approx(ref.rho_s, rel=1e-9)
+        assert info["guess_relres"] == pytest.approx(method.relres(A_ref, b, ref.x0), rel=1e-9)
+    seq.close()
+
+
+def _separated_history(n, M, seed):
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((n, M)))
+    V, _ = np.linalg.qr(rng.standard_normal((M, M)))
+    sig = 0.5 ** np.arange(M)
+    return U @ np.diag(sig) @ V.T, sig, V
+
+
+@pytest.mark.parametrize("M,m,extra", [(8, 3, 0), (10, 10, 4), (6, 1, 2)])
+def test_pod_matches_oracle_on_separated_spectrum(M, m, extra):
+    p = workloads.plain_nonsym(24)
+    Xh, sig, Vr = _separated_history(p.n, M, M + m)
+    rng = np.random.default_rng(1)
+    pre = [rng.standard_normal(p.n) for _ in range(extra)]       # pushed out of the ring
+    seq = _sa().Sequence(p.n, M, 48, zeta=8, seed=SEED, guess="pod", basis_m=m)
+    for c in pre + [Xh[:, l] for l in range(M)]:
+        seq.push(_t(c))
+    A, bd, A_ref, b = _gpu_system(p, 4)
+    x0 = torch.empty(p.n, dtype=torch.float64, device=DEV)
+    info = seq.guess(A, bd, x0)
+    S = sketch.sparse_sign_matrix(p.n, 48, 8, SEED)
+    ref = basis.pod_guess(A_ref, b, Xh, m, S)
+    V, lam, sweeps = seq.pod_state()
+    assert V.shape == (M, m) and 0 < sweeps < 40
+    # Weyl: rounding of G by ~u ||G|| moves every eigenvalue by at most that much
+    assert np.abs(lam[:m] - sig[:m] ** 2).max() <= 1e-13 * sig[0] ** 2
+    # eigenvector subspace = leading right singular vectors
+    Pv = V @ V.T
+    Pr = Vr[:, :m] @ Vr[:, :m].T
+    assert np.abs(Pv - Pr).max() <= 1e-10
+    x0 = x0.cpu().numpy()
+    assert np.linalg.norm(x0 - ref.x0) <= 1e-9 * np.linalg.norm(ref.x0)
+    assert info["sketch_resid"] == pytest.approx(ref.rho_s, rel=1e-9)
+    assert info["history_cols"] == M and info["rank"] == ref.rank
+    seq.close()
+
+
+def _oracle_history(p, upto, M, tol):
+    S = sketch.sparse_sign_matrix(p.n, 40, 8, 77)
+    h = method.History(p.n, M)
+    xs = []
+    for i in range(upto):
+        rowptr, colind, vals, b = workloads.csr_system(p, i)
+        out = method.solve_step(krylov.csr(rowptr, colind, vals, p.n), b, h, S, tol, "gmres",
+                                max_iters=50000)
+        xs.append(out["x"])
+    return xs
+
+
+@pytest.mark.parametrize("mode,m", [("pod", 5), ("rand", 5), ("pod", 10)])
+def test_compressed_guess_on_solution_history(mode, m):
+    """Ill-conditioned history (the oracle's own solutions): the true residuals
+    of the GPU and oracle guesses agree, and neither beats the whole span."""
+    p = workloads.plain_nonsym(32)
+    M = 10
+    xs = _oracle_history(p, M + 3, M, 1e-10)
+    seq = _sa().Sequence(p.n, M, 40, zeta=8, seed=SEED, guess=mode, basis_m=m)
+    S = sketch.sparse_sign_matrix(p.n, 40, 8, SEED)
+    rrf = basis.RandRangeFinder(m, 50, SEED)
+    hist = method.History(p.n, M)
+    for c in xs:
+        rrf.on_push(c, hist.cols[0] if len(hist.cols) == M else None)
+        hist.push(c)
+        seq.push(_t(c))
+    A, bd, A_ref, b = _gpu_system(p, M + 3)
+    x0 = torch.empty(p.n, dtype=torch.float64, device=DEV)
+    info = seq.guess(A, bd, x0)
+    X = hist.matrix()
+    ref = basis.pod_guess(A_ref, b, X, m, S) if mode == "pod" else basis.rand_guess(A_ref, b, rrf, X, S)
+    full = method.sketched_guess(A_ref, b, X, S)
+    r_gpu = method.relres(A_ref, b, x0.cpu().numpy())
+    r_ref = method.relres(A_ref, b, ref.x0)
+    assert r_gpu == pytest.approx(r_ref, rel=1e-3)
+    assert info["guess_relres"] == pytest.approx(r_gpu, rel=1e-6)
+    assert info["sketch_resid"] >= full.rho_s * (1 - 1e-6)
+    seq.close()
+
+
+@pytest.mark.parametrize("mode", ["pod", "rand"])
+def test_compressed_sequence_converges(mode):
+    """A 40-system GMRES sequence through the C-ABI in each mode: every system
+    reaches the tolerance (checked with the oracle's SpMV), and the compressed
+    guess beats the previous-solution guess on average."""
+    p = workloads.plain_nonsym(32)
+    M, m = 10, 5
+    seq = _sa().Sequence(p.n, M, 40, zeta=8, seed=SEED, guess=mode, basis_m=m, refresh=7)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    prev = None
+    ratios = []
+    for i in range(40):
+        A, bd, A_ref, b = _gpu_system(p, i)
+        g = seq.guess(A, bd, x)
+        if prev is not None and i >= M:
+            ratios.append(g["guess_relres"] / method.relres(A_ref, b, prev))
+        info = seq.solve(A, bd, 1e-10, x)
+        xh = x.cpu().numpy()
+        assert info["status"] == 0
+        assert method.relres(A_ref, b, xh) <= 1e-10 * (1 + 1e-9)
+        seq.push(x)
+        prev = xh
+    assert np.exp(np.mean(np.log(ratios))) < 0.1
+    seq.close()
+
+
+def test_compressed_config_checks():
+    sa = _sa()
+    for kw in ({"guess": "pod", "basis_m": 0}, {"guess": "rand", "basis_m": 11},
+               {"guess": "pod", "basis_m": 3, "precision": "mixed"}, {"guess": "rand", "basis_m": 2, "refresh": -1}):
+        with pytest.raises(sa.SeqError):
+            sa.Sequence(100, 10, 40, **kw)
+    seq = sa.Sequence(100, 10, 40, guess="rand", basis_m=3)
+    with pytest.raises(sa.SeqError):
+        seq.rand_state()          # no Omega before the first guess
+    seq.close()
