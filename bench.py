@@ -462,6 +462,133 @@ def learned_ablation(args):
     net.close()
 
 
+def guess_modes(args):
+    """Guess modes compared on identical histories (the comparison of the
+    paper's Section 4 experiment on the 1024 x 1024 sequence): the previous
+    solution (the paper's baseline), Algorithm 1 over the whole span (sketched),
+    POD (Algorithm 2) and the randomised range finder (Algorithm 4, refresh 50),
+    m = args.basis_m.  A driver context (whole span) primes and advances the
+    history; at each timed step every mode guesses from the same history and
+    solves from its own guess (GMRES(30) to 1e-8, FP64); the driver's solution
+    is pushed into all contexts.  Prints one JSON line."""
+    import numpy as np
+    import torch
+    import paper_2309_02156_gb300 as sa
+    import workloads
+    K = args.modes_steps
+    dev = torch.device("cuda", 0)
+    total = M_HIST + K
+    host = generate(list(range(total)))
+    rowptr, colind, _ = workloads.pattern(N_GRID)
+    rp = torch.from_numpy(rowptr).to(dev)
+    ci = torch.from_numpy(colind).to(dev)
+    n = N_GRID * N_GRID
+    mk = lambda g, **kw: sa.Sequence(n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, guess=g, krylov="gmres",
+                                     restart=RESTART, max_iters=200000, **kw)
+    modes = {"prev": mk("prev"), "sketch": mk("sketch"),
+             "pod": mk("pod", basis_m=args.basis_m), "rand": mk("rand", basis_m=args.basis_m, refresh=50)}
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    rec = {k: {"iters": [], "guess": [], "guess_ms": [], "solve_ms": []} for k in modes}
+    for i in range(total):
+        v = torch.from_numpy(host[i][0]).to(dev)
+        b = torch.from_numpy(host[i][1]).to(dev)
+        A = sa.CSR(rp, ci, v)
+        timed = i >= M_HIST
+        if timed:
+            for k, ctx in modes.items():
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                torch.cuda.synchronize()
+                ev[0].record(stream)
+                g = ctx.guess(A, b, y)
+                ev[1].record(stream)
+                info = ctx.solve(A, b, TOL, y)
+                ev[2].record(stream)
+                torch.cuda.synchronize()
+                r = rec[k]
+                r["iters"].append(info["iters"])
+                r["guess"].append(g["guess_relres"])
+                r["guess_ms"].append(ev[0].elapsed_time(ev[1]))
+                r["solve_ms"].append(ev[1].elapsed_time(ev[2]))
+                if k == "sketch":
+                    x.copy_(y)              # the whole-span solution advances every history
+        else:
+            for k, ctx in modes.items():
+                if k == "sketch":
+                    ctx.guess(A, b, x)
+                    ctx.solve(A, b, TOL, x)
+            for k, ctx in modes.items():
+                if k != "sketch":
+                    ctx.guess(A, b, y)      # keeps each mode's state in step (RAND: Omega)
+        for ctx in modes.values():
+            ctx.push(x)
+    for ctx in modes.values():
+        ctx.close()
+    gm = lambda v: float(np.exp(np.mean(np.log(np.maximum(np.asarray(v, dtype=np.float64), 1e-300)))))
+    out = {"guess_modes": True, "workload": WORKLOAD, "basis_m": args.basis_m, "steps": K,
+           "modes": {k: {"iters_mean": float(np.mean(r["iters"])),
+                         "guess_relres_geomean": gm(r["guess"]),
+                         "guess_ms_mean": float(np.mean(r["guess_ms"])),
+                         "solve_ms_mean": float(np.mean(r["solve_ms"])),
+                         "systems_per_s": 1e3 * K / (sum(r["guess_ms"]) + sum(r["solve_ms"]))}
+                     for k, r in rec.items()}}
+    print(json.dumps(out), flush=True)
+
+
+def e1_sequence(args):
+    """The paper's Section 4 test sequence (workloads/e1.py): N x N fourth-order
+    discretisation of div(a grad f) = g, t0 = 2.3, `steps` systems, GMRES(30)
+    to 1e-7, unpreconditioned (the paper uses ILU, so the iteration counts are
+    not those of its Figure 1).  For each of dt = 1e-5 (M = 20, m = 10) and
+    dt = 1e-3 (M = 31, m = 20: the paper's M = 35 exceeds this library's
+    M <= 31), every guess mode runs its own sequence.  Prints one JSON line."""
+    import numpy as np
+    import torch
+    import paper_2309_02156_gb300 as sa
+    from workloads import e1
+    dev = torch.device("cuda", 0)
+    N, steps, tol = args.e1_grid, args.e1_steps, 1e-7
+    rowptr, colind = e1.pattern(N)
+    rp = torch.from_numpy(rowptr).to(dev)
+    ci = torch.from_numpy(colind).to(dev)
+    n = N * N
+    out = {"e1": True, "grid": N, "steps": steps, "tol": tol, "runs": []}
+    for dt, M, m in ((1e-5, 20, 10), (1e-3, 31, 20)):
+        p = e1.E1Params(N=N, dt=dt)
+        sysv = [e1.system(p, k, rowptr, colind) for k in range(steps)]
+        vals = [torch.from_numpy(v[2]).to(dev) for v in sysv]
+        bs = [torch.from_numpy(v[3]).to(dev) for v in sysv]
+        fx = [v[4] for v in sysv]
+        run = {"dt": dt, "M": M, "m": m, "modes": {}}
+        for mode in ("prev", "sketch", "pod", "rand"):
+            kw = {"basis_m": m, "refresh": 50} if mode in ("pod", "rand") else {}
+            seq = sa.Sequence(n, M, 80, zeta=ZETA, seed=SEED, guess=mode, krylov="gmres",
+                              restart=RESTART, max_iters=500000, **kw)
+            x = torch.zeros(n, dtype=torch.float64, device=dev)
+            its, zero, errs = [], 0, []
+            torch.cuda.synchronize()
+            t0 = time.time()
+            for k in range(steps):
+                A = sa.CSR(rp, ci, vals[k])
+                seq.guess(A, bs[k], x)
+                info = seq.solve(A, bs[k], tol, x)
+                its.append(info["iters"])
+                zero += info["iters"] == 0
+                seq.push(x)
+                if k % 50 == 0:
+                    errs.append(float(np.abs(x.cpu().numpy() - fx[k]).max() / np.abs(fx[k]).max()))
+            torch.cuda.synchronize()
+            wall = time.time() - t0
+            seq.close()
+            run["modes"][mode] = {"iters_mean": float(np.mean(its)), "iters_total": int(np.sum(its)),
+                                  "zero_iteration_steps": int(zero), "seconds": wall,
+                                  "iters_first10": its[:10], "iters_last10": its[-10:],
+                                  "max_rel_error_vs_f_sampled": max(errs)}
+        out["runs"].append(run)
+    print(json.dumps(out), flush=True)
+
+
 def _gen_nonsym(job):
     import workloads
     N, i = job
@@ -556,6 +683,12 @@ def main():
     ap.add_argument("--iters-per-system", type=float, default=0.0)
     ap.add_argument("--gmres-iters", type=int, default=120)
     ap.add_argument("--profile-run", type=int, default=0, metavar="ITERS")
+    ap.add_argument("--e1", action="store_true")
+    ap.add_argument("--e1-grid", type=int, default=100)
+    ap.add_argument("--e1-steps", type=int, default=200)
+    ap.add_argument("--guess-modes", action="store_true")
+    ap.add_argument("--modes-steps", type=int, default=8)
+    ap.add_argument("--basis-m", type=int, default=10)
     ap.add_argument("--precision-form", action="store_true")
     ap.add_argument("--precision-kind", default="mixed", choices=["mixed", "mixed_krylov", "f64"])
     ap.add_argument("--precision-grid", type=int, default=2048)
@@ -574,6 +707,12 @@ def main():
         return
     if args.precision_form:
         precision_form(args)
+        return
+    if args.guess_modes:
+        guess_modes(args)
+        return
+    if args.e1:
+        e1_sequence(args)
         return
     if args.profile_run:
         profile_run(args.profile_run)
