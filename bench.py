@@ -224,11 +224,12 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def profile_run(iters: int) -> None:
-    """A bounded full-size command for ncu: one sketched guess from a synthetic
-    20-column history and `iters` GMRES(30) iterations on system 23 of the
-    1024 x 1024 sequence (about 12 launches per 4 Arnoldi steps), so that a
-    profiler can capture every launch of the run."""
+def profile_run(iters: int, precision: str = "f64", guess: str = "sketch") -> None:
+    """A bounded full-size command for ncu: one guess (`guess` mode; m = 10 for
+    POD / RAND) from a synthetic 20-column history and `iters` GMRES(30)
+    iterations (`precision`: f64, or mixed_krylov = FP32 inner iterations) on
+    system 23 of the 1024 x 1024 sequence, so that a profiler can capture every
+    launch of the run."""
     import numpy as np
     import torch
     import paper_2309_02156_gb300 as sa
@@ -239,8 +240,9 @@ def profile_run(iters: int) -> None:
     A = sa.CSR(torch.from_numpy(rowptr).to(dev), torch.from_numpy(colind).to(dev),
                torch.from_numpy(vals).to(dev))
     bd = torch.from_numpy(b).to(dev)
+    kw = {"basis_m": 10} if guess in ("pod", "rand") else {}
     seq = sa.Sequence(p.n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, krylov="gmres",
-                      restart=RESTART, max_iters=iters)
+                      restart=RESTART, max_iters=iters, precision=precision, guess=guess, **kw)
     rng = np.random.default_rng(1)
     for _ in range(M_HIST):
         seq.push(torch.from_numpy(rng.standard_normal(p.n)).to(dev))
@@ -253,7 +255,7 @@ def profile_run(iters: int) -> None:
     seq.close()
 
 
-def batched_form(K, W, hbm_peak):
+def batched_form(K, W, hbm_peak, count=512):
     """512 independent SPD sequences (grid side 48..384, M = 12, s = 48), FP32 CG
     inside FP64 refinement to 1e-8, one persistent launch per time step (CUDA
     graph).  Systems are assembled on the device between timed steps."""
@@ -263,7 +265,7 @@ def batched_form(K, W, hbm_peak):
     import workloads
     from workloads.torch_pde import BatchedSystems
     dev = torch.device("cuda", torch.cuda.current_device())
-    ps = workloads.batched_params(512, SEED)
+    ps = workloads.batched_params(count, SEED)
     gen = BatchedSystems(ps, dev)
     pats = [(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)) for rp, ci in gen.patterns]
     M, S = 12, 48
@@ -309,9 +311,9 @@ def batched_form(K, W, hbm_peak):
     secs = total_ms / 1e3
     flat = [f for infos in infos_all for f in infos]
     return {
-        "form": "batched: 512 SPD sequences (N 48..384, sum n = %d), M = 12, s = 48, FP32 CG "
-                "inside FP64 refinement to 1e-8, one persistent launch per step" % int(n.sum()),
-        "value": 512 * K / secs, "unit": "systems/s", "ms_per_step": total_ms / K,
+        "form": "batched: %d SPD sequences (N 48..384, sum n = %d), M = 12, s = 48, FP32 CG "
+                "inside FP64 refinement to 1e-8, one persistent launch per step" % (count, int(n.sum())),
+        "value": count * K / secs, "unit": "systems/s", "ms_per_step": total_ms / K,
         "schedule": chosen, "iters_mean": float(np.mean([f["iters"] for f in flat])),
         "refinements_mean": float(np.mean([f["refinements"] for f in flat])),
         "final_relres_max": max(f["final_relres"] for f in flat),
@@ -683,6 +685,10 @@ def main():
     ap.add_argument("--iters-per-system", type=float, default=0.0)
     ap.add_argument("--gmres-iters", type=int, default=120)
     ap.add_argument("--profile-run", type=int, default=0, metavar="ITERS")
+    ap.add_argument("--profile-precision", default="f64", choices=["f64", "mixed_krylov"])
+    ap.add_argument("--profile-guess", default="sketch", choices=["sketch", "pod", "rand"])
+    ap.add_argument("--batched-only", action="store_true")
+    ap.add_argument("--batched-count", type=int, default=512)
     ap.add_argument("--e1", action="store_true")
     ap.add_argument("--e1-grid", type=int, default=100)
     ap.add_argument("--e1-steps", type=int, default=200)
@@ -715,7 +721,13 @@ def main():
         e1_sequence(args)
         return
     if args.profile_run:
-        profile_run(args.profile_run)
+        profile_run(args.profile_run, args.profile_precision, args.profile_guess)
+        return
+    if args.batched_only:
+        import torch
+        hbm_peak, _ = peaks()
+        torch.cuda.set_device(0)
+        print(json.dumps(batched_form(args.batched_steps, args.warmup, hbm_peak, args.batched_count)))
         return
     if args.cpu_baseline_worker:
         cpu_baseline_worker(args.iters_per_system, args.gmres_iters)
