@@ -15,6 +15,12 @@ already meets the tolerance, Sections 4 and 5) can happen.  Conventions shared w
   Givens rotations with r = hypot(a, b), inner stop when |g_{j+1}| <= tol ||b||,
   happy breakdown when h_{j+1,j} <= 1e-14 ||h_{:,j}||, and the true residual
   recomputed at every restart;
+* preconditioned GMRES (optional): right preconditioning, GMRES on A M^{-1}
+  with x = x0 + M^{-1} V y, so the minimised residual is the true one and the
+  stopping test is unchanged; M^{-1} = a fixed number of damped Jacobi sweeps
+  on A z = u from z = 0 (a polynomial in D^{-1} A times D^{-1}; Jacobi and
+  polynomial preconditioners are the GPU-friendly members of the family the
+  paper's runs use, ILU and AMG, Sections 4-5);
 * mixed refinement: r = b - A64 x in FP64; the correction d solves
   A32 d = r / ||r|| by the same solver run entirely in float32, to a relative
   residual max(inner_tol, theta * tol ||b|| / ||r||); x += ||r|| d in FP64.
@@ -78,11 +84,30 @@ def cg(A, b, x, tol: float, max_iters: int):
         p = r + beta * p
 
 
-def gmres(A, b, x, tol: float, restart: int, max_iters: int, record=None):
-    """Restarted GMRES with CGS2 Arnoldi from x.  Returns (x, iters, relres, status).
+def jacobi_sweeps(A, sweeps: int, omega: float):
+    """M^{-1} u = the result of `sweeps` damped Jacobi sweeps on A z = u from
+    z = 0:  z_1 = omega D^{-1} u,  z_{k+1} = z_k + omega D^{-1} (u - A z_k),
+    with D = diag(A) in A's precision.  Equals sum_{k<sweeps} (I - omega
+    D^{-1} A)^k omega D^{-1} (a fixed linear operator).  sweeps = 0: identity."""
+    if sweeps <= 0:
+        return None
+    dinv = 1.0 / A.diagonal()
+    om = dinv.dtype.type(omega)
+
+    def minv(u):
+        z = (om * dinv) * u
+        for _ in range(sweeps - 1):
+            z = z + (om * dinv) * (u - A @ z)
+        return z
+    return minv
+
+
+def gmres(A, b, x, tol: float, restart: int, max_iters: int, record=None, minv=None):
+    """Restarted GMRES with CGS2 Arnoldi from x, right-preconditioned by the
+    linear operator `minv` when given.  Returns (x, iters, relres, status).
 
     ``record`` (optional list) receives (V, Hbar) of every cycle, for tests of
-    the Arnoldi relation.
+    the Arnoldi relation (of A M^{-1} when preconditioned).
     """
     dt = b.dtype
     x = x.astype(dt, copy=True)
@@ -107,7 +132,7 @@ def gmres(A, b, x, tol: float, restart: int, max_iters: int, record=None):
         V[:, 0] = r / dt.type(beta)
         k = 0
         for j in range(restart):
-            w = A @ V[:, j]
+            w = A @ (V[:, j] if minv is None else minv(V[:, j]))
             h1 = V[:, :j + 1].T @ w
             w = w - V[:, :j + 1] @ h1
             h2 = V[:, :j + 1].T @ w
@@ -145,12 +170,13 @@ def gmres(A, b, x, tol: float, restart: int, max_iters: int, record=None):
             yk[i] = (g[i] - np.dot(H[i, i + 1:k], yk[i + 1:k])) / H[i, i]
         if record is not None:
             record.append((V[:, :k + 1].copy(), Hbar[:k + 1, :k].copy()))
-        x = x + V[:, :k] @ yk.astype(dt)
+        step = V[:, :k] @ yk.astype(dt)
+        x = x + (step if minv is None else minv(step))
 
 
 def mixed_refine(A64, A32, b, x, tol: float, inner: str, restart: int,
                  max_iters: int, inner_tol: float = 1e-2, theta: float = 0.5,
-                 max_refinements: int = 100):
+                 max_refinements: int = 100, precond=None):
     """FP32-inner / FP64-outer iterative refinement.  Returns
     (x, inner_iterations, refinements, relres, status)."""
     x = x.astype(np.float64, copy=True)
@@ -172,7 +198,8 @@ def mixed_refine(A64, A32, b, x, tol: float, inner: str, restart: int,
         if inner == "cg":
             d, it, _, st = cg(A32, rhs32, d0, itol, budget)
         else:
-            d, it, _, st = gmres(A32, rhs32, d0, itol, restart, budget)
+            minv = jacobi_sweeps(A32, *precond) if precond else None
+            d, it, _, st = gmres(A32, rhs32, d0, itol, restart, budget, minv=minv)
         total += it
         refinements += 1
         if st == BREAKDOWN:

@@ -91,7 +91,8 @@ def relres(A, b, x) -> float:
 
 
 def solve_step(A, b, hist: History, S, tol: float, krylov_kind: str,
-               guess: str = "sketch", restart: int = 30, max_iters: int = 30000):
+               guess: str = "sketch", restart: int = 30, max_iters: int = 30000,
+               precond=None):
     """One system of the sequence: guess, Krylov solve, push.  Returns a dict."""
     X = hist.matrix()
     if guess == "sketch":
@@ -107,7 +108,8 @@ def solve_step(A, b, hist: History, S, tol: float, krylov_kind: str,
     if krylov_kind == "cg":
         x, it, rel, st = krylov.cg(A, b, x0, tol, max_iters)
     else:
-        x, it, rel, st = krylov.gmres(A, b, x0, tol, restart, max_iters)
+        minv = krylov.jacobi_sweeps(A, *precond) if precond else None
+        x, it, rel, st = krylov.gmres(A, b, x0, tol, restart, max_iters, minv=minv)
     hist.push(x)
     return {"x": x, "x0": x0, "guess_relres": r0, "iters": it, "relres": rel,
             "status": st, "rank": g.rank if g else 0, "rho_s": g.rho_s if g else 0.0,

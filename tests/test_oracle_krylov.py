@@ -135,3 +135,71 @@ def test_arnoldi_relation_on_stiff_operator():
     lhs = A @ V[:, :30]
     assert np.linalg.norm(lhs - V @ Hbar) <= 1e-14 * np.linalg.norm(lhs)
     assert np.abs(V.T @ V - np.eye(31)).max() < 1e-13
+
+
+# ---- right preconditioning by damped Jacobi sweeps --------------------------
+
+def _nonsym(N=12, i=3):
+    import workloads
+    p = workloads.plain_nonsym(N)
+    rowptr, colind, vals, b = workloads.csr_system(p, i)
+    return krylov.csr(rowptr, colind, vals, p.n), b
+
+
+def test_jacobi_sweeps_one_sweep_is_scaled_jacobi():
+    A, b = _nonsym()
+    minv = krylov.jacobi_sweeps(A, 1, 0.8)
+    np.testing.assert_array_equal(minv(b), (0.8 * (1.0 / A.diagonal())) * b)
+    assert krylov.jacobi_sweeps(A, 0, 0.8) is None
+
+
+@pytest.mark.parametrize("d,omega", [(2, 0.8), (5, 0.7), (8, 1.0)])
+def test_jacobi_sweeps_equal_the_neumann_polynomial(d, omega):
+    """The recurrence equals sum_{k<d} (I - omega D^-1 A)^k omega D^-1."""
+    A, b = _nonsym(8)
+    Ad = A.toarray()
+    n = Ad.shape[0]
+    Dinv = np.diag(1.0 / np.diag(Ad))
+    T = np.eye(n) - omega * Dinv @ Ad
+    P = np.zeros((n, n))
+    Tk = np.eye(n)
+    for _ in range(d):
+        P += Tk @ (omega * Dinv)
+        Tk = Tk @ T
+    u = np.random.default_rng(d).standard_normal(n)
+    got = krylov.jacobi_sweeps(A, d, omega)(u)
+    np.testing.assert_allclose(got, P @ u, rtol=1e-12, atol=1e-12 * np.abs(P @ u).max())
+
+
+def test_jacobi_sweeps_converge_to_the_inverse_on_a_dominant_matrix():
+    rng = np.random.default_rng(3)
+    n = 40
+    M = rng.standard_normal((n, n)) * 0.1
+    M += np.diag(np.abs(M).sum(axis=1) + 1.0)          # strictly diagonally dominant
+    import scipy.sparse as sp
+    A = sp.csr_matrix(M)
+    u = rng.standard_normal(n)
+    z = krylov.jacobi_sweeps(A, 300, 1.0)(u)
+    np.testing.assert_allclose(z, np.linalg.solve(M, u), rtol=1e-12, atol=1e-12)
+
+
+def test_preconditioned_gmres_exact_inverse_takes_one_iteration():
+    A, b = _nonsym(10)
+    lu = scipy.sparse.linalg.splu(A.tocsc())
+    x, it, rel, st = krylov.gmres(A, b, np.zeros_like(b), 1e-10, 30, 100, minv=lu.solve)
+    assert st == krylov.CONVERGED and it == 1 and rel <= 1e-10
+
+
+def test_preconditioned_gmres_arnoldi_relation_and_gain():
+    A, b = _nonsym(24)
+    minv = krylov.jacobi_sweeps(A, 4, 0.8)
+    rec = []
+    x, it, rel, st = krylov.gmres(A, b, np.zeros_like(b), 1e-10, 30, 20000, record=rec, minv=minv)
+    assert st == krylov.CONVERGED
+    assert np.linalg.norm(b - A @ x) <= 1e-10 * np.linalg.norm(b) * (1 + 1e-9)
+    V, Hbar = rec[0]
+    k = Hbar.shape[1]
+    AMV = np.column_stack([A @ minv(V[:, c]) for c in range(k)])
+    assert np.linalg.norm(AMV - V @ Hbar) <= 1e-12 * np.linalg.norm(AMV)
+    _, it0, _, st0 = krylov.gmres(A, b, np.zeros_like(b), 1e-10, 30, 20000)
+    assert st0 == krylov.CONVERGED and it < it0
