@@ -591,6 +591,69 @@ def e1_sequence(args):
     print(json.dumps(out), flush=True)
 
 
+def precond_form(args):
+    """The 1024 x 1024 sequence with right-preconditioned GMRES(30) (M^{-1} =
+    `sweeps` damped Jacobi sweeps, omega 0.8), in FP64 and in the mixed form
+    (FP32 inner solves in FP64 refinement), to rel-res 1e-8; sketched guess
+    M = 20, s = 80.  M + W priming systems, then K timed steps (guess + solve +
+    push, CUDA events).  Prints one JSON line."""
+    import numpy as np
+    import torch
+    import paper_2309_02156_gb300 as sa
+    import workloads
+    K, W, d = args.steps, args.warmup, args.precond_sweeps
+    total = M_HIST + W + K
+    host = generate(list(range(total)))
+    dev = torch.device("cuda", 0)
+    rowptr, colind, _ = workloads.pattern(N_GRID)
+    rp = torch.from_numpy(rowptr).to(dev)
+    ci = torch.from_numpy(colind).to(dev)
+    n = N_GRID * N_GRID
+    vals = {i: torch.from_numpy(host[i][0]).to(dev) for i in range(total)}
+    bs = {i: torch.from_numpy(host[i][1]).to(dev) for i in range(total)}
+    stream = torch.cuda.current_stream()
+    out = {"precond_form": True, "workload": WORKLOAD.replace("GMRES(30)", "right-preconditioned GMRES(30)"),
+           "sweeps": d, "omega": 0.8, "steps": K, "forms": {}}
+    for prec in ("f64", "mixed_krylov"):
+        seq = sa.Sequence(n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, krylov="gmres", restart=RESTART,
+                          max_iters=200000, precision=prec, precond_sweeps=d)
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        rec = []
+
+        def step(i):
+            A = sa.CSR(rp, ci, vals[i])
+            seq.guess(A, bs[i], x)
+            info = seq.solve(A, bs[i], TOL, x)
+            seq.push(x)
+            return info
+        for i in range(M_HIST + W):
+            step(i)
+        seq.set_profiling(True)
+        seq.kernel_stats(reset=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(M_HIST + W, total):
+            rec.append(step(i))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        stats = seq.kernel_stats(reset=True)
+        seq.close()
+        tot_ms = sum(v["ms"] for v in stats.values()) or 1.0
+        out["forms"][prec] = {
+            "value": 1e3 * K / ms, "unit": "systems/s", "ms_per_step": ms / K,
+            "iters_per_system": float(np.mean([r["iters"] for r in rec])),
+            "refinements_per_system": float(np.mean([r["refinements"] for r in rec])),
+            "final_relres_max": max(r["final_relres"] for r in rec),
+            "all_converged": all(r["status"] == 0 for r in rec),
+            "kernels": {k: {"launches": v["launches"], "share": v["ms"] / tot_ms,
+                            "GB/s": v["bytes"] / (v["ms"] * 1e6) if v["ms"] else 0.0}
+                        for k, v in stats.items() if v["launches"]}}
+    print(json.dumps(out), flush=True)
+
+
 def _gen_nonsym(job):
     import workloads
     N, i = job
@@ -689,6 +752,8 @@ def main():
     ap.add_argument("--profile-guess", default="sketch", choices=["sketch", "pod", "rand"])
     ap.add_argument("--batched-only", action="store_true")
     ap.add_argument("--batched-count", type=int, default=512)
+    ap.add_argument("--precond-form", action="store_true")
+    ap.add_argument("--precond-sweeps", type=int, default=4)
     ap.add_argument("--e1", action="store_true")
     ap.add_argument("--e1-grid", type=int, default=100)
     ap.add_argument("--e1-steps", type=int, default=200)
@@ -719,6 +784,9 @@ def main():
         return
     if args.e1:
         e1_sequence(args)
+        return
+    if args.precond_form:
+        precond_form(args)
         return
     if args.profile_run:
         profile_run(args.profile_run, args.profile_precision, args.profile_guess)

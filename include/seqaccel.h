@@ -106,6 +106,11 @@ typedef struct {
                              (ignored by the other modes)                          */
     int32_t refresh;      /* SEQ_GUESS_RAND: progressive updates between from-scratch
                              computations of Omega; 0 selects 50 (Section 4)       */
+    int32_t precond_sweeps; /* GMRES only: right preconditioner M^{-1} = this many
+                             damped Jacobi sweeps on A z = u from z = 0 (0: none,
+                             at most 32); the minimised and tested residual stays
+                             the true one (x = x0 + M^{-1} V y)                   */
+    double precond_omega; /* sweep weight omega in (0, 2); 0 selects 0.8          */
 } seq_config;
 
 typedef struct {
@@ -203,7 +208,8 @@ typedef enum {
     SEQ_K_CGS_PASS3 = 3,  /* w -= V h2, ||w||, Givens update (basis column j+1)          */
     SEQ_K_UPDATE = 4,     /* x += V y at the end of a restart cycle                      */
     SEQ_K_RESTART = 5,    /* r = b - A x, ||r|| at a cycle start                         */
-    SEQ_K_COUNT = 6
+    SEQ_K_PRECOND = 6,    /* preconditioner kernels (scale and Jacobi sweeps)            */
+    SEQ_K_COUNT = 7
 } seq_kernel_kind;
 
 typedef struct {

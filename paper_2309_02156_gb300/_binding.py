@@ -38,7 +38,8 @@ class _Config(ctypes.Structure):
                 ("krylov", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("max_iters", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("rank_tol", ctypes.c_double), ("basis_m", ctypes.c_int32),
-                ("refresh", ctypes.c_int32)]
+                ("refresh", ctypes.c_int32), ("precond_sweeps", ctypes.c_int32),
+                ("precond_omega", ctypes.c_double)]
 
 
 class SeqInfo(ctypes.Structure):
@@ -57,7 +58,7 @@ class KernelStat(ctypes.Structure):
                 ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
-KERNEL_KINDS = ["spmv", "cgs_dot", "cgs_pass2", "cgs_pass3", "update", "restart"]
+KERNEL_KINDS = ["spmv", "cgs_dot", "cgs_pass2", "cgs_pass3", "update", "restart", "precond"]
 
 _LIB = None
 
@@ -183,10 +184,12 @@ class Sequence:
     def __init__(self, n: int, M: int, s: int, zeta: int = 8, seed: int = 0x5EEDBA5E,
                  precision: str = "f64", guess: str = "sketch", krylov: str = "gmres",
                  restart: int = 30, max_iters: int = 30000, inner_tol: float = 0.0,
-                 rank_tol: float = 0.0, basis_m: int = 0, refresh: int = 0):
+                 rank_tol: float = 0.0, basis_m: int = 0, refresh: int = 0,
+                 precond_sweeps: int = 0, precond_omega: float = 0.0):
         self._lib = load()
         cfg = _Config(n, M, s, zeta, seed, PRECISION[precision], GUESS[guess], KRYLOV[krylov],
-                      restart, max_iters, inner_tol, rank_tol, basis_m, refresh)
+                      restart, max_iters, inner_tol, rank_tol, basis_m, refresh,
+                      precond_sweeps, precond_omega)
         h = ctypes.c_void_p()
         rc = self._lib.seq_create(ctypes.byref(cfg), ctypes.c_void_p(_stream()), ctypes.byref(h))
         if rc != 0:

@@ -85,6 +85,10 @@ struct seq_ctx {
     double* Wp = nullptr;            // POD: reduced block [W1 V_k | wb]
     LsqOut* lsq_red = nullptr;
     int pod_mi = 0, pod_kk = 0;
+    void* dinv = nullptr;            // preconditioner: 1 / diag(A) and sweep vectors
+    void* za = nullptr;
+    void* zb = nullptr;
+    void* tprec = nullptr;
     cudaGraphExec_t cycle = nullptr;
     cudaGraphExec_t cycle_prof = nullptr;   // same cycle with timing events between kernels
     std::vector<cudaEvent_t> ev;
@@ -223,9 +227,11 @@ int capture_cycle(seq_ctx* ctx, bool prof) {
     if (*exec) return SEQ_OK;
     const int R = ctx->cfg.restart;
     cudaEvent_t* ev = nullptr;
+    const int sw = ctx->cfg.precond_sweeps;
+    const double om = ctx->cfg.precond_omega;
     if (prof) {
         if (ctx->ev.empty()) {
-            ctx->ev.resize(kKernelsPerStep * R + 3);
+            ctx->ev.resize(cycle_kernels(R, sw) + 1);
             for (auto& e : ctx->ev) CK(cudaEventCreate(&e));
         }
         ev = ctx->ev.data();
@@ -234,11 +240,14 @@ int capture_cycle(seq_ctx* ctx, bool prof) {
     CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
     if (!ctx->mixed)
         launch_gmres_cycle_f64(ctx->d_args, ctx->ks, (double*)ctx->V, ctx->ldv, (double*)ctx->w,
-                               ctx->kpartial, ctx->nblk, R, ctx->cap, &ctx->cycle_launches, ev);
+                               ctx->kpartial, ctx->nblk, R, ctx->cap, &ctx->cycle_launches, ev, sw,
+                               om, (const double*)ctx->dinv, (double*)ctx->za, (double*)ctx->zb,
+                               (double*)ctx->tprec);
     else
         launch_gmres_cycle_f32(ctx->d_args_in, ctx->ks_in, (float*)ctx->V, ctx->ldv,
                                (float*)ctx->w, (float*)ctx->kpartial, ctx->nblk, R, ctx->cap,
-                               &ctx->cycle_launches, ev);
+                               &ctx->cycle_launches, ev, sw, om, (const float*)ctx->dinv,
+                               (float*)ctx->za, (float*)ctx->zb, (float*)ctx->tprec);
     CK(cudaStreamEndCapture(ctx->cap, &g));
     cudaError_t e = cudaGraphInstantiate(exec, g, 0);
     cudaGraphDestroy(g);
@@ -271,17 +280,37 @@ void account_cycle(seq_ctx* ctx, bool f32, int jd, bool updated, int nnz) {
     // and value arrays plus the slice offsets), the CSR arrays otherwise.
     const double ns = (ctx->cfg.n + 31) / 32;
     const double spmv_mat = ctx->sell_ok ? 4.0 * (ns + 1) + (4.0 + E) * (double)*ctx->h_int : csr;
-    const int S = kKernelsPerStep;
+    const int sw = ctx->cfg.precond_sweeps;
+    const int S = kKernelsPerStep + sw;
+    // Preconditioner: the scale reads u, dinv and writes z; a sweep reads the
+    // matrix, z (gathered), u, dinv and writes the next z.
+    auto precond = [&](int ev0) {
+        add_stat(ctx, SEQ_K_PRECOND, ev0, 3.0 * E * n, 2.0 * n);
+        for (int k = 1; k < sw; ++k)
+            add_stat(ctx, SEQ_K_PRECOND, ev0 + k, spmv_mat + 4.0 * E * n, 2.0 * nnz + 4.0 * n);
+    };
     for (int j = 0; j < jd; ++j) {
         const double nk = j + 1;
-        add_stat(ctx, SEQ_K_SPMV, S * j, spmv_mat + 2.0 * E * n, 2.0 * nnz + n);
-        add_stat(ctx, SEQ_K_CGS_DOT, S * j + 1, E * n * (nk + 1), 2.0 * n * nk);
-        add_stat(ctx, SEQ_K_CGS_PASS2, S * j + 2, E * n * (nk + 2), 4.0 * n * nk);
-        add_stat(ctx, SEQ_K_CGS_PASS3, S * j + 3, E * n * (nk + 2), 2.0 * n * nk + 2.0 * n);
+        const int e = S * j + sw;
+        if (sw > 0) precond(S * j);
+        add_stat(ctx, SEQ_K_SPMV, e, spmv_mat + 2.0 * E * n, 2.0 * nnz + n);
+        add_stat(ctx, SEQ_K_CGS_DOT, e + 1, E * n * (nk + 1), 2.0 * n * nk);
+        add_stat(ctx, SEQ_K_CGS_PASS2, e + 2, E * n * (nk + 2), 4.0 * n * nk);
+        add_stat(ctx, SEQ_K_CGS_PASS3, e + 3, E * n * (nk + 2), 2.0 * n * nk + 2.0 * n);
     }
-    const int u = S * (int)R;
-    if (updated) add_stat(ctx, SEQ_K_UPDATE, u, E * n * (jd + 2), 2.0 * n * jd);
-    add_stat(ctx, SEQ_K_RESTART, u + 1, csr + 3.0 * E * n, 2.0 * nnz + 4.0 * n);
+    int u = S * (int)R;
+    if (sw > 0) {
+        if (updated) {
+            add_stat(ctx, SEQ_K_UPDATE, u, E * n * (jd + 1), 2.0 * n * jd);
+            precond(u + 1);
+            add_stat(ctx, SEQ_K_UPDATE, u + 1 + sw, 3.0 * E * n, n);
+        }
+        u += sw + 2;
+    } else {
+        if (updated) add_stat(ctx, SEQ_K_UPDATE, u, E * n * (jd + 2), 2.0 * n * jd);
+        u += 1;
+    }
+    add_stat(ctx, SEQ_K_RESTART, u, csr + 3.0 * E * n, 2.0 * nnz + 4.0 * n);
 }
 
 // One restarted GMRES solve on the system bound to (args, ks); `f32` selects
@@ -347,12 +376,16 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
     const bool compressed = c.guess == SEQ_GUESS_POD || c.guess == SEQ_GUESS_RAND;
     if (compressed && (c.basis_m < 1 || c.basis_m > c.M || c.refresh < 0 || c.precision == SEQ_MIXED))
         return SEQ_EINVAL;
+    if (c.precond_sweeps < 0 || c.precond_sweeps > 32 || c.precond_omega < 0.0 ||
+        c.precond_omega >= 2.0 || (c.precond_sweeps > 0 && c.krylov != SEQ_GMRES))
+        return SEQ_EINVAL;
     seq_ctx* ctx = new seq_ctx();
     memset(ctx->stats, 0, sizeof(ctx->stats));
     ctx->cfg = c;
     if (ctx->cfg.inner_tol <= 0) ctx->cfg.inner_tol = 1e-2;
     if (ctx->cfg.rank_tol <= 0) ctx->cfg.rank_tol = c.precision == SEQ_MIXED ? 1e-5 : 1e-12;
     if (ctx->cfg.refresh <= 0) ctx->cfg.refresh = 50;
+    if (ctx->cfg.precond_omega <= 0.0) ctx->cfg.precond_omega = 0.8;
     ctx->mixed = c.precision != SEQ_F64;
     ctx->hist32 = c.precision == SEQ_MIXED;
     ctx->stream = (cudaStream_t)cuda_stream;
@@ -399,6 +432,12 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
         ok = ok && cudaMalloc(&ctx->yhat, sizeof(float) * kMaxM) == cudaSuccess;
         ok = ok && cudaMalloc(&ctx->used_net, 16) == cudaSuccess;     // int flag | double rho
         ok = ok && cudaMallocHost(&ctx->h_used, 16) == cudaSuccess;
+    }
+    if (c.precond_sweeps > 0) {
+        ok = ok && cudaMalloc(&ctx->dinv, el * (size_t)n) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->za, el * (size_t)n) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->zb, el * (size_t)n) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->tprec, el * (size_t)n) == cudaSuccess;
     }
     if (c.guess == SEQ_GUESS_RAND) {
         ctx->ldo = round_up(c.basis_m, 4);
@@ -451,7 +490,8 @@ int seq_destroy(seq_ctx* ctx) {
                         ctx->d_args, ctx->d_args_in, ctx->ks, ctx->ks_in, ctx->sell_width,
                         ctx->sell_off, ctx->sell_col, ctx->sell_val, ctx->yring, ctx->sample,
                         ctx->yhat, ctx->used_net, ctx->Om, ctx->Zs, ctx->gpart, ctx->gcount,
-                        ctx->G, ctx->Vk, ctx->lam, ctx->sweeps, ctx->Wp, ctx->lsq_red};
+                        ctx->G, ctx->Vk, ctx->lam, ctx->sweeps, ctx->Wp, ctx->lsq_red,
+                        ctx->dinv, ctx->za, ctx->zb, ctx->tprec};
     for (void* p : dev_ptrs)
         if (p) cudaFree(p);
     void* host_ptrs[] = {ctx->lsq_host, ctx->h_args, ctx->h_args_in, ctx->h_ks, ctx->h_int,
@@ -707,6 +747,14 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
     }
     rc = set_args(ctx, A, b_dev, x_dev, tol, c.max_iters);
     if (rc) return rc;
+    if (c.precond_sweeps > 0) {
+        if (!ctx->mixed)
+            launch_diag_inv_f64(ctx->d_args, (double*)ctx->dinv, c.n, ctx->stream);
+        else
+            launch_diag_inv_f32(ctx->d_args_in, (float*)ctx->dinv, c.n, ctx->stream);
+        ctx->launches += 1;
+        CK(cudaGetLastError());
+    }
     int status = SEQ_OK;
     if (!ctx->mixed) {
         if (c.krylov == SEQ_GMRES) {

@@ -56,6 +56,13 @@ void launch_pod_coeff(const LsqOut* red, const double* Vk, int mi, int kk, int M
 
 // krylov.cu
 int stream_grid(int n);
+// Kernels of one restart cycle: per Arnoldi step the preconditioner's
+// `sweeps` kernels (scale + sweeps - 1 sweeps) and the four Arnoldi kernels;
+// then the update (combine, preconditioner, axpy; or one update kernel) and
+// the restart residual.
+inline int cycle_kernels(int R, int sweeps) {
+    return (kKernelsPerStep + sweeps) * R + (sweeps > 0 ? sweeps + 2 : 1) + 1;
+}
 // ||b - A x|| and ||b|| of FP64 vectors; results in st->beta, st->bnorm and
 // st->first_relres = beta / bnorm.
 void launch_residual_norm(const DevArgs* a, KState* ks, double* partial, int nblk,
@@ -64,15 +71,23 @@ void launch_residual_norm(const DevArgs* a, KState* ks, double* partial, int nbl
 // full cycle (R Arnoldi steps, basis update, residual of the updated iterate).
 void launch_gmres_start_f64(const DevArgs* a, KState* ks, double* V, size_t ldv, double* partial,
                             int nblk, int first, cudaStream_t st);
+// Right preconditioning (sweeps > 0): M^{-1} = `sweeps` damped Jacobi sweeps
+// with weight omega and dinv = 1 / diag(A); za, zb, t: n-vectors of scratch.
 void launch_gmres_cycle_f64(const DevArgs* a, KState* ks, double* V, size_t ldv, double* w,
                             double* partial, int nblk, int R, cudaStream_t st, int* launches,
-                            cudaEvent_t* ev = nullptr);
+                            cudaEvent_t* ev = nullptr, int sweeps = 0, double omega = 1.0,
+                            const double* dinv = nullptr, double* za = nullptr,
+                            double* zb = nullptr, double* t = nullptr);
+void launch_diag_inv_f64(const DevArgs* a, double* dinv, int n, cudaStream_t st);
 // Same on the FP32 inner system A32 d = rhs32 (mixed precision).
 void launch_gmres_start_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, float* partial,
                             int nblk, int first, cudaStream_t st);
 void launch_gmres_cycle_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, float* w,
                             float* partial, int nblk, int R, cudaStream_t st, int* launches,
-                            cudaEvent_t* ev = nullptr);
+                            cudaEvent_t* ev = nullptr, int sweeps = 0, double omega = 1.0,
+                            const float* dinv = nullptr, float* za = nullptr,
+                            float* zb = nullptr, float* t = nullptr);
+void launch_diag_inv_f32(const DevArgs* a, float* dinv, int n, cudaStream_t st);
 // Mixed precision outer step: x += scale * d (FP64 += FP32), then the FP64
 // residual r = b - A64 x, its norm, and rhs32 = r / ||r||.
 void launch_refine_residual(const DevArgs* a, KState* ks, float* rhs32, double* partial, int nblk,

@@ -10,8 +10,21 @@ void launch_gmres_start_f32(const DevArgs* a, KState* ks, float* V, size_t, floa
 }
 void launch_gmres_cycle_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, float* w,
                             float* partial, int nblk, int R, cudaStream_t st, int* launches,
-                            cudaEvent_t* ev) {
-    launch_cycle<SysF32>(a, ks, V, ldv, w, partial, nblk, R, st, launches, ev);
+                            cudaEvent_t* ev, int sweeps, double omega, const float* dinv,
+                            float* za, float* zb, float* t) {
+    PrecondArgs<float> pc;
+    pc.sweeps = sweeps;
+    pc.omega = omega;
+    pc.dinv = dinv;
+    pc.za = za;
+    pc.zb = zb;
+    pc.t = t;
+    launch_cycle<SysF32>(a, ks, V, ldv, w, partial, nblk, R, st, launches, ev, pc);
+}
+void launch_diag_inv_f32(const DevArgs* a, float* dinv, int n, cudaStream_t st) {
+    int b = (n + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    diag_inv_kernel<SysF32><<<b > 0 ? b : 1, 256, 0, st>>>(a, dinv);
 }
 
 }  // namespace sa

@@ -1,0 +1,126 @@
+"""Right-preconditioned GMRES (damped Jacobi sweeps) on the GPU against the
+oracle's krylov.gmres(minv=krylov.jacobi_sweeps(...)).
+
+Tolerances: as for the unpreconditioned GMRES (both sides run the same
+stopping test on the true residual; rounding moves the stopping iteration by a
+few steps: iterations within max(2, 3%)); the mixed form within 50% of the
+oracle's float32 emulation (the inner float32 solves amplify rounding
+differences); every final true residual meets the tolerance, checked with the
+oracle's FP64 product.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import krylov, method, sketch
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_02156_gb300 as sa
+    sa.load()
+    yield
+
+
+def _sa():
+    import paper_2309_02156_gb300 as sa
+    return sa
+
+
+def _t(x, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device=DEV, dtype=dtype)
+
+
+def _system(N, i):
+    p = workloads.plain_nonsym(N)
+    rowptr, colind, vals, b = workloads.csr_system(p, i)
+    A = _sa().CSR(_t(rowptr, torch.int32), _t(colind, torch.int32), _t(vals))
+    return p, A, _t(b), krylov.csr(rowptr, colind, vals, p.n), b
+
+
+@pytest.mark.parametrize("N,d,omega", [(32, 1, 0.8), (45, 4, 0.8), (40, 3, 1.0), (24, 8, 0.7)])
+def test_preconditioned_gmres_matches_oracle(N, d, omega):
+    p, A, bd, A_ref, b = _system(N, 4)
+    minv = krylov.jacobi_sweeps(A_ref, d, omega)
+    x_ref, it_ref, rel_ref, st_ref = krylov.gmres(A_ref, b, np.zeros(p.n), 1e-9, 30, 50000, minv=minv)
+    seq = _sa().Sequence(p.n, 4, 16, krylov="gmres", restart=30, max_iters=50000,
+                         precond_sweeps=d, precond_omega=omega)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    info = seq.solve(A, bd, 1e-9, x)
+    assert info["status"] == 0 and st_ref == 0
+    assert abs(info["iters"] - it_ref) <= max(2, 0.03 * it_ref)
+    xh = x.cpu().numpy()
+    assert method.relres(A_ref, b, xh) <= 1e-9 * (1 + 1e-9)
+    assert info["final_relres"] == pytest.approx(method.relres(A_ref, b, xh), rel=1e-6)
+    assert np.linalg.norm(xh - x_ref) <= 1e-6 * np.linalg.norm(x_ref)
+    seq.close()
+
+
+def test_preconditioning_cuts_iterations_and_profiles_its_kernels():
+    p, A, bd, A_ref, b = _system(64, 2)
+    its = {}
+    for d in (0, 4):
+        seq = _sa().Sequence(p.n, 4, 16, krylov="gmres", restart=30, max_iters=50000,
+                             precond_sweeps=d)
+        seq.set_profiling(True)
+        x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+        info = seq.solve(A, bd, 1e-10, x)
+        assert info["status"] == 0
+        assert method.relres(A_ref, b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-9)
+        st = seq.kernel_stats()
+        its[d] = info["iters"]
+        assert st["spmv"]["launches"] == info["iters"]
+        if d:
+            # scale + (d - 1) sweeps per Arnoldi step, plus the same per cycle update
+            assert st["precond"]["launches"] >= d * info["iters"]
+        else:
+            assert st["precond"]["launches"] == 0
+        seq.close()
+    assert its[4] < 0.6 * its[0]
+
+
+def test_mixed_preconditioned_reaches_tolerance():
+    p, A, bd, A_ref, b = _system(48, 3)
+    A32 = A_ref.astype(np.float32)
+    x_ref, it_ref, nref, rel, st = krylov.mixed_refine(A_ref, A32, b, np.zeros(p.n), 1e-10, "gmres",
+                                                      30, 100000, precond=(4, 0.8))
+    assert st == 0
+    seq = _sa().Sequence(p.n, 4, 16, krylov="gmres", precision="mixed_krylov", restart=30,
+                         max_iters=100000, precond_sweeps=4)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    info = seq.solve(A, bd, 1e-10, x)
+    assert info["status"] == 0
+    assert method.relres(A_ref, b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-9)
+    assert abs(info["iters"] - it_ref) <= 0.5 * it_ref + 10
+    seq.close()
+
+
+def test_preconditioned_sequence_with_sketched_guess():
+    """20 systems: sketched guess + preconditioned GMRES through the C-ABI;
+    every system converges (oracle SpMV check)."""
+    p = workloads.plain_nonsym(40)
+    seq = _sa().Sequence(p.n, 8, 40, krylov="gmres", precond_sweeps=4, max_iters=50000)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    for i in range(20):
+        _, A, bd, A_ref, b = _system(40, i)
+        seq.guess(A, bd, x)
+        info = seq.solve(A, bd, 1e-9, x)
+        assert info["status"] == 0
+        assert method.relres(A_ref, b, x.cpu().numpy()) <= 1e-9 * (1 + 1e-9)
+        seq.push(x)
+    seq.close()
+
+
+def test_preconditioner_config_checks():
+    sa = _sa()
+    for kw in ({"krylov": "cg", "precond_sweeps": 2}, {"precond_sweeps": 33},
+               {"precond_sweeps": 2, "precond_omega": 2.0}, {"precond_sweeps": -1}):
+        with pytest.raises(sa.SeqError):
+            sa.Sequence(100, 4, 16, **kw)
