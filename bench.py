@@ -683,7 +683,8 @@ def precision_form(args):
     ci = torch.from_numpy(colind).to(dev)
     n = N * N
     seq = sa.Sequence(n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, precision=args.precision_kind,
-                      krylov="gmres", restart=RESTART, max_iters=400000)
+                      krylov="gmres", restart=RESTART, max_iters=400000,
+                      precond_sweeps=args.precision_sweeps)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     total = P + W + K
     nxt = pool.map_async(_gen_nonsym, [(N, i) for i in range(0, min(4, total))])
@@ -721,7 +722,10 @@ def precision_form(args):
     out = {
         "precision_form": True,
         "workload": "nonsym advection-diffusion %dx%d (n=%d), M=20, s=80, %s: FP32 values/history/"
-                    "inner GMRES(30), FP64 refinement to rel-res 1e-10" % (N, N, n, args.precision_kind),
+                    "inner GMRES(30)%s, FP64 refinement to rel-res 1e-10"
+                    % (N, N, n, args.precision_kind,
+                       " right-preconditioned by %d Jacobi sweeps" % args.precision_sweeps
+                       if args.precision_sweeps else ""),
         "value": 1e3 * K / sum(timed_ms), "unit": "systems/s", "ms_per_step": sum(timed_ms) / K,
         "steps": K, "warmup": W, "prime": P,
         "iters_mean": float(np.mean([r["iters"] for r in timed])),
@@ -766,6 +770,7 @@ def main():
     ap.add_argument("--precision-prime", type=int, default=20)
     ap.add_argument("--precision-warmup", type=int, default=1)
     ap.add_argument("--precision-steps", type=int, default=5)
+    ap.add_argument("--precision-sweeps", type=int, default=0)
     ap.add_argument("--learned-ablation", action="store_true")
     ap.add_argument("--learned-train", type=int, default=400)
     ap.add_argument("--learned-eval", type=int, default=400)
