@@ -24,6 +24,8 @@ already meets the tolerance, Sections 4 and 5) can happen.  Conventions shared w
 * mixed refinement: r = b - A64 x in FP64; the correction d solves
   A32 d = r / ||r|| by the same solver run entirely in float32, to a relative
   residual max(inner_tol, theta * tol ||b|| / ||r||); x += ||r|| d in FP64.
+  A GMRES inner solve is a single restart cycle, so every restart begins from
+  a residual formed in FP64 (GMRES-based iterative refinement).
 
 Status codes: 0 converged, 1 not converged within max_iters, -4 breakdown.
 
@@ -176,9 +178,17 @@ def gmres(A, b, x, tol: float, restart: int, max_iters: int, record=None, minv=N
 
 def mixed_refine(A64, A32, b, x, tol: float, inner: str, restart: int,
                  max_iters: int, inner_tol: float = 1e-2, theta: float = 0.5,
-                 max_refinements: int = 100, precond=None):
+                 max_refinements: int = None, precond=None):
     """FP32-inner / FP64-outer iterative refinement.  Returns
-    (x, inner_iterations, refinements, relres, status)."""
+    (x, inner_iterations, refinements, relres, status).
+
+    A GMRES inner solve is one restart cycle (at most `restart` iterations):
+    every restart of the restarted GMRES starts from a residual formed in
+    FP64 by the refinement.  (Restarting inside the float32 solve would form
+    the residual in float32, whose rounding noise, about u32 cond(A) ||r||,
+    stalls the inner solve on ill-conditioned systems.)  The number of
+    refinements is bounded by max_iters, each costing at least one iteration,
+    unless max_refinements is given."""
     x = x.astype(np.float64, copy=True)
     bnorm = math.sqrt(float(np.dot(b, b)))
     target = tol * bnorm
@@ -189,7 +199,7 @@ def mixed_refine(A64, A32, b, x, tol: float, inner: str, restart: int,
         rn = math.sqrt(float(np.dot(r, r)))
         if rn <= target:
             return x, total, refinements, rn / bnorm, CONVERGED
-        if refinements >= max_refinements or total >= max_iters:
+        if (max_refinements is not None and refinements >= max_refinements) or total >= max_iters:
             return x, total, refinements, rn / bnorm, NOT_CONVERGED
         rhs32 = (r / rn).astype(np.float32)
         itol = max(inner_tol, theta * target / rn)
@@ -199,7 +209,7 @@ def mixed_refine(A64, A32, b, x, tol: float, inner: str, restart: int,
             d, it, _, st = cg(A32, rhs32, d0, itol, budget)
         else:
             minv = jacobi_sweeps(A32, *precond) if precond else None
-            d, it, _, st = gmres(A32, rhs32, d0, itol, restart, budget, minv=minv)
+            d, it, _, st = gmres(A32, rhs32, d0, itol, restart, min(restart, budget), minv=minv)
         total += it
         refinements += 1
         if st == BREAKDOWN:

@@ -785,7 +785,11 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
         double beta = ctx->h_ks->beta;
         int bad = ctx->h_ks->bad_index;
         status = SEQ_OK;
-        const int max_ref = 100;
+        // A GMRES inner solve is one restart cycle: every restart then starts
+        // from the FP64 residual (an FP32 residual has rounding noise of about
+        // u32 cond(A) ||r||, which stalls restarts on ill-conditioned systems).
+        // Each refinement costs at least one iteration, so max_iters bounds them.
+        const int max_ref = c.krylov == SEQ_GMRES ? c.max_iters + 1 : 100;
         while (beta > target) {
             if (!isfinite(beta)) {
                 status = SEQ_ENONFINITE;
@@ -798,6 +802,7 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
             DevArgs* hi = ctx->h_args_in;
             hi->tol = fmax(c.inner_tol, theta * target / beta);
             hi->max_iters = c.max_iters - total;
+            if (c.krylov == SEQ_GMRES && hi->max_iters > c.restart) hi->max_iters = c.restart;
             CK(cudaMemcpyAsync(ctx->d_args_in, hi, sizeof(DevArgs), cudaMemcpyHostToDevice,
                                ctx->stream));
             if (c.krylov == SEQ_GMRES) {
