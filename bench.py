@@ -255,7 +255,7 @@ def profile_run(iters: int, precision: str = "f64", guess: str = "sketch") -> No
     seq.close()
 
 
-def batched_form(K, W, hbm_peak, count=512):
+def batched_form(K, W, hbm_peak, count=512, plain_sample=16):
     """512 independent SPD sequences (grid side 48..384, M = 12, s = 48), FP32 CG
     inside FP64 refinement to 1e-8, one persistent launch per time step (CUDA
     graph).  Systems are assembled on the device between timed steps."""
@@ -279,14 +279,27 @@ def batched_form(K, W, hbm_peak, count=512):
         torch.cuda.synchronize()
         return gen.split(v, gen.nnz_off), gen.split(b, gen.n_off), (v, b)
 
+    # The plain FP64 GPU method (single-sequence API: sketched guess, FP64 CG,
+    # push) on a sample of the sequences, fed the batch's solutions so that it
+    # sees the same histories; timed on the step after the batched timing.
+    sample = list(range(0, count, max(1, count // plain_sample)))[:plain_sample]
+    plain = {k: sa.Sequence(ps[k].n, M, S, zeta=ZETA, seed=SEED, krylov="cg", max_iters=200000)
+             for k in sample} if plain_sample else {}
+
+    def feed():
+        for k, ctx in plain.items():
+            ctx.push(xs[k])
+
     for i in range(M):
         vs, bs, keep = inputs(i)
         bt.step(vs, bs, xs, TOL)
+        feed()
     vs, bs, keep = inputs(M)
     chosen = bt.autotune(vs, bs, xs, TOL)
     for i in range(M, M + W):
         vs, bs, keep = inputs(i)
         bt.step(vs, bs, xs, TOL)
+        feed()
     total_ms, infos_all = 0.0, []
     for i in range(M + W, M + W + K):
         vs, bs, keep = inputs(i)
@@ -298,7 +311,36 @@ def batched_form(K, W, hbm_peak, count=512):
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
         infos_all.append(infos)
+        feed()
     bt.close()
+    plain_out = None
+    if plain:
+        i = M + W + K
+        vs, bs, keep = inputs(i)
+        pms, pits, prel = 0.0, [], []
+        for k, ctx in plain.items():
+            A = sa.CSR(pats[k][0], pats[k][1], vs[k].contiguous())
+            bk = bs[k].contiguous()
+            x = torch.empty(ps[k].n, dtype=torch.float64, device=dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.guess(A, bk, x)
+            info = ctx.solve(A, bk, TOL, x)
+            ctx.push(x)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pms += e0.elapsed_time(e1)
+            pits.append(info["iters"])
+            prel.append(info["final_relres"])
+            ctx.close()
+        plain_out = {"method": "plain FP64 GPU method, one sequence at a time (sketched guess, FP64 CG, "
+                               "push) on %d of the %d sequences (every %d-th), same histories, "
+                               "the step after the timed ones" % (len(plain), count, count // len(plain)),
+                     "value": 1e3 * len(plain) / pms, "unit": "systems/s",
+                     "iters_mean": float(np.mean(pits)), "final_relres_max": max(prel),
+                     "sample_n_mean": float(np.mean([ps[k].n for k in plain])),
+                     "all_n_mean": float(np.mean([p.n for p in ps]))}
     n = np.array([p.n for p in ps], dtype=np.float64)
     nnz = np.array([p.nnz for p in ps], dtype=np.float64)
     byts = 0.0
@@ -318,6 +360,7 @@ def batched_form(K, W, hbm_peak, count=512):
         "refinements_mean": float(np.mean([f["refinements"] for f in flat])),
         "final_relres_max": max(f["final_relres"] for f in flat),
         "all_converged": all(f["status"] == 0 for f in flat),
+        "plain_fp64": plain_out,
         "roofline": {"bound": "hbm", "kernel": "batched_step_kernel",
                      "achieved": byts / secs / 1e9, "peak": hbm_peak, "unit": "GB/s",
                      "frac": byts / secs / 1e9 / hbm_peak},
