@@ -25,6 +25,7 @@
 
 #include "../../include/seqaccel.h"
 #include "common.cuh"
+#include "internal.h"
 
 namespace sa {
 namespace {
@@ -42,8 +43,11 @@ struct BatchSeq {
     const int* rowptr;
     const int* colind;
     double* X;                             // history ring, n x ldx (FP64)
-    float* val32;                          // FP32 copy of this step's values
-    float *r, *p, *q, *d;                  // FP32 CG vectors
+    float* val32;                          // zeros (source of the SELL padding fill)
+    const int* soff;                       // SELL-32 copy of the pattern for the FP32 CG:
+    const int* scol;                       //   slice offsets, padded column indices,
+    float* sval;                           //   values refreshed every step (FP32)
+    float *r, *p, *q, *d;                  // FP32 CG vectors (16-byte aligned, stride nv)
     // per step
     const double* val;
     const double* b;
@@ -324,12 +328,83 @@ __device__ void block_lsq(const double* Wsum, int s, int M, int m, int oldest, d
 
 // FP32 CG on A32 d = rhs (d from 0) to ||rhs - A32 d|| <= itol ||rhs||, in
 // one block; returns iterations (negative status on breakdown).
+// FP32 SELL-32 product of one sequence by a whole block: warp per 32-row
+// slice (lane = row); for every slice the index and value loads are issued
+// first (coalesced), then the gathers, then the row sums in CSR order.  Padding (column -1) costs no arithmetic; a
+// column >= n is skipped and flagged.  Row results go to epi(row, value).
+constexpr int kBW = 5;      // 5-point stencils: every slice fits; wider rows take the loop
+
+template <typename Epi>
+__device__ __forceinline__ void bsell_spmv(const BatchSeq& q, const float* __restrict__ x, int nw,
+                                           int* bad, Epi& epi) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n = q.n;
+    const int ns = (n + 31) >> 5;
+    int flag = 0;
+    for (int sl = warp; sl < ns; sl += nw) {
+        const int o = q.soff[sl], w = (q.soff[sl + 1] - o) >> 5;
+        float a = 0.f;
+        if (w <= kBW) {
+            int c[kBW];
+            float v[kBW], xv[kBW];
+#pragma unroll
+            for (int k = 0; k < kBW; ++k) {
+                c[k] = k < w ? q.scol[o + k * 32 + lane] : -1;
+                v[k] = k < w ? q.sval[o + k * 32 + lane] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < kBW; ++k) {
+                xv[k] = (unsigned)c[k] < (unsigned)n ? x[c[k]] : 0.f;
+                flag |= c[k] >= n;
+            }
+#pragma unroll
+            for (int k = 0; k < kBW; ++k)
+                if (k < w) a = fmaf(v[k], xv[k], a);
+        } else {
+            for (int k = 0; k < w; ++k) {
+                const int cc = q.scol[o + k * 32 + lane];
+                if ((unsigned)cc < (unsigned)n) a = fmaf(q.sval[o + k * 32 + lane], x[cc], a);
+                else flag |= cc >= n;
+            }
+        }
+        const int r = sl * 32 + lane;
+        if (r < n) epi(r, a);
+    }
+    if (flag) atomicOr(bad, 1);
+}
+
+struct CgProductEpi {
+    float* qv;
+    const float* p;
+    float acc;
+    __device__ void operator()(int r, float a) {
+        qv[r] = a;
+        acc = fmaf(p[r], a, acc);
+    }
+};
+
 __device__ int block_cg32(const BatchSeq& q, double itol, int max_iters, float* sred, float* stage,
                           int* sbad, int& status) {
+    // Vector phases use 16-byte loads over the first 4 floor(n / 4) entries
+    // (the vectors are 16-byte aligned), then the ragged tail.
+    const int n4 = q.n >> 2;
+    float4* r4 = reinterpret_cast<float4*>(q.r);
+    float4* p4 = reinterpret_cast<float4*>(q.p);
+    float4* q4 = reinterpret_cast<float4*>(q.q);
+    float4* d4 = reinterpret_cast<float4*>(q.d);
+    (void)stage;
     const int n = q.n, tid = threadIdx.x, bd = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+    const int nw = bd >> 5;
     float rr_l = 0.f;
-    for (int i = tid; i < n; i += bd) {
+    for (int i = tid; i < n4; i += bd) {
+        const float4 ri = r4[i];
+        d4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        p4[i] = ri;
+        rr_l = fmaf(ri.x, ri.x, rr_l);
+        rr_l = fmaf(ri.y, ri.y, rr_l);
+        rr_l = fmaf(ri.z, ri.z, rr_l);
+        rr_l = fmaf(ri.w, ri.w, rr_l);
+    }
+    for (int i = 4 * n4 + tid; i < n; i += bd) {
         const float ri = q.r[i];
         q.d[i] = 0.f;
         q.p[i] = ri;
@@ -346,24 +421,34 @@ __device__ int block_cg32(const BatchSeq& q, double itol, int max_iters, float* 
             break;
         }
         __syncthreads();
-        float pq_l = 0.f;
-        for (int r0 = warp * 32; r0 < n; r0 += nw * 32) {
-            const float qi = warp_tile_spmv<float>(q.rowptr, q.colind, q.val32, q.p, n, q.nnz, r0,
-                                                   stage + warp * kTileChunks * 32, sbad);
-            const int i = r0 + lane;
-            if (i < n) {
-                q.q[i] = qi;
-                pq_l = fmaf(q.p[i], qi, pq_l);
-            }
-        }
-        const float pq = btotal(pq_l, sred);
+        CgProductEpi epi{q.q, q.p, 0.f};
+        bsell_spmv(q, q.p, nw, sbad, epi);
+        const float pq = btotal(epi.acc, sred);
         if (!(pq > 0.f)) {
             status = isfinite(pq) ? -4 : -5;
             break;
         }
         const float alpha = rr / pq;
         float rn_l = 0.f;
-        for (int i = tid; i < n; i += bd) {
+        for (int i = tid; i < n4; i += bd) {
+            const float4 pv = p4[i], qv = q4[i];
+            float4 dv = d4[i], rv = r4[i];
+            dv.x = fmaf(alpha, pv.x, dv.x);
+            dv.y = fmaf(alpha, pv.y, dv.y);
+            dv.z = fmaf(alpha, pv.z, dv.z);
+            dv.w = fmaf(alpha, pv.w, dv.w);
+            rv.x = fmaf(-alpha, qv.x, rv.x);
+            rv.y = fmaf(-alpha, qv.y, rv.y);
+            rv.z = fmaf(-alpha, qv.z, rv.z);
+            rv.w = fmaf(-alpha, qv.w, rv.w);
+            d4[i] = dv;
+            r4[i] = rv;
+            rn_l = fmaf(rv.x, rv.x, rn_l);
+            rn_l = fmaf(rv.y, rv.y, rn_l);
+            rn_l = fmaf(rv.z, rv.z, rn_l);
+            rn_l = fmaf(rv.w, rv.w, rn_l);
+        }
+        for (int i = 4 * n4 + tid; i < n; i += bd) {
             q.d[i] = fmaf(alpha, q.p[i], q.d[i]);
             const float ri = fmaf(-alpha, q.q[i], q.r[i]);
             q.r[i] = ri;
@@ -373,7 +458,16 @@ __device__ int block_cg32(const BatchSeq& q, double itol, int max_iters, float* 
         ++it;
         const float beta = rr_new / rr;
         rr = rr_new;
-        for (int i = tid; i < n; i += bd) q.p[i] = fmaf(beta, q.p[i], q.r[i]);
+        for (int i = tid; i < n4; i += bd) {
+            const float4 rv = r4[i];
+            float4 pv = p4[i];
+            pv.x = fmaf(beta, pv.x, rv.x);
+            pv.y = fmaf(beta, pv.y, rv.y);
+            pv.z = fmaf(beta, pv.z, rv.z);
+            pv.w = fmaf(beta, pv.w, rv.w);
+            p4[i] = pv;
+        }
+        for (int i = 4 * n4 + tid; i < n; i += bd) q.p[i] = fmaf(beta, q.p[i], q.r[i]);
     }
     __syncthreads();
     return it;
@@ -434,7 +528,13 @@ batched_step_kernel(BatchSeq* seqs, const int* __restrict__ order, int count, in
                 q.x[i] = acc;
             }
         }
-        for (int e = tid; e < q.nnz; e += bd) q.val32[e] = (float)q.val[e];
+        // This step's values into the SELL copy (FP32): entry k of row i goes
+        // to soff[i / 32] + 32 k + i % 32.
+        for (int i = tid; i < n; i += bd) {
+            const int e0 = q.rowptr[i], e1 = q.rowptr[i + 1];
+            float* dst = q.sval + q.soff[i >> 5] + (i & 31);
+            for (int e = e0; e < e1; ++e) dst[(e - e0) * 32] = (float)q.val[e];
+        }
         __syncthreads();
         // Warp-tile staging for the products (aliases the guess workspace).
         double* stage_d = smem;
@@ -650,15 +750,48 @@ int seq_batch_create(int32_t count, const seq_csr* patterns, int32_t M, int32_t 
         if (rc) break;
         q.X = (double*)p;
         cudaMemsetAsync(q.X, 0, sizeof(double) * (size_t)q.n * ldx, bt->stream);
-        rc = batch_alloc(bt, &p, sizeof(float) * (size_t)q.nnz);
+        rc = batch_alloc(bt, &p, sizeof(float) * (size_t)(q.nnz > 0 ? q.nnz : 1));
         if (rc) break;
         q.val32 = (float*)p;
-        rc = batch_alloc(bt, &p, sizeof(float) * 4 * (size_t)q.n);
+        cudaMemsetAsync(q.val32, 0, sizeof(float) * (size_t)(q.nnz > 0 ? q.nnz : 1), bt->stream);
+        // SELL-32 copy of the pattern (column indices once; the values are
+        // written by the step kernel; padding stays column -1, value 0).
+        const int ns = (q.n + 31) / 32;
+        rc = batch_alloc(bt, &p, sizeof(int) * (size_t)ns);
+        if (rc) break;
+        int* width = (int*)p;
+        rc = batch_alloc(bt, &p, sizeof(int) * (size_t)(ns + 1));
+        if (rc) break;
+        int* off = (int*)p;
+        launch_sell_layout(q.rowptr, q.n, q.nnz, width, off, bt->stream);
+        int total = 0;
+        if (cudaMemcpyAsync(&total, off + ns, sizeof(int), cudaMemcpyDeviceToHost, bt->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(bt->stream) != cudaSuccess) {
+            rc = SEQ_ECUDA;
+            break;
+        }
+        if (total < 0 || (long long)total > 2LL * q.nnz + 64LL * ns) {
+            rc = SEQ_EINVAL;
+            break;
+        }
+        rc = batch_alloc(bt, &p, sizeof(int) * (size_t)(total > 0 ? total : 1));
+        if (rc) break;
+        int* scol = (int*)p;
+        rc = batch_alloc(bt, &p, sizeof(float) * (size_t)(total > 0 ? total : 1));
+        if (rc) break;
+        float* sval = (float*)p;
+        launch_sell_fill_f32(q.rowptr, q.colind, q.val32, q.n, q.nnz, off, scol, sval, bt->stream);
+        q.soff = off;
+        q.scol = scol;
+        q.sval = sval;
+        const size_t nv = ((size_t)q.n + 3) & ~(size_t)3;     // 16-byte aligned vectors
+        rc = batch_alloc(bt, &p, sizeof(float) * 4 * nv);
         if (rc) break;
         q.r = (float*)p;
-        q.p = q.r + q.n;
-        q.q = q.p + q.n;
-        q.d = q.q + q.n;
+        q.p = q.r + nv;
+        q.q = q.p + nv;
+        q.d = q.q + nv;
     }
     void* p = nullptr;
     if (rc == SEQ_OK) rc = batch_alloc(bt, &p, sizeof(BatchSeq) * count), bt->d_seqs = (BatchSeq*)p;
