@@ -279,3 +279,65 @@ def test_training_is_deterministic_and_reduces_loss():
     assert np.array_equal(pa, pb) and np.array_equal(la, lb)
     assert l1 < 0.5 * l0 and la[-1] < la[0]
     seq.close()
+
+
+def test_learned_gain_over_least_squares():
+    """What the trained network gains: two contexts see identical histories
+    (the least-squares path's solutions are pushed into both); the network is
+    trained on the first 40 systems' samples and used on the next 15.  The
+    fallback bounds the loss (a rejected prediction leaves the least-squares
+    guess, so the solve is the same); the gain is reported, not assumed."""
+    p = workloads.plain_nonsym(48)
+    mk = lambda: _sa().Sequence(p.n, M, S_ROWS, zeta=8, seed=SEED, guess="learned", krylov="gmres")
+    c_ls, c_net = mk(), mk()
+    inp = 4 * M + S_ROWS
+    stride = inp + M + M * M + 1
+    samples = []
+    x = torch.empty(p.n, dtype=torch.float64, device=DEV)
+    y = torch.empty(p.n, dtype=torch.float64, device=DEV)
+
+    def system(i):
+        rowptr, colind, vals, b = workloads.csr_system(p, i)
+        return _sa().CSR(_tensor(rowptr, torch.int32), _tensor(colind, torch.int32), _tensor(vals)), _tensor(b)
+
+    for i in range(40):
+        A, b = system(i)
+        c_ls.guess(A, b, x)
+        c_net.guess(A, b, y)
+        if i >= M + 4:
+            buf = torch.empty(stride, dtype=torch.float32, device=DEV)
+            c_ls.last_sample(buf)
+            samples.append(buf)
+        assert c_ls.solve(A, b, 1e-10, x)["status"] == 0
+        c_ls.push(x)
+        c_net.push(x)
+    net = _sa().MLP(M, S_ROWS, hidden=64, max_batch=16, seed=3)
+    St = torch.stack(samples)
+    net.fit_normalization(St)
+    net.train(St, epochs=60, batch=16, lr=1e-3, seed=1)
+    c_net.set_learned(net)
+    it_ls, it_net, used = [], [], []
+    for i in range(40, 55):
+        A, b = system(i)
+        g1 = c_ls.guess(A, b, x)
+        g2 = c_net.guess(A, b, y)
+        i1 = c_ls.solve(A, b, 1e-10, x)
+        i2 = c_net.solve(A, b, 1e-10, y)
+        assert i1["status"] == 0 and i2["status"] == 0
+        it_ls.append(i1["iters"])
+        it_net.append(i2["iters"])
+        used.append(not g2["fallback"])
+        if g2["fallback"]:
+            assert g2["guess_relres"] == pytest.approx(g1["guess_relres"], rel=1e-12)
+            assert i2["iters"] == i1["iters"]
+        else:
+            assert g2["sketch_resid"] <= 1.5 * g1["sketch_resid"] * (1 + 1e-12)
+        c_ls.push(x)
+        c_net.push(x)
+    gain = np.mean(it_ls) - np.mean(it_net)
+    print(f"learned form: network used on {sum(used)}/{len(used)} systems, mean GMRES iterations "
+          f"{np.mean(it_net):.1f} vs {np.mean(it_ls):.1f} with least squares (gain {gain:+.1f})")
+    assert np.mean(it_net) <= 1.1 * np.mean(it_ls) + 2
+    c_ls.close()
+    c_net.close()
+    net.close()
