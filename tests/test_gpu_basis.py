@@ -241,3 +241,33 @@ def test_paper_test_sequence_guess(mode):
     assert abs(r_gpu - r_ref) <= max(1e-3 * r_ref, 1e-9)
     assert r_gpu < 1e-2
     seq.close()
+
+
+@pytest.mark.parametrize("mode,M,m,pushes", [("pod", 31, 31, 31), ("pod", 8, 5, 2), ("rand", 1, 1, 3),
+                                             ("rand", 31, 7, 40), ("pod", 7, 7, 1)])
+def test_compressed_edge_shapes(mode, M, m, pushes):
+    """Largest history (M = 31, odd Jacobi size), a basis larger than the
+    history held (start-up), M = m = 1, a wrapped ring; well-conditioned
+    Gaussian columns, so the guesses agree tightly with the oracle."""
+    p = workloads.plain_nonsym(20)
+    s = min(max(2 * M + 2, 16), 128)          # s >= zeta = 8
+    rng = np.random.default_rng(M * 100 + pushes)
+    cols = [rng.standard_normal(p.n) for _ in range(pushes)]
+    seq = _sa().Sequence(p.n, M, s, zeta=8, seed=SEED, guess=mode, basis_m=m, refresh=50)
+    S = sketch.sparse_sign_matrix(p.n, s, 8, SEED)
+    rrf = basis.RandRangeFinder(m, 50, SEED)
+    hist = method.History(p.n, M)
+    A, bd, A_ref, b = _gpu_system(p, 2)
+    for c in cols:
+        rrf.on_push(c, hist.cols[0] if len(hist.cols) == M else None)
+        hist.push(c)
+        seq.push(_t(c))
+    x0 = torch.empty(p.n, dtype=torch.float64, device=DEV)
+    info = seq.guess(A, bd, x0)
+    X = hist.matrix()
+    ref = basis.pod_guess(A_ref, b, X, m, S) if mode == "pod" else basis.rand_guess(A_ref, b, rrf, X, S)
+    x0 = x0.cpu().numpy()
+    assert info["history_cols"] == X.shape[1]
+    assert np.linalg.norm(x0 - ref.x0) <= 1e-8 * np.linalg.norm(ref.x0)
+    assert info["sketch_resid"] == pytest.approx(ref.rho_s, rel=1e-8)
+    seq.close()

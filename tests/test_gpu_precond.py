@@ -124,3 +124,25 @@ def test_preconditioner_config_checks():
                {"precond_sweeps": 2, "precond_omega": 2.0}, {"precond_sweeps": -1}):
         with pytest.raises(sa.SeqError):
             sa.Sequence(100, 4, 16, **kw)
+
+
+@pytest.mark.parametrize("restart,d", [(1, 1), (5, 2), (30, 6)])
+def test_preconditioned_gmres_on_wide_rows(restart, d):
+    """The Section 4 fourth-order operator (rows of up to 9 entries: the SELL
+    slices are wider than the unrolled width, so the sweeps take the general
+    row loop), short restarts included."""
+    from workloads import e1
+    p = e1.E1Params(N=20, dt=1e-3)
+    rowptr, colind, vals, b, _ = e1.system(p, 3)
+    A_ref = krylov.csr(rowptr, colind, vals, p.n)
+    minv = krylov.jacobi_sweeps(A_ref, d, 0.8)
+    _, it_ref, _, st_ref = krylov.gmres(A_ref, b, np.zeros(p.n), 1e-9, restart, 200000, minv=minv)
+    A = _sa().CSR(_t(rowptr, torch.int32), _t(colind, torch.int32), _t(vals))
+    seq = _sa().Sequence(p.n, 4, 16, krylov="gmres", restart=restart, max_iters=200000,
+                         precond_sweeps=d)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    info = seq.solve(A, _t(b), 1e-9, x)
+    assert info["status"] == 0 and st_ref == 0
+    assert abs(info["iters"] - it_ref) <= max(2, 0.03 * it_ref)
+    assert method.relres(A_ref, b, x.cpu().numpy()) <= 1e-9 * (1 + 1e-9)
+    seq.close()
