@@ -202,7 +202,7 @@ int seq_sketch_columns(int32_t n, int32_t s, int32_t zeta, uint64_t seed,
 /* Kernel kinds reported by seq_kernel_stats (the GMRES cycle of Algorithm 1,
  * step 4, and the stages of the guess). */
 typedef enum {
-    SEQ_K_SPMV = 0,       /* w = A v_j (CSR product)                                     */
+    SEQ_K_SPMV = 0,       /* w = A v_j (FP32 inner solves: fused with the first CGS pass) */
     SEQ_K_CGS_DOT = 1,    /* first classical Gram-Schmidt pass h1 = V^T w               */
     SEQ_K_CGS_PASS2 = 2,  /* w -= V h1 fused with the second pass h2 = V^T w             */
     SEQ_K_CGS_PASS3 = 3,  /* w -= V h2, ||w||, Givens update (basis column j+1)          */

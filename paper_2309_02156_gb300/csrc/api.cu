@@ -231,7 +231,7 @@ int capture_cycle(seq_ctx* ctx, bool prof) {
     const double om = ctx->cfg.precond_omega;
     if (prof) {
         if (ctx->ev.empty()) {
-            ctx->ev.resize(cycle_kernels(R, sw) + 1);
+            ctx->ev.resize(cycle_kernels(R, sw, ctx->mixed) + 1);
             for (auto& e : ctx->ev) CK(cudaEventCreate(&e));
         }
         ev = ctx->ev.data();
@@ -281,7 +281,7 @@ void account_cycle(seq_ctx* ctx, bool f32, int jd, bool updated, int nnz) {
     const double ns = (ctx->cfg.n + 31) / 32;
     const double spmv_mat = ctx->sell_ok ? 4.0 * (ns + 1) + (4.0 + E) * (double)*ctx->h_int : csr;
     const int sw = ctx->cfg.precond_sweeps;
-    const int S = kKernelsPerStep + sw;
+    const int S = step_kernels(f32) + sw;
     // Preconditioner: the scale reads u, dinv and writes z; a sweep reads the
     // matrix, z (gathered), u, dinv and writes the next z.
     auto precond = [&](int ev0) {
@@ -291,10 +291,17 @@ void account_cycle(seq_ctx* ctx, bool f32, int jd, bool updated, int nnz) {
     };
     for (int j = 0; j < jd; ++j) {
         const double nk = j + 1;
-        const int e = S * j + sw;
+        int e = S * j + sw;
         if (sw > 0) precond(S * j);
-        add_stat(ctx, SEQ_K_SPMV, e, spmv_mat + 2.0 * E * n, 2.0 * nnz + n);
-        add_stat(ctx, SEQ_K_CGS_DOT, e + 1, E * n * (nk + 1), 2.0 * n * nk);
+        if (f32) {
+            // fused SpMV + first-pass dots: matrix, gathered vector, w written
+            // once, basis columns 0..j (w re-read from cache, not counted)
+            add_stat(ctx, SEQ_K_SPMV, e, spmv_mat + E * n * (nk + 2), 2.0 * nnz + n + 2.0 * n * nk);
+            e -= 1;
+        } else {
+            add_stat(ctx, SEQ_K_SPMV, e, spmv_mat + 2.0 * E * n, 2.0 * nnz + n);
+            add_stat(ctx, SEQ_K_CGS_DOT, e + 1, E * n * (nk + 1), 2.0 * n * nk);
+        }
         add_stat(ctx, SEQ_K_CGS_PASS2, e + 2, E * n * (nk + 2), 4.0 * n * nk);
         add_stat(ctx, SEQ_K_CGS_PASS3, e + 3, E * n * (nk + 2), 2.0 * n * nk + 2.0 * n);
     }

@@ -56,12 +56,15 @@ void launch_pod_coeff(const LsqOut* red, const double* Vk, int mi, int kk, int M
 
 // krylov.cu
 int stream_grid(int n);
+// Arnoldi kernels per step: FP64 SpMV, first-pass dots, pass 2, pass 3; FP32
+// fuses the SpMV with the first-pass dots.
+inline int step_kernels(bool f32) { return f32 ? kKernelsPerStep - 1 : kKernelsPerStep; }
 // Kernels of one restart cycle: per Arnoldi step the preconditioner's
-// `sweeps` kernels (scale + sweeps - 1 sweeps) and the four Arnoldi kernels;
-// then the update (combine, preconditioner, axpy; or one update kernel) and
-// the restart residual.
-inline int cycle_kernels(int R, int sweeps) {
-    return (kKernelsPerStep + sweeps) * R + (sweeps > 0 ? sweeps + 2 : 1) + 1;
+// `sweeps` kernels (scale + sweeps - 1 sweeps) and the Arnoldi kernels; then
+// the update (combine, preconditioner, axpy; or one update kernel) and the
+// restart residual.
+inline int cycle_kernels(int R, int sweeps, bool f32) {
+    return (step_kernels(f32) + sweeps) * R + (sweeps > 0 ? sweeps + 2 : 1) + 1;
 }
 // ||b - A x|| and ||b|| of FP64 vectors; results in st->beta, st->bnorm and
 // st->first_relres = beta / bnorm.

@@ -906,18 +906,43 @@ __device__ __forceinline__ void f32_rows(const float* __restrict__ V, size_t ldv
     }
 }
 
+// FP32 w = A v_j (or A src, the preconditioned vector) fused with the first
+// CGS pass h1 = V^T w: each block forms w on its own rows (SELL-32 product,
+// warp per slice), then, after a block barrier, reads those rows back (from
+// cache) together with the basis columns.  Saves a launch and a pass over w.
 template <int NK>
 __global__ void __launch_bounds__(kStreamBlock, 1)
-f32_dot_kernel(const DevArgs* __restrict__ a, KState* ks, const float* __restrict__ V, size_t ldv,
-               const float* __restrict__ w, float* partial, int j) {
+f32_spmv_dot_kernel(const DevArgs* __restrict__ a, KState* ks, const float* __restrict__ V,
+                    size_t ldv, float* __restrict__ w, float* partial, int j, const float* src) {
     if (ks->cycle_over) return;
     __shared__ float wsum[kWarps * NK];
+    const int n = a->n;
+    const float sig = src ? 1.f : (float)ks->sigma[j];
+    const float* vj = src ? src : V + (size_t)j * ldv;
     int lo, hi;
-    block_rows(a->n, gridDim.x, blockIdx.x, lo, hi);
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    if (a->sell_off) {
+        sell_spmv_rows<float>(a->sell_off, a->sell_col, reinterpret_cast<const float*>(a->sell_val),
+                              vj, n, lo, hi, sig, w, kWarps, &ks->bad_index);
+    } else {                                      // no SELL copy: CSR, one row per thread
+        const float* val = a->val32;
+        int flag = 0;
+        for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) {
+            float acc = 0.f;
+            for (int e = a->rowptr[r]; e < a->rowptr[r + 1]; ++e) {
+                const int c = a->colind[e];
+                if ((unsigned)c < (unsigned)n) acc = fmaf(val[e], vj[c], acc);
+                else flag = 1;
+            }
+            w[r] = acc * sig;
+        }
+        if (flag) atomicOr(&ks->bad_index, 1);
+    }
+    __syncthreads();
     float part[NK];
 #pragma unroll
     for (int k = 0; k < NK; ++k) part[k] = 0.f;
-    f32_rows<NK, 0>(V, ldv, const_cast<float*>(w), nullptr, nullptr, lo, hi, part);
+    f32_rows<NK, 0>(V, ldv, w, nullptr, nullptr, lo, hi, part);
     block_columns<float, NK>(part, NK, wsum, partial + (size_t)blockIdx.x * kMaxBasis);
     if (last_block_arrive(&ks->counter[CNT_DOT])) {
         __shared__ double tot[NK];
@@ -1021,16 +1046,16 @@ static void launch_step(const DevArgs* a, KState* ks, typename Sys::T* V, size_t
     const typename Sys::T* src = nullptr;
     if (pc.sweeps > 0)
         src = launch_precond<Sys>(a, ks, pc, V + (size_t)j * ldv, j, 0, nblk, st, ev, k);
-    arnoldi_spmv_kernel<Sys><<<nblk, kSpmvBlock, spmv_smem<Sys>(), st>>>(a, ks, V, ldv, w, j, src);
-    mark(ev, k, st);
     if constexpr (sizeof(typename Sys::T) == 4) {
-        f32_dot_kernel<NK><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j);
+        f32_spmv_dot_kernel<NK><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j, src);
         mark(ev, k, st);
         f32_pass2_kernel<NK><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j);
         mark(ev, k, st);
         f32_pass3_kernel<NK><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j, R);
         mark(ev, k, st);
     } else {
+        arnoldi_spmv_kernel<Sys><<<nblk, kSpmvBlock, spmv_smem<Sys>(), st>>>(a, ks, V, ldv, w, j, src);
+        mark(ev, k, st);
         arnoldi_dot_kernel<Sys><<<nblk, kDotBlock, 0, st>>>(a, ks, V, ldv, w, partial, j, kMaxBasis);
         mark(ev, k, st);
         arnoldi_pass2_kernel<Sys, NK><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j);
@@ -1061,10 +1086,11 @@ struct StepTable<Sys, kMaxRestart + 1> {
 
 // One restart cycle.  With `ev` (cycle_kernels + 1 timing events) an event is
 // recorded before the first kernel and after every kernel: kernel i of the
-// cycle lies between ev[i] and ev[i + 1].  With S = 4 + sweeps kernels per
-// Arnoldi step j: S j .. S j + sweeps - 1 the preconditioner, then SpMV,
-// first-pass dots, pass 2, pass 3; from S R the update kernels (one, or
-// combine + sweeps + axpy), then the restart residual.
+// cycle lies between ev[i] and ev[i + 1].  With S = step_kernels + sweeps
+// kernels per Arnoldi step j: S j .. S j + sweeps - 1 the preconditioner, then
+// SpMV, first-pass dots, pass 2, pass 3 (FP32: SpMV with the dots, pass 2,
+// pass 3); from S R the update kernels (one, or combine + sweeps + axpy), then
+// the restart residual.
 template <class Sys>
 static void launch_cycle(const DevArgs* a, KState* ks, typename Sys::T* V, size_t ldv,
                          typename Sys::T* w, typename Sys::T* partial, int nblk, int R,
@@ -1086,7 +1112,7 @@ static void launch_cycle(const DevArgs* a, KState* ks, typename Sys::T* V, size_
     }
     gmres_start_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, partial, 0);
     mark(ev, &k, st);
-    if (launches) *launches = cycle_kernels(R, pc.sweeps);
+    if (launches) *launches = cycle_kernels(R, pc.sweeps, sizeof(typename Sys::T) == 4);
 }
 
 }  // namespace sa
