@@ -632,146 +632,7 @@ gmres_update_kernel(const DevArgs* __restrict__ a, const KState* ks,
     }
 }
 
-// ---------------------------------------------------------------------------
-// Right preconditioning (optional): GMRES runs on A M^{-1}, the cycle's
-// correction is x += M^{-1} (V y), so the residual GMRES minimises and tests
-// is the true one.  M^{-1} u = `sweeps` damped Jacobi sweeps on A z = u from
-// z = 0:  z_1 = omega D^{-1} u,  z_{k+1} = z_k + omega D^{-1} (u - A z_k)
-// (a fixed polynomial in D^{-1} A times D^{-1}).  Phase 0 kernels belong to an
-// Arnoldi step (skipped once the cycle is over), phase 1 kernels to the basis
-// update (skipped like the update).
-__device__ __forceinline__ bool update_skipped(const KState* ks) {
-    return (ks->status != ST_OK && ks->status != ST_NOT_CONVERGED) || ks->finished;
-}
-__device__ __forceinline__ bool precond_skipped(const KState* ks, int phase) {
-    return phase == 0 ? ks->cycle_over != 0 : update_skipped(ks);
-}
-
-// dinv = 1 / diag(A) in the system's precision (1 where the diagonal is
-// missing or zero).
-template <class Sys>
-__global__ void __launch_bounds__(kStreamBlock)
-diag_inv_kernel(const DevArgs* __restrict__ a, typename Sys::T* __restrict__ dinv) {
-    using T = typename Sys::T;
-    const T* val = Sys::val(a);
-    const int n = a->n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        T d = 0;
-        for (int e = a->rowptr[i]; e < a->rowptr[i + 1]; ++e)
-            if (a->colind[e] == i) d = val[e];
-        dinv[i] = d != (T)0 ? (T)1 / d : (T)1;
-    }
-}
-
-// z = (omega dinv) (s u), s = sigma_{sig_idx} (a stored basis column) or 1.
-template <class Sys>
-__global__ void __launch_bounds__(kStreamBlock)
-precond_scale_kernel(const DevArgs* __restrict__ a, const KState* __restrict__ ks,
-                     const typename Sys::T* __restrict__ u, int sig_idx,
-                     const typename Sys::T* __restrict__ dinv, double omega,
-                     typename Sys::T* __restrict__ z, int phase) {
-    using T = typename Sys::T;
-    if (precond_skipped(ks, phase)) return;
-    const T sc = sig_idx >= 0 ? (T)ks->sigma[sig_idx] : (T)1, om = (T)omega;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a->n; i += gridDim.x * blockDim.x)
-        z[i] = (om * dinv[i]) * (sc * u[i]);
-}
-
-template <typename T>
-struct SweepEpi {
-    const T* zin;
-    const T* u;
-    const T* dinv;
-    T sc, om;
-    T* zout;
-    __device__ void operator()(int r, T ax) const {
-        zout[r] = zin[r] + (om * dinv[r]) * (sc * u[r] - ax);
-    }
-};
-
-// z_out = z_in + (omega dinv) (s u - A z_in).
-template <class Sys>
-__global__ void __launch_bounds__(kSpmvBlock, 1)
-precond_sweep_kernel(const DevArgs* __restrict__ a, KState* ks, const typename Sys::T* __restrict__ u,
-                     int sig_idx, const typename Sys::T* __restrict__ dinv, double omega,
-                     const typename Sys::T* __restrict__ zin, typename Sys::T* __restrict__ zout,
-                     int phase) {
-    using T = typename Sys::T;
-    if (precond_skipped(ks, phase)) return;
-    const T sc = sig_idx >= 0 ? (T)ks->sigma[sig_idx] : (T)1, om = (T)omega;
-    const int n = a->n;
-    int lo, hi;
-    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
-    const SweepEpi<T> epi{zin, u, dinv, sc, om, zout};
-    if (a->sell_off) {
-        sell_rows<T>(a->sell_off, a->sell_col, reinterpret_cast<const T*>(a->sell_val), zin, n, lo,
-                     hi, kSpmvWarps, &ks->bad_index, epi);
-        return;
-    }
-    const T* val = Sys::val(a);
-    int flag = 0;
-    for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) {
-        T ax = 0;
-        for (int e = a->rowptr[r]; e < a->rowptr[r + 1]; ++e) {
-            const int c = a->colind[e];
-            if ((unsigned)c < (unsigned)n) ax = fma(val[e], zin[c], ax);
-            else flag = 1;
-        }
-        epi(r, ax);
-    }
-    if (flag) atomicOr(&ks->bad_index, 1);
-}
-
-// t = V_stored cy (the cycle's correction before preconditioning).
-template <class Sys>
-__global__ void __launch_bounds__(kStreamBlock, 1)
-gmres_combine_kernel(const DevArgs* __restrict__ a, const KState* ks,
-                     const typename Sys::T* __restrict__ V, size_t ldv, typename Sys::T* __restrict__ t) {
-    using T = typename Sys::T;
-    if (update_skipped(ks)) return;
-    __shared__ T cy[kMaxBasis];
-    __shared__ int kk;
-    if (threadIdx.x == 0) kk = ks->jdone;
-    for (int k = threadIdx.x; k < kMaxBasis; k += blockDim.x) cy[k] = (T)ks->cy[k];
-    __syncthreads();
-    const int k = kk, n = a->n;
-    int lo, hi;
-    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
-    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        T acc = 0;
-        for (int l = 0; l < k; ++l) acc = fma(V[(size_t)l * ldv + i], cy[l], acc);
-        t[i] = acc;
-    }
-}
-
-// x += z.
-template <class Sys>
-__global__ void __launch_bounds__(kStreamBlock)
-gmres_axpy_kernel(const DevArgs* __restrict__ a, const KState* ks, const typename Sys::T* __restrict__ z) {
-    using T = typename Sys::T;
-    if (update_skipped(ks)) return;
-    T* x = Sys::x(a);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a->n; i += gridDim.x * blockDim.x)
-        x[i] += z[i];
-}
-
-template <typename T>
-struct PrecondArgs {
-    int sweeps = 0;            // 0: no preconditioner
-    double omega = 1.0;
-    const T* dinv = nullptr;
-    T* za = nullptr;           // sweep ping-pong vectors
-    T* zb = nullptr;
-    T* t = nullptr;            // correction before preconditioning
-};
-
-// Applies M^{-1} to s u (phase 0: u = basis column sig_idx; phase 1: u = t);
-// returns the vector holding the result.
-template <class Sys>
-static const typename Sys::T* launch_precond(const DevArgs* a, KState* ks,
-                                             const PrecondArgs<typename Sys::T>& pc,
-                                             const typename Sys::T* u, int sig_idx, int phase,
-                                             int nblk, cudaStream_t st, cudaEvent_t* ev, int* k);
+#include "precond_kernels.cuh"
 
 template <class Sys>
 static void launch_start(const DevArgs* a, KState* ks, typename Sys::T* V, typename Sys::T* partial,
@@ -792,224 +653,7 @@ static size_t spmv_smem() {
     return bytes;
 }
 
-// ---------------------------------------------------------------------------
-// FP32 CGS kernels (inner solves of the mixed forms).  In FP32 the passes are
-// bound by memory, not by arithmetic, so they are organised for bytes in
-// flight: each thread owns VW consecutive rows and reads them from every
-// basis column with one VW-wide vector load (a warp reads 32 VW 4-byte values
-// of a column per instruction), U vectors per iteration; the row-parallel
-// layout replaces the column-segment dot kernel of FP64.  Rows past the last
-// full vector of the block's range are handled one per thread.  Reductions:
-// per-thread partials over its rows, warp reduce-scatter, warps in order,
-// blocks in order in the last block (deterministic).
-template <int VW> struct F32x;
-template <> struct F32x<1> {
-    using type = float;
-    __device__ static void get(const float* p, float (&o)[1]) { o[0] = *p; }
-    __device__ static void put(float* p, const float (&o)[1]) { *p = o[0]; }
-};
-template <> struct F32x<2> {
-    using type = float2;
-    __device__ static void get(const float* p, float (&o)[2]) {
-        const float2 v = *reinterpret_cast<const float2*>(p);
-        o[0] = v.x; o[1] = v.y;
-    }
-    __device__ static void put(float* p, const float (&o)[2]) {
-        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
-    }
-};
-template <> struct F32x<4> {
-    using type = float4;
-    __device__ static void get(const float* p, float (&o)[4]) {
-        const float4 v = *reinterpret_cast<const float4*>(p);
-        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-    }
-    __device__ static void put(float* p, const float (&o)[4]) {
-        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
-    }
-};
-template <int NK> struct F32Shape {
-    static constexpr int VW = NK >= 32 ? 1 : (NK >= 12 ? 2 : 4);
-    static constexpr int per = (NK + 1) * VW;                 // floats loaded per vector
-    static constexpr int U = per >= 32 ? 1 : (32 + per - 1) / per;
-};
-
-// MODE 0: part[k] = sum v_k w (first CGS pass, h1).
-// MODE 1: r = w - sum_k v_k c1_k, w = r, part[k] = sum v_k r (fused pass 2).
-// MODE 2: r = w - sum_k v_k c2_k, v_{j+1} = r, part[0] = sum r^2 (pass 3).
-template <int NK, int MODE>
-__device__ __forceinline__ void f32_rows(const float* __restrict__ V, size_t ldv, float* w,
-                                         float* vout, const float* cf, int lo, int hi,
-                                         float (&part)[NK]) {
-    constexpr int VW = F32Shape<NK>::VW, U = F32Shape<NK>::U;
-    using X = F32x<VW>;
-    const int bd = blockDim.x;
-    const int hv = lo + ((hi - lo) / VW) * VW;               // end of the full vectors
-    for (int i0 = lo + threadIdx.x * VW; i0 < hv; i0 += U * bd * VW) {
-        float vv[U][NK][VW];
-        float r[U][VW];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int i = min(i0 + u * bd * VW, hv - VW);
-#pragma unroll
-            for (int k = 0; k < NK; ++k) X::get(V + (size_t)k * ldv + i, vv[u][k]);
-            X::get(w + i, r[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int i = i0 + u * bd * VW;
-            if (i >= hv) continue;
-            if constexpr (MODE == 0) {
-#pragma unroll
-                for (int k = 0; k < NK; ++k)
-#pragma unroll
-                    for (int e = 0; e < VW; ++e) part[k] = fmaf(vv[u][k][e], r[u][e], part[k]);
-            } else {
-#pragma unroll
-                for (int e = 0; e < VW; ++e)
-#pragma unroll
-                    for (int k = 0; k < NK; ++k) r[u][e] = fmaf(-vv[u][k][e], cf[k], r[u][e]);
-                if constexpr (MODE == 1) {
-                    X::put(w + i, r[u]);
-#pragma unroll
-                    for (int k = 0; k < NK; ++k)
-#pragma unroll
-                        for (int e = 0; e < VW; ++e) part[k] = fmaf(vv[u][k][e], r[u][e], part[k]);
-                } else {
-                    X::put(vout + i, r[u]);
-#pragma unroll
-                    for (int e = 0; e < VW; ++e) part[0] = fmaf(r[u][e], r[u][e], part[0]);
-                }
-            }
-        }
-    }
-    for (int i = hv + threadIdx.x; i < hi; i += bd) {        // ragged tail, one row per thread
-        float rr = w[i];
-        if constexpr (MODE == 0) {
-#pragma unroll
-            for (int k = 0; k < NK; ++k) part[k] = fmaf(V[(size_t)k * ldv + i], rr, part[k]);
-        } else {
-            float vk[NK];
-#pragma unroll
-            for (int k = 0; k < NK; ++k) vk[k] = V[(size_t)k * ldv + i];
-#pragma unroll
-            for (int k = 0; k < NK; ++k) rr = fmaf(-vk[k], cf[k], rr);
-            if constexpr (MODE == 1) {
-                w[i] = rr;
-#pragma unroll
-                for (int k = 0; k < NK; ++k) part[k] = fmaf(vk[k], rr, part[k]);
-            } else {
-                vout[i] = rr;
-                part[0] = fmaf(rr, rr, part[0]);
-            }
-        }
-    }
-}
-
-// FP32 w = A v_j (or A src, the preconditioned vector) fused with the first
-// CGS pass h1 = V^T w: each block forms w on its own rows (SELL-32 product,
-// warp per slice), then, after a block barrier, reads those rows back (from
-// cache) together with the basis columns.  Saves a launch and a pass over w.
-template <int NK>
-__global__ void __launch_bounds__(kStreamBlock, 1)
-f32_spmv_dot_kernel(const DevArgs* __restrict__ a, KState* ks, const float* __restrict__ V,
-                    size_t ldv, float* __restrict__ w, float* partial, int j, const float* src) {
-    if (ks->cycle_over) return;
-    __shared__ float wsum[kWarps * NK];
-    const int n = a->n;
-    const float sig = src ? 1.f : (float)ks->sigma[j];
-    const float* vj = src ? src : V + (size_t)j * ldv;
-    int lo, hi;
-    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
-    if (a->sell_off) {
-        sell_spmv_rows<float>(a->sell_off, a->sell_col, reinterpret_cast<const float*>(a->sell_val),
-                              vj, n, lo, hi, sig, w, kWarps, &ks->bad_index);
-    } else {                                      // no SELL copy: CSR, one row per thread
-        const float* val = a->val32;
-        int flag = 0;
-        for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) {
-            float acc = 0.f;
-            for (int e = a->rowptr[r]; e < a->rowptr[r + 1]; ++e) {
-                const int c = a->colind[e];
-                if ((unsigned)c < (unsigned)n) acc = fmaf(val[e], vj[c], acc);
-                else flag = 1;
-            }
-            w[r] = acc * sig;
-        }
-        if (flag) atomicOr(&ks->bad_index, 1);
-    }
-    __syncthreads();
-    float part[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) part[k] = 0.f;
-    f32_rows<NK, 0>(V, ldv, w, nullptr, nullptr, lo, hi, part);
-    block_columns<float, NK>(part, NK, wsum, partial + (size_t)blockIdx.x * kMaxBasis);
-    if (last_block_arrive(&ks->counter[CNT_DOT])) {
-        __shared__ double tot[NK];
-        reduce_blocks(partial, gridDim.x, kMaxBasis, NK, tot);
-        for (int k = threadIdx.x; k < NK; k += blockDim.x) {
-            const double hk = ks->sigma[k] * tot[k];
-            ks->h1[k] = hk;
-            ks->c1[k] = ks->sigma[k] * hk;
-        }
-        if (threadIdx.x == 0) ks->counter[CNT_DOT] = 0;
-    }
-}
-
-template <int NK>
-__global__ void __launch_bounds__(kStreamBlock, 1)
-f32_pass2_kernel(const DevArgs* __restrict__ a, KState* ks, const float* __restrict__ V, size_t ldv,
-                 float* __restrict__ w, float* partial, int j) {
-    if (ks->cycle_over) return;
-    __shared__ float cf[NK];
-    __shared__ float wsum[kWarps * NK];
-    for (int k = threadIdx.x; k < NK; k += blockDim.x) cf[k] = (float)ks->c1[k];
-    __syncthreads();
-    int lo, hi;
-    block_rows(a->n, gridDim.x, blockIdx.x, lo, hi);
-    float part[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) part[k] = 0.f;
-    f32_rows<NK, 1>(V, ldv, w, nullptr, cf, lo, hi, part);
-    block_columns<float, NK>(part, NK, wsum, partial + (size_t)blockIdx.x * kMaxBasis);
-    if (last_block_arrive(&ks->counter[CNT_PASS2])) {
-        __shared__ double tot[NK];
-        reduce_blocks(partial, gridDim.x, kMaxBasis, NK, tot);
-        for (int k = threadIdx.x; k < NK; k += blockDim.x) {
-            const double hk = ks->sigma[k] * tot[k];
-            ks->h2[k] = hk;
-            ks->c2[k] = ks->sigma[k] * hk;
-        }
-        if (threadIdx.x == 0) ks->counter[CNT_PASS2] = 0;
-    }
-}
-
-template <int NK>
-__global__ void __launch_bounds__(kStreamBlock, 1)
-f32_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, float* __restrict__ V, size_t ldv,
-                 const float* __restrict__ w, float* partial, int j, int R) {
-    if (ks->cycle_over) return;
-    __shared__ float cf[NK];
-    __shared__ float scratch[kWarps];
-    __shared__ float red[1];
-    for (int k = threadIdx.x; k < NK; k += blockDim.x) cf[k] = (float)ks->c2[k];
-    __syncthreads();
-    int lo, hi;
-    block_rows(a->n, gridDim.x, blockIdx.x, lo, hi);
-    float part[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) part[k] = 0.f;
-    f32_rows<NK, 2>(V, ldv, const_cast<float*>(w), V + (size_t)(j + 1) * ldv, cf, lo, hi, part);
-    float p1[1] = {part[0]};
-    block_sum<float, 1>(p1, 1, red, scratch);
-    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
-    if (last_block_arrive(&ks->counter[CNT_PASS3])) {
-        __shared__ double tot[1];
-        reduce_blocks(partial, gridDim.x, 1, 1, tot);
-        if (threadIdx.x == 0) ks->counter[CNT_PASS3] = 0;
-        arnoldi_finish(ks, a, j, R, tot[0]);
-    }
-}
+#include "krylov_f32_kernels.cuh"
 
 // Records ev[*k] (when timing events are supplied) and advances *k.
 inline void mark(cudaEvent_t* ev, int* k, cudaStream_t st) {
