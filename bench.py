@@ -102,6 +102,23 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def max_over_ranks(ms, dist=None, device=None):
+    """The slowest rank's time in ms (every rank receives it); the time itself
+    with a single process."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ms, world):
+    """Units per second of the whole job: all ranks' units over the slowest
+    rank's time (replicas: every rank processes the same number of units)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -915,14 +932,10 @@ def main():
     clocks = sampler.stop()
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     stats = seq.kernel_stats(reset=True)
     seq.set_profiling(False)
-    value = world * K / (ms / 1e3)
+    value = whole_job_rate(K, ms, world)
     iters = [inf["iters"] for _, inf in infos]
     launches = sum(g["launches"] + inf["launches"] + 1 for g, inf in infos)
     worst = max(inf["final_relres"] for _, inf in infos)
@@ -984,12 +997,8 @@ def main():
         x_h.copy_(x, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e2.elapsed_time(e3)
-    if dist:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = t.item()
-    e2e_value = world * K / (ms_e2e / 1e3)
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3), dist, dev)
+    e2e_value = whole_job_rate(K, ms_e2e, world)
 
     # Other forms on the same systems, each with its own priming: the mixed
     # form (FP64 history, sketch and guess, FP32 GMRES(30) inner solves inside
@@ -1014,11 +1023,7 @@ def main():
         cinfos = [step(i) for i in range(M_HIST + W, M_HIST + W + K)]
         c1.record(stream)
         torch.cuda.synchronize()
-        cms = c0.elapsed_time(c1)
-        if dist:
-            t = torch.tensor([cms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            cms = t.item()
+        cms = max_over_ranks(c0.elapsed_time(c1), dist, dev)
         cst = seq.kernel_stats(reset=True)
         seq.set_profiling(False)
         assert all(inf["status"] == 0 for _, inf in cinfos), "a %s solve did not converge" % label
@@ -1027,13 +1032,13 @@ def main():
         ct = cs["ms"] / 1e3 / max(cs["launches"], 1)
         cb = cs["bytes"] / max(cs["launches"], 1)
         return {
-            "form": label, "value": world * K / (cms / 1e3), "unit": "systems/s",
+            "form": label, "value": whole_job_rate(K, cms, world), "unit": "systems/s",
             "ms_per_step": cms / K,
             "dtype": "f32 inner + f64 refinement" if precision != "f64" else "f64",
             "iters_per_system": float(np.mean([inf["iters"] for _, inf in cinfos])),
             "refinements_per_system": float(np.mean([inf["refinements"] for _, inf in cinfos])),
             "final_relres_max": max(inf["final_relres"] for _, inf in cinfos),
-            "vs_plain": (world * K / (cms / 1e3)) / value,
+            "vs_plain": whole_job_rate(K, cms, world) / value,
             "roofline": {"bound": "hbm", "kernel": cdom, "achieved": cb / ct / 1e9,
                          "peak": hbm_peak, "unit": "GB/s", "frac": cb / ct / 1e9 / hbm_peak,
                          "launch_us": ct * 1e6, "algorithmic_bytes_per_launch": cb},
