@@ -87,7 +87,11 @@ class History:
 
 
 def relres(A, b, x) -> float:
-    return float(np.linalg.norm(b - A @ x) / np.linalg.norm(b))
+    """||b - A x|| / ||b||; the absolute residual when b = 0 (then undefined
+    relative to b; x = 0 solves the system exactly)."""
+    rn = float(np.linalg.norm(b - A @ x))
+    bn = float(np.linalg.norm(b))
+    return rn / bn if bn > 0 else rn
 
 
 def solve_step(A, b, hist: History, S, tol: float, krylov_kind: str,

@@ -360,7 +360,7 @@ int run_gmres(seq_ctx* ctx, bool f32) {
 void fill_info(seq_info* info, const KState* t) {
     if (!info) return;
     info->guess_relres = t->first_relres;
-    info->final_relres = t->bnorm > 0 ? t->beta / t->bnorm : t->beta;
+    info->final_relres = rel_residual(t->beta, t->bnorm);
     info->iters = t->iters;
     info->status = t->status;
 }
@@ -788,7 +788,7 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
         rc = read_tail(ctx, ctx->ks);
         if (rc) return rc;
         const double bnorm = ctx->h_ks->bnorm, target = ctx->h_ks->target;
-        const double first = ctx->h_ks->beta / bnorm;
+        const double first = rel_residual(ctx->h_ks->beta, bnorm);
         double beta = ctx->h_ks->beta;
         int bad = ctx->h_ks->bad_index;
         status = SEQ_OK;
@@ -797,7 +797,7 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
         // u32 cond(A) ||r||, which stalls restarts on ill-conditioned systems).
         // Each refinement costs at least one iteration, so max_iters bounds them.
         const int max_ref = c.krylov == SEQ_GMRES ? c.max_iters + 1 : 100;
-        while (beta > target) {
+        while (!(beta <= target)) {           // a NaN residual enters and is reported
             if (!isfinite(beta)) {
                 status = SEQ_ENONFINITE;
                 break;
@@ -845,7 +845,7 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
             info->iters = total;
             info->refinements = refinements;
             info->guess_relres = first;
-            info->final_relres = beta / bnorm;
+            info->final_relres = rel_residual(beta, bnorm);
             info->status = status;
         }
         if (bad) status = SEQ_EINVAL;

@@ -136,6 +136,12 @@ __device__ __forceinline__ T sum_over_blocks(const T* partial, int nblk, int str
 }
 
 // SplitMix64 output finaliser (Steele, Lea, Flood 2014; variant-13 mixer).
+// ||r|| / ||b||, or ||r|| itself when b = 0 (the relative residual is then
+// undefined; x = 0 is the exact solution and has residual 0).
+__host__ __device__ __forceinline__ double rel_residual(double rnorm, double bnorm) {
+    return bnorm > 0.0 ? rnorm / bnorm : rnorm;
+}
+
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;

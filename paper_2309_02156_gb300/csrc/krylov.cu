@@ -47,7 +47,7 @@ residual_norm_kernel(const DevArgs* __restrict__ a, KState* ks, double* partial,
         if (threadIdx.x == 0) {
             ks->beta = sqrt(tot[0]);
             ks->bnorm = sqrt(tot[1]);
-            ks->first_relres = sqrt(tot[0]) / sqrt(tot[1]);
+            ks->first_relres = rel_residual(sqrt(tot[0]), sqrt(tot[1]));
             ks->counter[CNT_RES] = 0;
         }
     }
@@ -304,9 +304,11 @@ cg_block_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* r, t
     const T bb = block_total(bb_l, sred);
     const double bnorm = sqrt((double)bb);
     const double target = a->tol * bnorm;
-    const double first = sqrt((double)rr) / bnorm;
+    const double first = rel_residual(sqrt((double)rr), bnorm);
     int it = 0, status = ST_OK;
-    if (sqrt((double)rr) > target) {
+    if (!isfinite((double)rr) || !isfinite(bnorm)) {
+        status = ST_NONFINITE;
+    } else if (sqrt((double)rr) > target) {
         for (;;) {
             if (it >= a->max_iters) {
                 status = ST_NOT_CONVERGED;

@@ -102,7 +102,7 @@ gmres_start_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* V
                 ks->target = a->tol * ks->bnorm;
                 ks->iters = 0;
                 ks->status = ST_OK;
-                ks->first_relres = beta / ks->bnorm;
+                ks->first_relres = rel_residual(beta, ks->bnorm);
             }
             ks->last_jdone = first ? 0 : ks->jdone;
             ks->beta = beta;

@@ -301,3 +301,31 @@ def test_repeatable_bit_for_bit():
         outs.append(x.cpu().numpy().copy())
         seq.close()
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("krylov_kind,precision", [("gmres", "f64"), ("cg", "f64"), ("gmres", "mixed_krylov")])
+def test_zero_and_nonfinite_right_hand_sides(krylov_kind, precision):
+    """b = 0: the sketched guess is x0 = 0 (w_b = 0), the system is solved with
+    0 iterations and the (absolute) residual 0; a NaN in b is reported as
+    SEQ_ENONFINITE, not iterated on."""
+    sa = _sa()
+    p = workloads.plain_spd(12) if krylov_kind == "cg" else workloads.plain_nonsym(12)
+    rowptr, colind, vals, b = workloads.csr_system(p, 1)
+    Ad, _ = _dev_system(rowptr, colind, vals, b)
+    seq = sa.Sequence(p.n, 4, 16, zeta=4, krylov=krylov_kind, precision=precision)
+    rng = np.random.default_rng(0)
+    for _ in range(4):
+        seq.push(_tensor(rng.standard_normal(p.n)))
+    zero = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    x = torch.full((p.n,), 3.0, dtype=torch.float64, device=DEV)
+    g = seq.guess(Ad, zero, x)
+    assert torch.all(x == 0) and g["guess_relres"] == 0.0
+    info = seq.solve(Ad, zero, 1e-10, x)
+    assert info["status"] == 0 and info["iters"] == 0 and info["final_relres"] == 0.0
+    bn = torch.from_numpy(b.copy()).to(DEV)
+    bn[5] = float("nan")
+    x.zero_()
+    with pytest.raises(sa.SeqError) as e:
+        seq.solve(Ad, bn, 1e-10, x)
+    assert e.value.code == -5
+    seq.close()
