@@ -151,16 +151,26 @@ int seq_history_size(const seq_ctx* ctx);
 /* Initial guess for A x = b (Algorithm 1, steps 1-3, with the sketched reduced
  * problem; or the guess mode chosen in the config).  Writes x0_dev (device, n
  * FP64).  With an empty history x0 = 0; with m < M columns the m available
- * ones are used.  Fills info (guess_relres, sketch_resid, rank, history_cols).
- * Synchronises the stream.  Errors: SEQ_EINVAL, SEQ_ECUDA. */
+ * ones are used.  Fills info (guess_relres, sketch_resid, rank, history_cols;
+ * net_resid in SEQ_GUESS_LEARNED).  guess_relres is ||b - A x0|| / ||b||, or
+ * ||b - A x0|| when b = 0.  Synchronises the stream.
+ * Returns SEQ_OK, or SEQ_FALLBACK_USED (learned mode: the network's y was
+ * rejected and the least-squares y used; x0 is valid).
+ * Errors: SEQ_EINVAL (bad argument or column index), SEQ_ENONFINITE (NaN or
+ * Inf in the residual of the guess), SEQ_ECUDA. */
 int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev,
               double* x0_dev, seq_info* info);
 
 /* Krylov solve from x_dev (Algorithm 1, step 4): on entry x_dev holds the
  * starting vector, on exit the iterate with ||b - A x|| <= tol ||b|| (status
  * SEQ_OK) or the last iterate (SEQ_NOT_CONVERGED after max_iters iterations).
- * CG or GMRES(restart) with CGS2 per the config; SEQ_MIXED runs FP32 inner
- * solves inside FP64 iterative refinement.  Does not push x.  Synchronises. */
+ * CG or GMRES(restart) with CGS2 per the config, optionally right-
+ * preconditioned (precond_sweeps); the mixed precisions run FP32 inner solves
+ * inside FP64 iterative refinement of the true residual (a GMRES inner solve
+ * is one restart cycle).  With b = 0 the test is ||b - A x|| <= 0 and x = 0
+ * passes it.  Does not push x.  Synchronises.
+ * Errors: SEQ_EINVAL, SEQ_EBREAKDOWN (CG p^T A p <= 0, singular Hessenberg),
+ * SEQ_ENONFINITE (NaN or Inf met), SEQ_ETIMEOUT (host cycle bound), SEQ_ECUDA. */
 int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol,
               double* x_dev, seq_info* info);
 
