@@ -524,6 +524,52 @@ def learned_ablation(args):
     net.close()
 
 
+def spd_small(steps=60):
+    """The 64 x 64 SPD sequence (n = 4096, M = 10, s = 40, CG to 1e-10, 60
+    systems): the sketched guess against the previous-solution guess (the
+    paper's baseline), each in its own sequence; CG iterations and device time
+    per system over systems M..59 (this size is L2- and latency-bound, so the
+    time per system, not an HBM fraction, is the figure)."""
+    import numpy as np
+    import torch
+    import paper_2309_02156_gb300 as sa
+    import workloads
+    dev = torch.device("cuda", torch.cuda.current_device())
+    p = workloads.plain_spd(64)
+    M, S = 10, 40
+    systems = []
+    for i in range(steps):
+        rowptr, colind, vals, b = workloads.csr_system(p, i)
+        systems.append((torch.from_numpy(rowptr).to(dev), torch.from_numpy(colind).to(dev),
+                        torch.from_numpy(vals).to(dev), torch.from_numpy(b).to(dev)))
+    stream = torch.cuda.current_stream()
+    out = {"workload": "SPD 64x64 (n=4096), M=10, s=40, CG to rel-res 1e-10, %d systems" % steps}
+    for mode in ("sketch", "prev"):
+        seq = sa.Sequence(p.n, M, S, zeta=ZETA, seed=SEED, krylov="cg", guess=mode, max_iters=100000)
+        x = torch.zeros(p.n, dtype=torch.float64, device=dev)
+        its, ms = [], 0.0
+        for i, (rp, ci, v, b) in enumerate(systems):
+            A = sa.CSR(rp, ci, v)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            seq.guess(A, b, x)
+            info = seq.solve(A, b, 1e-10, x)
+            seq.push(x)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            assert info["status"] == 0
+            if i >= M:
+                its.append(info["iters"])
+                ms += e0.elapsed_time(e1)
+        seq.close()
+        out[mode] = {"iters_mean": float(np.mean(its)), "us_per_system": 1e3 * ms / len(its),
+                     "systems_per_s": 1e3 * len(its) / ms}
+    out["iteration_ratio_prev_over_sketch"] = out["prev"]["iters_mean"] / max(out["sketch"]["iters_mean"], 1e-9)
+    return out
+
+
 def guess_modes(args):
     """Guess modes compared on identical histories (the comparison of the
     paper's Section 4 experiment on the 1024 x 1024 sequence): the previous
@@ -1067,6 +1113,10 @@ def main():
         seq.close()
         batched = batched_form(args.batched_steps, 2, hbm_peak)
 
+    small = None
+    if not args.no_chosen:
+        small = spd_small()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(float(np.mean(iters)))
@@ -1085,6 +1135,7 @@ def main():
             "roofline": roof, "kernels": kernels, "clocks": clocks,
             "chosen": chosen,
             "preconditioned": preconditioned,
+            "spd_4096": small,
             "batched": batched,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "systems/s", "h2d_bytes_per_step": h2d,
