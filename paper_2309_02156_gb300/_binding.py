@@ -280,8 +280,7 @@ class Sequence:
         return V[:mi * kk].reshape(kk, mi).T.copy(), lam[:mi].copy(), dims[2]
 
     def last_sketch(self):
-        """(W, y) of the last guess as float64 CPU tensors, oldest history column first."""
-        m = None
+        """(W, y) of the last guess as float64 host arrays, oldest history column first."""
         import numpy as np
         W = np.zeros(self.s * (self.M + 1))
         y = np.zeros(self.M)
