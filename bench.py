@@ -661,7 +661,8 @@ def e1_sequence(args):
     rp = torch.from_numpy(rowptr).to(dev)
     ci = torch.from_numpy(colind).to(dev)
     n = N * N
-    out = {"e1": True, "grid": N, "steps": steps, "tol": tol, "runs": []}
+    out = {"e1": True, "grid": N, "steps": steps, "tol": tol, "precond_sweeps": args.e1_sweeps,
+           "runs": []}
     for dt, M, m in ((1e-5, 20, 10), (1e-3, 31, 20)):
         p = e1.E1Params(N=N, dt=dt)
         sysv = [e1.system(p, k, rowptr, colind) for k in range(steps)]
@@ -672,7 +673,7 @@ def e1_sequence(args):
         for mode in ("prev", "sketch", "pod", "rand"):
             kw = {"basis_m": m, "refresh": 50} if mode in ("pod", "rand") else {}
             seq = sa.Sequence(n, M, 80, zeta=ZETA, seed=SEED, guess=mode, krylov="gmres",
-                              restart=RESTART, max_iters=500000, **kw)
+                              restart=RESTART, max_iters=500000, precond_sweeps=args.e1_sweeps, **kw)
             x = torch.zeros(n, dtype=torch.float64, device=dev)
             its, zero, errs = [], 0, []
             torch.cuda.synchronize()
@@ -867,6 +868,7 @@ def main():
     ap.add_argument("--e1", action="store_true")
     ap.add_argument("--e1-grid", type=int, default=100)
     ap.add_argument("--e1-steps", type=int, default=200)
+    ap.add_argument("--e1-sweeps", type=int, default=0)
     ap.add_argument("--guess-modes", action="store_true")
     ap.add_argument("--modes-steps", type=int, default=8)
     ap.add_argument("--basis-m", type=int, default=10)
