@@ -49,3 +49,21 @@ def test_create_rejects_bad_config_without_gpu_work():
     for cfg in bad:
         assert lib.seq_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
         assert not h.value
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library the package raises."""
+    import paper_2309_02156_gb300._binding as b
+    monkeypatch.setattr(b, "_LIB", None)
+    monkeypatch.setattr(b._build, "LIB", str(tmp_path / "missing" / "libseqaccel.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        b.load(build_if_needed=False)
+
+
+def test_device_pointers_are_required():
+    """The binding passes device pointers only: a host tensor is rejected
+    before any call crosses the boundary."""
+    import torch
+    import paper_2309_02156_gb300._binding as b
+    with pytest.raises((ValueError, TypeError, RuntimeError)):
+        b._ptr(torch.zeros(4, dtype=torch.float64), torch.float64, 4)
