@@ -131,3 +131,33 @@ def test_batched_reports_bad_column_index():
     with pytest.raises(sa.SeqError):
         bt.step(vals, bs, xs, 1e-8)
     bt.close()
+
+
+def test_full_size_batch_sampled_residuals():
+    """The 512-sequence workload at full size (grid sides 48..384, M = 12,
+    s = 48), systems assembled on the device as in the bench: after the
+    history is primed, one step; every sequence reports convergence and the
+    oracle's FP64 product confirms the residual of a sample of sequences."""
+    import paper_2309_02156_gb300 as sa
+    from workloads.torch_pde import BatchedSystems
+    ps = workloads.batched_params(512, 0x5EEDBA5E)
+    gen = BatchedSystems(ps, torch.device(DEV))
+    pats = [(torch.from_numpy(rp).to(DEV), torch.from_numpy(ci).to(DEV)) for rp, ci in gen.patterns]
+    bt = sa.Batch(pats, M=12, s=48, zeta=8, seed=0x5EEDBA5E, max_iters=200000)
+    xs = [torch.empty(p.n, dtype=torch.float64, device=DEV) for p in ps]
+    for i in range(14):
+        v, b = gen.values(i), gen.rhs(i)
+        torch.cuda.synchronize()
+        infos = bt.step(gen.split(v, gen.nnz_off), gen.split(b, gen.n_off), xs, 1e-8)
+    assert all(f["status"] == 0 and f["final_relres"] <= 1e-8 * (1 + 1e-9) for f in infos)
+    assert all(f["history_cols"] == 12 for f in infos)
+    for k in range(0, 512, 73):
+        rowptr, colind = gen.patterns[k]
+        A = krylov.csr(rowptr, colind, gen.split(v, gen.nnz_off)[k].cpu().numpy(), ps[k].n)
+        bk = gen.split(b, gen.n_off)[k].cpu().numpy()
+        r = method.relres(A, bk, xs[k].cpu().numpy())
+        # both residuals are FP64 sums in different orders: they agree to the
+        # rounding of b - A x, about 1e-12 of ||b|| here
+        assert r <= 1e-8 * (1 + 1e-3)
+        assert abs(r - infos[k]["final_relres"]) <= 1e-11
+    bt.close()

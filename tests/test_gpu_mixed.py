@@ -110,3 +110,30 @@ def test_mixed_sequence_reaches_tolerance_every_step():
         assert method.relres(A, b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-9)
         seq.push(x)
     seq.close()
+
+
+def test_full_size_precision_form_first_systems():
+    """The 2048 x 2048 operator (n = 4,194,304) at the precision form's
+    settings (FP32 values, history and inner GMRES(30) with 8 Jacobi sweeps,
+    FP64 refinement to 1e-10): the first two systems converge, checked with the
+    oracle's FP64 product.  At this size the rounding of b - A x in FP64 alone is
+    about u ||A|| ||x|| ~ 2e-11 of ||b|| (diagonal 4/h^2 ~ 1.7e7), so the GPU's and
+    the oracle's residuals agree to 3e-11 and the oracle's may exceed 1e-10 by
+    that much."""
+    import paper_2309_02156_gb300 as sa
+    p = workloads.plain_nonsym(2048)
+    seq = sa.Sequence(p.n, 20, 80, precision="mixed", krylov="gmres", max_iters=400000,
+                      precond_sweeps=8)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    for i in range(2):
+        rowptr, colind, vals, b = workloads.csr_system(p, i)
+        Ad, bd = _dev(rowptr, colind, vals, b)
+        seq.guess(Ad, bd, x)
+        info = seq.solve(Ad, bd, 1e-10, x)
+        assert info["status"] == 0
+        r = method.relres(krylov.csr(rowptr, colind, vals, p.n), b, x.cpu().numpy())
+        assert info["final_relres"] <= 1e-10
+        assert r <= 1e-10 + 3e-11
+        assert abs(info["final_relres"] - r) <= 3e-11
+        seq.push(x)
+    seq.close()
