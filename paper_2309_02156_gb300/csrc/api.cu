@@ -90,6 +90,7 @@ struct seq_ctx {
     void* zb = nullptr;
     void* tprec = nullptr;
     cudaGraphExec_t cycle = nullptr;
+    cudaGraphExec_t cg_graph = nullptr;     // grid-wide CG iterations (large systems)
     cudaGraphExec_t cycle_prof = nullptr;   // same cycle with timing events between kernels
     std::vector<cudaEvent_t> ev;
     bool profiling = false;
@@ -357,6 +358,74 @@ int run_gmres(seq_ctx* ctx, bool f32) {
     return SEQ_OK;
 }
 
+// Grid-wide CG on the system bound to (args, ks) (FP32: the inner solve from
+// d = 0): the start kernel, then graph launches of kGridCgGraphIters
+// iterations; between launches the host answers a true-residual check
+// request (KState::jdone) with the check kernel.  Ends with the true
+// residual of the final iterate in ks->beta.
+int run_cg_grid(seq_ctx* ctx, bool f32) {
+    KState* ks = f32 ? ctx->ks_in : ctx->ks;
+    const DevArgs* args = f32 ? ctx->d_args_in : ctx->d_args;
+    if (f32)
+        launch_cgg_start_f32(args, ks, (float*)ctx->r, (float*)ctx->p, (float*)ctx->kpartial,
+                             ctx->nblk, ctx->stream);
+    else
+        launch_cgg_start_f64(args, ks, (double*)ctx->r, (double*)ctx->p, ctx->kpartial, ctx->nblk,
+                             ctx->stream);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    int rc = read_tail(ctx, ks);
+    if (rc) return rc;
+    if (!ctx->cg_graph) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+        if (f32)
+            launch_cgg_iterations_f32(args, ks, (float*)ctx->r, (float*)ctx->p, (float*)ctx->q,
+                                      (float*)ctx->kpartial, ctx->nblk, kGridCgGraphIters, ctx->cap);
+        else
+            launch_cgg_iterations_f64(args, ks, (double*)ctx->r, (double*)ctx->p, (double*)ctx->q,
+                                      ctx->kpartial, ctx->nblk, kGridCgGraphIters, ctx->cap);
+        CK(cudaStreamEndCapture(ctx->cap, &g));
+        cudaError_t e = cudaGraphInstantiate(&ctx->cg_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ctx->cg_graph = nullptr;
+            return fail(ctx, SEQ_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        }
+    }
+    // Every graph launch performs at least one iteration or ends the solve,
+    // and every check either ends it or is followed by a launch.
+    const long max_rounds = 2L * ((long)ctx->cfg.max_iters + 2);
+    long rounds = 0;
+    while (!ctx->h_ks->finished) {
+        if (++rounds > max_rounds) return fail(ctx, SEQ_ETIMEOUT, "CG round bound exceeded");
+        if (ctx->h_ks->jdone) {
+            if (f32)
+                launch_cgg_true_residual_f32(args, ks, (float*)ctx->r, (float*)ctx->p,
+                                             (float*)ctx->kpartial, ctx->nblk, 1, ctx->stream);
+            else
+                launch_cgg_true_residual_f64(args, ks, (double*)ctx->r, (double*)ctx->p,
+                                             ctx->kpartial, ctx->nblk, 1, ctx->stream);
+            ctx->launches += 1;
+        } else {
+            CK(cudaGraphLaunch(ctx->cg_graph, ctx->stream));
+            ctx->launches += 3 * kGridCgGraphIters;
+        }
+        CK(cudaGetLastError());
+        rc = read_tail(ctx, ks);
+        if (rc) return rc;
+    }
+    if (f32)
+        launch_cgg_true_residual_f32(args, ks, (float*)ctx->r, nullptr, (float*)ctx->kpartial,
+                                     ctx->nblk, 0, ctx->stream);
+    else
+        launch_cgg_true_residual_f64(args, ks, (double*)ctx->r, nullptr, ctx->kpartial, ctx->nblk,
+                                     0, ctx->stream);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    return read_tail(ctx, ks);
+}
+
 void fill_info(seq_info* info, const KState* t) {
     if (!info) return;
     info->guess_relres = t->first_relres;
@@ -425,7 +494,7 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
         ok = ok && cudaMalloc(&ctx->rhs32, sizeof(float) * (size_t)n) == cudaSuccess;
         ok = ok && cudaMalloc(&ctx->d, sizeof(float) * (size_t)n) == cudaSuccess;
     }
-    if (c.krylov == SEQ_GMRES) {
+    if (c.krylov == SEQ_GMRES) {                            // SELL-32 copy for the cycles
         const int ns = (n + 31) / 32;
         ok = ok && cudaMalloc(&ctx->sell_width, sizeof(int) * (size_t)ns) == cudaSuccess;
         ok = ok && cudaMalloc(&ctx->sell_off, sizeof(int) * (size_t)(ns + 1)) == cudaSuccess;
@@ -490,6 +559,7 @@ int seq_destroy(seq_ctx* ctx) {
     if (!ctx) return SEQ_OK;
     if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
     if (ctx->cycle) cudaGraphExecDestroy(ctx->cycle);
+    if (ctx->cg_graph) cudaGraphExecDestroy(ctx->cg_graph);
     if (ctx->cycle_prof) cudaGraphExecDestroy(ctx->cycle_prof);
     for (auto e : ctx->ev) cudaEventDestroy(e);
     void* dev_ptrs[] = {ctx->X, ctx->sk, ctx->sk_partial, ctx->W, ctx->lsq, ctx->kpartial,
@@ -748,6 +818,7 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
     CK(cudaMemsetAsync(ctx->ks_in, 0, sizeof(KState), ctx->stream));
     rc = ensure_val32(ctx, A);
     if (rc) return rc;
+    const bool grid_cg = c.krylov == SEQ_CG && c.n >= kGridCgMinRows;
     if (c.krylov == SEQ_GMRES) {
         rc = build_sell(ctx, A);
         if (rc) return rc;
@@ -766,6 +837,9 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
     if (!ctx->mixed) {
         if (c.krylov == SEQ_GMRES) {
             rc = run_gmres(ctx, false);
+            if (rc) return rc;
+        } else if (grid_cg) {
+            rc = run_cg_grid(ctx, false);
             if (rc) return rc;
         } else {
             launch_cg_block_f64(ctx->d_args, ctx->ks, (double*)ctx->r, (double*)ctx->p,
@@ -814,6 +888,9 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
                                ctx->stream));
             if (c.krylov == SEQ_GMRES) {
                 rc = run_gmres(ctx, true);
+                if (rc) return rc;
+            } else if (grid_cg) {
+                rc = run_cg_grid(ctx, true);
                 if (rc) return rc;
             } else {
                 launch_cg_block_f32(ctx->d_args_in, ctx->ks_in, (float*)ctx->r, (float*)ctx->p,

@@ -103,6 +103,23 @@ void launch_cg_block_f64(const DevArgs* a, KState* ks, double* r, double* p, dou
 void launch_cg_block_f32(const DevArgs* a, KState* ks, float* r, float* p, float* q,
                          cudaStream_t st);
 void launch_round_f32(const double* src, float* dst, int n, cudaStream_t st);
+// Grid-wide CG for large systems (all SMs; three kernels per iteration): the
+// start (FP32: from x = 0), `iters` iterations (the body of a CUDA graph), and
+// the true residual (check != 0: convergence check and restart).
+constexpr int kGridCgMinRows = 65536;
+constexpr int kGridCgGraphIters = 16;
+void launch_cgg_start_f64(const DevArgs* a, KState* ks, double* r, double* p, double* partial,
+                          int nblk, cudaStream_t st);
+void launch_cgg_start_f32(const DevArgs* a, KState* ks, float* r, float* p, float* partial,
+                          int nblk, cudaStream_t st);
+void launch_cgg_iterations_f64(const DevArgs* a, KState* ks, double* r, double* p, double* q,
+                               double* partial, int nblk, int iters, cudaStream_t st);
+void launch_cgg_iterations_f32(const DevArgs* a, KState* ks, float* r, float* p, float* q,
+                               float* partial, int nblk, int iters, cudaStream_t st);
+void launch_cgg_true_residual_f64(const DevArgs* a, KState* ks, double* r, double* p,
+                                  double* partial, int nblk, int check, cudaStream_t st);
+void launch_cgg_true_residual_f32(const DevArgs* a, KState* ks, float* r, float* p,
+                                  float* partial, int nblk, int check, cudaStream_t st);
 // CSR -> SELL-32 (slice widths and offsets, then the padded arrays).
 void launch_sell_layout(const int* rowptr, int n, int nnz, int* width, int* off, cudaStream_t st);
 void launch_sell_fill_f64(const int* rowptr, const int* colind, const double* val, int n, int nnz,

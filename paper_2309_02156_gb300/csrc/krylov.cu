@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include "krylov_kernels.cuh"
+#include "cg_kernels.cuh"
 
 namespace sa {
 
@@ -386,6 +387,31 @@ void launch_cg_block_f64(const DevArgs* a, KState* ks, double* r, double* p, dou
 void launch_cg_block_f32(const DevArgs* a, KState* ks, float* r, float* p, float* q,
                          cudaStream_t st) {
     cg_block_kernel<SysF32><<<1, 1024, 0, st>>>(a, ks, r, p, q);
+}
+
+void launch_cgg_start_f64(const DevArgs* a, KState* ks, double* r, double* p, double* partial,
+                          int nblk, cudaStream_t st) {
+    cgg_start_kernel<SysF64><<<nblk, kStreamBlock, 0, st>>>(a, ks, r, p, partial, 0);
+}
+void launch_cgg_start_f32(const DevArgs* a, KState* ks, float* r, float* p, float* partial,
+                          int nblk, cudaStream_t st) {
+    cgg_start_kernel<SysF32><<<nblk, kStreamBlock, 0, st>>>(a, ks, r, p, partial, 1);
+}
+void launch_cgg_iterations_f64(const DevArgs* a, KState* ks, double* r, double* p, double* q,
+                               double* partial, int nblk, int iters, cudaStream_t st) {
+    launch_cg_iterations<SysF64>(a, ks, r, p, q, partial, nblk, iters, st);
+}
+void launch_cgg_iterations_f32(const DevArgs* a, KState* ks, float* r, float* p, float* q,
+                               float* partial, int nblk, int iters, cudaStream_t st) {
+    launch_cg_iterations<SysF32>(a, ks, r, p, q, partial, nblk, iters, st);
+}
+void launch_cgg_true_residual_f64(const DevArgs* a, KState* ks, double* r, double* p,
+                                  double* partial, int nblk, int check, cudaStream_t st) {
+    cgg_true_residual_kernel<SysF64><<<nblk, kStreamBlock, 0, st>>>(a, ks, r, p, partial, check);
+}
+void launch_cgg_true_residual_f32(const DevArgs* a, KState* ks, float* r, float* p,
+                                  float* partial, int nblk, int check, cudaStream_t st) {
+    cgg_true_residual_kernel<SysF32><<<nblk, kStreamBlock, 0, st>>>(a, ks, r, p, partial, check);
 }
 
 }  // namespace sa

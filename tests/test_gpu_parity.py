@@ -329,3 +329,51 @@ def test_zero_and_nonfinite_right_hand_sides(krylov_kind, precision):
         seq.solve(Ad, bn, 1e-10, x)
     assert e.value.code == -5
     seq.close()
+
+
+@pytest.mark.parametrize("N,guess_scale", [(260, 0.0), (300, 1.0)])
+def test_grid_cg_matches_oracle(N, guess_scale):
+    """CG on systems with n >= 65,536 runs on the whole GPU (three kernels per
+    iteration in a CUDA graph); same iteration as the oracle's CG within
+    max(2, 2%), true residual within the tolerance."""
+    p = workloads.plain_spd(N)
+    rowptr, colind, vals, b = workloads.csr_system(p, 3)
+    A = krylov.csr(rowptr, colind, vals, p.n)
+    rng = np.random.default_rng(N)
+    x0 = guess_scale * 1e-3 * rng.standard_normal(p.n)
+    x_ref, it_ref, _, st_ref = krylov.cg(A, b, x0, 1e-10, 100000)
+    Ad, bd = _dev_system(rowptr, colind, vals, b)
+    seq = _sa().Sequence(p.n, 4, 16, krylov="cg", max_iters=100000)
+    x = _tensor(x0)
+    info = seq.solve(Ad, bd, 1e-10, x)
+    assert info["status"] == 0 and st_ref == 0
+    assert abs(info["iters"] - it_ref) <= max(2, 0.02 * it_ref)
+    xh = x.cpu().numpy()
+    assert method.relres(A, b, xh) <= 1e-10 * (1 + 1e-9)
+    assert info["final_relres"] == pytest.approx(method.relres(A, b, xh), rel=1e-6)
+    assert info["guess_relres"] == pytest.approx(method.relres(A, b, x0), rel=1e-9)
+    assert np.linalg.norm(xh - x_ref) <= 1e-6 * np.linalg.norm(x_ref)
+    seq.close()
+
+
+def test_grid_cg_mixed_and_cap():
+    """The FP32 inner CG of the mixed form on the whole GPU reaches the FP64
+    tolerance; an unreachable tolerance stops at the iteration cap."""
+    p = workloads.plain_spd(280)
+    rowptr, colind, vals, b = workloads.csr_system(p, 1)
+    A = krylov.csr(rowptr, colind, vals, p.n)
+    Ad, bd = _dev_system(rowptr, colind, vals, b)
+    seq = _sa().Sequence(p.n, 4, 16, krylov="cg", precision="mixed_krylov", max_iters=200000)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    info = seq.solve(Ad, bd, 1e-10, x)
+    assert info["status"] == 0 and info["refinements"] >= 1
+    assert method.relres(A, b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-9)
+    _, it_ref, nref, _, st = krylov.mixed_refine(A, A.astype(np.float32), b, np.zeros(p.n), 1e-10,
+                                                 "cg", 30, 200000)
+    assert st == 0 and abs(info["iters"] - it_ref) <= 0.5 * it_ref + 10
+    seq.close()
+    seq2 = _sa().Sequence(p.n, 4, 16, krylov="cg", max_iters=37)
+    x.zero_()
+    info = seq2.solve(Ad, bd, 1e-30, x, allow=(1,))
+    assert info["rc"] == 1 and info["iters"] == 37
+    seq2.close()
