@@ -481,7 +481,7 @@ def learned_ablation(args):
             if g2["net_resid"] > 0 and g1["sketch_resid"] > 0:
                 rec["ratio"].append(g2["net_resid"] / g1["sketch_resid"])
             # Floor of any FP32-output predictor: the least-squares y itself
-            # rounded to FP32, judged in FP64 on the same sketched block.
+            # rounded to FP32, tested in FP64 on the same sketched block.
             Wf, yf = c_ls.last_sketch()
             Wf = Wf.reshape(S_ROWS, M_HIST + 1)
             r64 = np.linalg.norm(Wf[:, :M_HIST] @ yf - Wf[:, M_HIST])

@@ -624,7 +624,7 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
     int mode = c.guess;
     const bool learned = mode == SEQ_GUESS_LEARNED;
     if (learned) mode = SEQ_GUESS_SKETCH;
-    bool predicted = false;          // the network's y was computed (and judged)
+    bool predicted = false;          // the network's y was computed (and tested)
     ctx->sample_ready = false;
     ctx->sell_ok = false;            // the SELL copy belongs to the last seq_solve's matrix
     if (m == 0 && mode != SEQ_GUESS_ZERO) mode = SEQ_GUESS_ZERO;
