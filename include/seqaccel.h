@@ -8,7 +8,7 @@
  *                        by one column per system;
  *   Algorithm 1          guess = argmin over span(X) of ||A(t_i) s - b(t_i)||_2,
  *                        then the Krylov solver starts from it.
- * Here the reduced least-squares problem of Algorithm 1, step 3 is sketched
+ * Here the reduced least-squares problem of Algorithm 1 is sketched
  * with a sparse-sign matrix S (s x n, zeta nonzeros of +-1/sqrt(zeta) per
  * column, generated from SplitMix64 counters):
  *   W = S [A X | b],  y = argmin ||W[:, :m] y - W[:, m]||_2 (pivoted Householder
@@ -161,7 +161,7 @@ int seq_history_size(const seq_ctx* ctx);
 int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev,
               double* x0_dev, seq_info* info);
 
-/* Krylov solve from x_dev (Algorithm 1, step 4): on entry x_dev holds the
+/* Krylov solve from x_dev (the solve of Algorithm 1): on entry x_dev holds the
  * starting vector, on exit the iterate with ||b - A x|| <= tol ||b|| (status
  * SEQ_OK) or the last iterate (SEQ_NOT_CONVERGED after max_iters iterations).
  * CG or GMRES(restart) with CGS2 per the config, optionally right-

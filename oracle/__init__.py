@@ -13,7 +13,7 @@ Modules
 sketch   sparse-sign row sketch S (s x n, zeta nonzeros of +-1/sqrt(zeta) per
          column) generated from SplitMix64 counters, and W = S [A X | b].
 lsq      column-scaled, column-pivoted Householder least squares with rank
-         truncation (the reduced problem of Algorithm 1, step 3).
+         truncation (the reduced problem of Algorithm 1).
 krylov   CSR products, CG (Hestenes-Stiefel), restarted GMRES with CGS2
          Arnoldi, and mixed-precision iterative refinement.
 method   Algorithm 1 of the paper with the subspace S = span(X) and the

@@ -1,4 +1,4 @@
-"""Krylov solvers started from the subspace guess (Algorithm 1, step 4).
+"""Krylov solvers started from the subspace guess (the solve of Algorithm 1).
 
 The paper runs GMRES (Saad and Schultz) for general matrices and names CG
 (Hestenes and Stiefel) for symmetric positive definite ones (Section 1); both

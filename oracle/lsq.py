@@ -1,4 +1,4 @@
-"""Small dense least squares min_y || W1 y - wb ||_2 (Algorithm 1, step 3).
+"""Small dense least squares min_y || W1 y - wb ||_2 (Algorithm 1).
 
 The paper solves the reduced problem with a QR factorisation (Section 2, the
 cost paragraph after Algorithm 1, citing Golub and Van Loan).  The

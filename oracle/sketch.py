@@ -2,7 +2,7 @@
 
 The paper compresses the history with a Gaussian *column* sketch (Section 2.2,
 Algorithm 4).  The hot path built here instead sketches the *rows* of the
-reduced least-squares problem of Algorithm 1, step 3: it solves
+reduced least-squares problem of Algorithm 1: it solves
 min_y || S (A X y - b) ||_2 with a sparse-sign S ("sketch-and-solve").  The
 paper does not define S, so this module fixes it (a reading, stated once here
 and implemented independently on the GPU side):

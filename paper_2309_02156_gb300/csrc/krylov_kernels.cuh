@@ -1,6 +1,6 @@
 // Krylov kernel templates shared by the FP64 and FP32 translation units.
 //
-// Krylov solvers started from the subspace guess (Algorithm 1, step 4; the
+// Krylov solvers started from the subspace guess (the solve of Algorithm 1; the
 // paper uses GMRES for general matrices and names CG for SPD ones, Section 1).
 //
 // Restarted GMRES(R) with CGS2 Arnoldi.  One Arnoldi step j is four

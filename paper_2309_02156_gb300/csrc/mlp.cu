@@ -1,7 +1,7 @@
 // Learned coefficient predictor: a small MLP that predicts the history
 // coefficients y of the guess from the coefficient vectors of the previous
 // four systems and the sketched residual of the linearly extrapolated guess
-// (the paper computes y by least squares every step, Algorithm 1 step 3; this
+// (the paper computes y by least squares every step, Algorithm 1; this
 // is the learned variant, with the sketched least squares as fallback).
 //
 // Network: 4M+s -> H -> H -> M, GELU (erf form), weights stored FP32 (master)
