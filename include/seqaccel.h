@@ -13,8 +13,8 @@
  * column, generated from SplitMix64 counters):
  *   W = S [A X | b],  y = argmin ||W[:, :m] y - W[:, m]||_2 (pivoted Householder
  *   QR, rank truncation), x0 = X y;
- * then CG (SPD) or restarted GMRES with CGS2 Arnoldi (Section 1, Algorithm 1
- * step 4) runs from x0 to ||b - A x|| <= tol ||b||.
+ * then CG (SPD) or restarted GMRES with CGS2 Arnoldi (Section 1, the solve of
+ * Algorithm 1) runs from x0 to ||b - A x|| <= tol ||b||.
  *
  * Conventions for every entry point
  *   - Pointers named *_dev are DEVICE pointers owned by the caller and only
@@ -148,7 +148,7 @@ int seq_push_solution(seq_ctx* ctx, const double* x_dev);
 /* Number of history columns currently held (0..M). */
 int seq_history_size(const seq_ctx* ctx);
 
-/* Initial guess for A x = b (Algorithm 1, steps 1-3, with the sketched reduced
+/* Initial guess for A x = b (the guess of Algorithm 1, with the sketched reduced
  * problem; or the guess mode chosen in the config).  Writes x0_dev (device, n
  * FP64).  With an empty history x0 = 0; with m < M columns the m available
  * ones are used.  Fills info (guess_relres, sketch_resid, rank, history_cols;
@@ -209,8 +209,8 @@ int seq_pod_state(seq_ctx* ctx, double* V_host, double* lam_host, int32_t* dims)
 int seq_sketch_columns(int32_t n, int32_t s, int32_t zeta, uint64_t seed,
                        int32_t* rows_dev, int8_t* signs_dev, void* cuda_stream);
 
-/* Kernel kinds reported by seq_kernel_stats (the GMRES cycle of Algorithm 1,
- * step 4, and the stages of the guess). */
+/* Kernel kinds reported by seq_kernel_stats (the GMRES cycle of the solve of
+ * Algorithm 1, and the stages of the guess). */
 typedef enum {
     SEQ_K_SPMV = 0,       /* w = A v_j (FP32 inner solves: fused with the first CGS pass) */
     SEQ_K_CGS_DOT = 1,    /* first classical Gram-Schmidt pass h1 = V^T w               */
@@ -299,8 +299,8 @@ int seq_last_sample(seq_ctx* ctx, float* sample_dev);
  *
  * Each sequence k has its own history (M columns, FP64), sketch (seed + k)
  * and fixed sparsity pattern; every step, for every sequence: the sketched
- * guess (Algorithm 1, steps 1-3), then FP64 iterative refinement around FP32
- * CG (the sequences are SPD) to ||b - A x|| <= tol ||b|| (step 4), then the
+ * guess (Algorithm 1), then FP64 iterative refinement around FP32 CG (the
+ * sequences are SPD) to ||b - A x|| <= tol ||b|| (the solve), then the
  * push.  One thread block processes one sequence at a time, taking sequences
  * from a device queue; the step is a single kernel launch captured in a CUDA
  * graph.  Limits: M <= 16, s <= 64, zeta <= min(s, 16). */

@@ -17,15 +17,15 @@ optimality (the identity following Algorithm 2): ||(I - Q Q^T) X||_F^2 equals
 the sum of the squared trailing singular values, the minimum over all
 orthonormal n x m bases.
 
-Randomised range finder (Algorithm 4): Omega = X Z with Z (M x m) Gaussian
-(steps 2-4) computed from scratch, then from one time step to the next
-updated in place (steps 6-9): the contribution of the column that leaves the
+Randomised range finder (Algorithm 4): Omega = X Z with Z (M x m) Gaussian,
+computed from scratch, then from one time step to the next updated in place
+(the algorithm's progressive update): the contribution of the column that leaves the
 history is removed with the first row of Z, the rows of Z move up by one, a
 new Gaussian row is drawn for the newest solution and its contribution is
 added.  The update is exact in exact arithmetic (Omega = X Z for the current Z
 at all times); to bound the drift from cancellation, Omega is recomputed from
 scratch with a newly drawn Z every `refresh` updates (the experiments of
-Section 4 use 50).  Step 11's reduced QR of Omega gives Q.
+Section 4 use 50).  The reduced QR of Omega gives Q.
 
 Readings (the paper assumes a full history):
   * while the history holds M_i < M columns, Z has M_i rows and a new
@@ -35,7 +35,7 @@ Readings (the paper assumes a full history):
   * the from-scratch recomputation happens at the guess that finds `refresh`
     or more progressive updates since the last one.
 
-Gaussian draws (steps 3 and 8).  Draw k = 0, 1, 2, ... of a context is the
+Gaussian draws (for Z from scratch and for each new row).  Draw k = 0, 1, 2, ... of a context is the
 Box-Muller transform (Box and Muller, 1958) of two outputs of SplitMix64
 (Steele, Lea and Flood, 2014) seeded with seed XOR 0x52414E44:
     h1 = output 2k+1,  h2 = output 2k+2,
@@ -110,7 +110,7 @@ class RandRangeFinder:
         return g
 
     def from_scratch(self, X: np.ndarray) -> None:
-        """Steps 2-4: Z drawn anew (one row per history column), Omega = X Z."""
+        """From scratch: Z drawn anew (one row per history column), Omega = X Z."""
         Mi = X.shape[1]
         Z = self._draw(Mi * self.m).reshape(Mi, self.m)
         self.Z = [Z[l].copy() for l in range(Mi)]
@@ -118,16 +118,17 @@ class RandRangeFinder:
         self.updates = 0
 
     def on_push(self, x_new: np.ndarray, x_leaving) -> None:
-        """Steps 6-9, for one new solution x_new; x_leaving is the column that
-        leaves the history (None while the history is still filling)."""
+        """The progressive update for one new solution x_new; x_leaving is the
+        column that leaves the history (None while the history is still
+        filling)."""
         if self.omega is None:
             return
         if x_leaving is not None:
-            self.omega = self.omega - np.outer(x_leaving, self.Z[0])     # step 6
-            self.Z = self.Z[1:]                                          # step 7
-        z_new = self._draw(self.m)                                       # step 8
+            self.omega = self.omega - np.outer(x_leaving, self.Z[0])     # leaving column out
+            self.Z = self.Z[1:]                                          # rows of Z move up
+        z_new = self._draw(self.m)                                       # new Gaussian row
         self.Z.append(z_new)
-        self.omega = self.omega + np.outer(x_new, z_new)                 # step 9
+        self.omega = self.omega + np.outer(x_new, z_new)                 # new column in
         self.updates += 1
 
     def basis(self, X: np.ndarray) -> np.ndarray:
@@ -141,7 +142,7 @@ class RandRangeFinder:
 
 
 def orthonormal_basis(omega: np.ndarray) -> np.ndarray:
-    """Step 11: reduced QR of Omega, Q factor."""
+    """Reduced QR of Omega (Algorithm 4), Q factor."""
     Q, _ = np.linalg.qr(omega)
     return Q
 

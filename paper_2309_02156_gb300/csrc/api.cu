@@ -1,6 +1,6 @@
 // C-ABI of libseqaccel (declared in include/seqaccel.h): context management
-// and the host orchestration of the guess (Algorithm 1, steps 1-3) and the
-// Krylov solve (step 4).  Device memory is allocated once per context; every
+// and the host orchestration of the guess of Algorithm 1 and the Krylov
+// solve that follows it.  Device memory is allocated once per context; every
 // call is ordered on the context's stream and synchronises only where a
 // seq_info is returned (once per GMRES restart cycle inside seq_solve).
 #include <math.h>
@@ -584,7 +584,7 @@ int seq_push_solution(seq_ctx* ctx, const double* x_dev) {
     if (!ctx || !x_dev) return fail(ctx, SEQ_EINVAL, "NULL argument");
     const int slot = ctx->pushes % ctx->cfg.M;
     if (ctx->cfg.guess == SEQ_GUESS_RAND && ctx->om_valid) {
-        // Algorithm 4, steps 6-9, fused with the push.
+        // The progressive update of Algorithm 4, fused with the push.
         const int mb = ctx->cfg.basis_m;
         launch_rand_push(x_dev, ctx->cfg.n, (double*)ctx->X, ctx->ldx, slot,
                          ctx->pushes >= ctx->cfg.M, ctx->Zs, mb, ctx->gseed, ctx->gdraws, ctx->Om,

@@ -13,9 +13,10 @@
 // pivoted-QR least squares, and x0 = X (V_k c).
 //
 // Randomised range finder.  Omega = X Z (n x m, row-major, FP64) is formed
-// from scratch with a Gaussian Z (steps 2-4) and, at every push of a new
+// from scratch with a Gaussian Z and, at every push of a new
 // solution, updated in the same pass that writes the solution into the ring:
-// Omega[r,:] = (Omega[r,:] - x_leaving[r] z_1) + x_new[r] z_new (steps 6-9).
+// Omega[r,:] = (Omega[r,:] - x_leaving[r] z_1) + x_new[r] z_new (the
+// progressive update of Algorithm 4).
 // Z is kept per ring slot, so "moving the rows of Z up" is the ring's index
 // arithmetic.  The guess sketches A Omega (m columns instead of M) and
 // solves the reduced least squares; x0 = Omega c.
@@ -82,7 +83,7 @@ __global__ void rand_scratch_kernel(const double* __restrict__ X, int ldx, int n
     }
 }
 
-// Steps 6-9 fused with the push: Omega[r,:] = (Omega[r,:] - x_old[r] z_old)
+// The progressive update fused with the push: Omega[r,:] = (Omega[r,:] - x_old[r] z_old)
 // + x_new[r] z_new and X[r, slot] = x_new[r] (x_old = the slot's previous
 // content when `remove`, else nothing is removed).
 __global__ void rand_push_kernel(const double* __restrict__ x, int n, double* __restrict__ X, int ldx,

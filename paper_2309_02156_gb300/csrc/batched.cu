@@ -5,11 +5,11 @@
 // by default, the order the autotuner picked otherwise) and runs the whole
 // step of one sequence with block barriers only -- there is no grid-wide
 // wait anywhere, so blocks never spin on one another:
-//   1. guess (Algorithm 1, steps 1-3): W = S [A X | b] accumulated in shared
+//   1. guess (Algorithm 1): W = S [A X | b] accumulated in shared
 //      memory (the sparse-sign S generated on the fly from its counters),
 //      the column-scaled pivoted Householder least squares in shared memory,
 //      x0 = X y with FP64 accumulation;
-//   2. FP64 iterative refinement around FP32 CG (step 4): r = b - A x in FP64,
+//   2. FP64 iterative refinement around FP32 CG (the solve): r = b - A x in FP64,
 //      inner CG on A32 d = r to a relative tolerance
 //      max(inner_tol, theta tol ||b|| / ||r||), x += d, until ||r|| <= tol ||b||;
 //   3. push x into the sequence's history ring (FP64).

@@ -1,4 +1,4 @@
-// Reduced least squares and guess expansion (Algorithm 1, steps 2-3).
+// Reduced least squares and guess expansion (Algorithm 1).
 //
 // y = argmin ||W1 y - wb||_2 for the s x m sketched block, solved by one
 // thread block in FP64 with column scaling, Householder QR with

@@ -4,8 +4,8 @@
 // candidate rows from SplitMix64 outputs 256 j + c + 1 (c = 0, 1, ...):
 // row = ((h >> 32) * s) >> 32, sign = bit 0 of h, repeated rows skipped; if
 // 256 candidates fall short, the smallest unused rows are taken with sign +1.
-// The sketch replaces the n-row reduced least-squares problem of Algorithm 1,
-// step 3 (min ||A(t_i) X y - b(t_i)||) by its s-row image; the paper itself
+// The sketch replaces the n-row reduced least-squares problem of Algorithm 1
+// (min ||A(t_i) X y - b(t_i)||) by its s-row image; the paper itself
 // sketches columns instead (Section 2.2), so this construction is this
 // library's own.
 //

@@ -43,7 +43,7 @@ def _columns(n, count, seed):
 
 @pytest.mark.parametrize("M,m,refresh", [(8, 5, 1000), (6, 9, 1000), (10, 4, 7)])
 def test_progressive_update_equals_from_scratch(M, m, refresh):
-    """Steps 6-9 keep Omega = X Z for the current X and Z (exact in exact
+    """The progressive updates keep Omega = X Z for the current X and Z (exact in exact
     arithmetic), through the start-up, the full ring and refreshes."""
     cols = _columns(200, 40, 1)
     rrf = basis.RandRangeFinder(m, refresh, seed=11)
