@@ -494,7 +494,7 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
         ok = ok && cudaMalloc(&ctx->rhs32, sizeof(float) * (size_t)n) == cudaSuccess;
         ok = ok && cudaMalloc(&ctx->d, sizeof(float) * (size_t)n) == cudaSuccess;
     }
-    if (c.krylov == SEQ_GMRES) {                            // SELL-32 copy for the cycles
+    if (c.krylov == SEQ_GMRES || n >= kGridCgMinRows) {     // SELL-32 copy for the cycles
         const int ns = (n + 31) / 32;
         ok = ok && cudaMalloc(&ctx->sell_width, sizeof(int) * (size_t)ns) == cudaSuccess;
         ok = ok && cudaMalloc(&ctx->sell_off, sizeof(int) * (size_t)(ns + 1)) == cudaSuccess;
@@ -819,7 +819,7 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
     rc = ensure_val32(ctx, A);
     if (rc) return rc;
     const bool grid_cg = c.krylov == SEQ_CG && c.n >= kGridCgMinRows;
-    if (c.krylov == SEQ_GMRES) {
+    if (c.krylov == SEQ_GMRES || grid_cg) {
         rc = build_sell(ctx, A);
         if (rc) return rc;
     }

@@ -42,14 +42,19 @@ struct CgResidual {                  // r[i] = b[i] - (A x)[i] (and p = r), acc 
     }
 };
 
-// Product over the block's rows [lo, hi): CSR rows, one per thread, entries
-// in CSR order.
+// Product over the block's rows [lo, hi): the SELL-32 copy when present,
+// CSR rows (one per thread) otherwise.  Each row reaches the epilogue once.
 template <class Sys, typename Epi>
 __device__ __forceinline__ void cg_product(const DevArgs* __restrict__ a, KState* ks,
                                            const typename Sys::T* x, int lo, int hi,
                                            const Epi& epi) {
     using T = typename Sys::T;
     const int n = a->n;
+    if (a->sell_off) {
+        sell_rows<T>(a->sell_off, a->sell_col, reinterpret_cast<const T*>(a->sell_val), x, n, lo,
+                     hi, kWarps, &ks->bad_index, epi);
+        return;
+    }
     const T* val = Sys::val(a);
     int flag = 0;
     for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) {

@@ -228,6 +228,10 @@ __device__ __forceinline__ void sell_rows(const int* __restrict__ off,
                                           const T* __restrict__ val,
                                           const T* __restrict__ x, int n, int lo, int hi,
                                           int nwarps, int* bad, const Epi& epi) {
+    // An empty range (a trailing block when the grid covers more than n rows)
+    // has no slice: lo = hi = n would otherwise map to the last partial slice
+    // and repeat rows that another block owns.
+    if (lo >= hi) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s_lo = lo >> 5, s_hi = (hi + 31) >> 5;
     int flag = 0;
