@@ -572,6 +572,13 @@ def spd_small(steps=60):
         out[mode] = {"iters_mean": float(np.mean(its)), "us_per_system": 1e3 * ms / len(its),
                      "systems_per_s": 1e3 * len(its) / ms}
     out["iteration_ratio_prev_over_sketch"] = out["prev"]["iters_mean"] / max(out["sketch"]["iters_mean"], 1e-9)
+    rec = os.path.join(ROOT, "tests", "golden", "oracle_iterations_spd64.json")
+    if os.path.exists(rec):
+        d = json.load(open(rec))
+        out["oracle"] = {"sketch_iters_mean": d["sketch"]["iters_mean_full_history"],
+                         "prev_iters_mean": d["prev"]["iters_mean_full_history"],
+                         "source": "recorded by oracle/measure_iterations.py --workload spd "
+                                   "(same sequence, systems M..59)"}
     return out
 
 

@@ -1,14 +1,22 @@
-"""Record the oracle's own Krylov iteration counts on a full-size sequence.
+"""Record the oracle's own Krylov iteration counts on a sequence.
 
-Runs Algorithm 1 with the sketched reduced problem followed by GMRES(30) to a
-relative residual of 1e-8 on the 1024 x 1024 advection-diffusion sequence
-(M = 20, s = 80, zeta = 8, seed 0x5EEDBA5E), entirely in the oracle, and
-writes the per-system iteration counts and timings as JSON.  The CPU
-baseline of the benchmark uses the mean count of the systems with a full
-history to turn a timed sample (one guess plus a bounded number of GMRES
-iterations) into systems per second.
+Test infrastructure: runs entirely in the oracle and writes JSON.
+
+--workload nonsym (default): Algorithm 1 with the sketched reduced problem
+followed by GMRES(30) to a relative residual of 1e-8 on the 1024 x 1024
+advection-diffusion sequence (M = 20, s = 80, zeta = 8, seed 0x5EEDBA5E);
+per-system iteration counts and timings.  The CPU baseline of the benchmark
+uses the mean count of the systems with a full history to turn a timed
+sample (one guess plus a bounded number of GMRES iterations) into systems
+per second.
+
+--workload spd: the 64 x 64 SPD sequence (n = 4096, M = 10, s = 40, CG to
+1e-10, 60 systems), once with the sketched guess and once with the previous
+solution (the paper's baseline), each in its own sequence; the benchmark
+quotes the means over the systems with a full history beside its own.
 
     python -m oracle.measure_iterations --steps 26 --out tests/golden/oracle_iterations_nonsym1024.json
+    python -m oracle.measure_iterations --workload spd --out tests/golden/oracle_iterations_spd64.json
 """
 from __future__ import annotations
 
@@ -29,14 +37,42 @@ import workloads  # noqa: E402
 from oracle import krylov, method, sketch  # noqa: E402
 
 
+def spd(out_path: str, N: int = 64, M: int = 10, s: int = 40, steps: int = 60,
+        tol: float = 1e-10) -> None:
+    p = workloads.plain_spd(N)
+    S = sketch.sparse_sign_matrix(p.n, s, 8, 0x5EEDBA5E)
+    doc = {"workload": f"SPD {N}x{N} (n={p.n}), M={M}, s={s}, zeta=8, seed 0x5EEDBA5E, "
+                       f"CG to {tol:g}, {steps} systems",
+           "host": platform.machine()}
+    for mode in ("sketch", "prev"):
+        hist = method.History(p.n, M)
+        rows = []
+        for i in range(steps):
+            rowptr, colind, vals, b = workloads.csr_system(p, i)
+            A = krylov.csr(rowptr, colind, vals, p.n)
+            out = method.solve_step(A, b, hist, S, tol, "cg", guess=mode, max_iters=100000)
+            assert out["status"] == krylov.CONVERGED
+            rows.append({"i": i, "iters": int(out["iters"]), "guess_relres": out["guess_relres"],
+                         "relres": out["relres"]})
+        full = [r["iters"] for r in rows if r["i"] >= M]
+        doc[mode] = {"systems": rows, "iters_mean_full_history": float(np.mean(full))}
+        print(mode, doc[mode]["iters_mean_full_history"], flush=True)
+    with open(out_path, "w") as f:
+        json.dump(doc, f, indent=1)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", choices=("nonsym", "spd"), default="nonsym")
     ap.add_argument("--N", type=int, default=1024)
     ap.add_argument("--M", type=int, default=20)
     ap.add_argument("--s", type=int, default=80)
     ap.add_argument("--steps", type=int, default=26)
     ap.add_argument("--out", required=True)
     a = ap.parse_args()
+    if a.workload == "spd":
+        spd(a.out)
+        return
     p = workloads.plain_nonsym(a.N)
     S = sketch.sparse_sign_matrix(p.n, a.s, 8, 0x5EEDBA5E)
     hist = method.History(p.n, a.M)

@@ -120,3 +120,22 @@ def test_startup_guess_is_zero():
     S = sketch.sparse_sign_matrix(p.n, 40, 8, 1)
     g = method.sketched_guess(A, b, np.zeros((p.n, 0)), S)
     assert np.all(g.x0 == 0.0)
+
+
+def test_recorded_spd_iterations_are_the_oracles(tmp_path):
+    """tests/golden/oracle_iterations_spd64.json is what the oracle produces
+    on the 64 x 64 SPD sequence (it is quoted beside the GPU's counts), and the
+    sketched guess needs fewer CG iterations than the previous solution."""
+    import json
+    import os
+    from oracle import measure_iterations
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    stored = json.load(open(os.path.join(root, "tests", "golden", "oracle_iterations_spd64.json")))
+    out = tmp_path / "spd.json"
+    measure_iterations.spd(str(out))
+    fresh = json.load(open(out))
+    for mode in ("sketch", "prev"):
+        # Equal here; a host with another BLAS may round a CG test differently.
+        for a, b in zip(fresh[mode]["systems"], stored[mode]["systems"]):
+            assert abs(a["iters"] - b["iters"]) <= 2
+    assert stored["sketch"]["iters_mean_full_history"] < 0.6 * stored["prev"]["iters_mean_full_history"]
