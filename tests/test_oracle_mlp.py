@@ -117,3 +117,31 @@ def test_he_uniform_bounds_and_moments():
     b = math.sqrt(6 / 160)
     assert W.shape == (256, 160) and np.abs(W).max() <= b
     assert abs(W.mean()) < 0.01 * b and abs(W.var() - b * b / 3) < 0.05 * b * b / 3
+
+
+def test_loss_is_the_excess_squared_relative_residual():
+    """With G = (AX)^T (AX) and the target y* = argmin ||A X y - b||, the loss of
+    a prediction y equals (||A X y - b||^2 - ||A X y* - b||^2) / ||b||^2, formed
+    here from explicit residuals; so it is never negative, and the net's
+    residual is never below the least-squares one."""
+    rng = np.random.default_rng(5)
+    p = _small_params(rng)
+    B, n, M = 3, 60, mlp.OUT
+    F = rng.standard_normal((B, mlp.IN))
+    y, _ = mlp.forward(p, F, dtype=np.float64, round_bf16=False)
+    T, G, nb, excess = [], [], [], []
+    for k in range(B):
+        AX = rng.standard_normal((n, M))
+        b = rng.standard_normal(n)
+        ys = np.linalg.lstsq(AX, b, rcond=None)[0]
+        T.append(ys)
+        G.append(AX.T @ AX)
+        nb.append(np.linalg.norm(b))
+        r_net = np.linalg.norm(AX @ y[k] - b)
+        r_opt = np.linalg.norm(AX @ ys - b)
+        assert r_net >= r_opt
+        excess.append((r_net ** 2 - r_opt ** 2) / nb[-1] ** 2)
+    loss, _ = mlp.loss_and_grad(p, F, np.array(T), np.array(G), np.array(nb), dtype=np.float64,
+                                round_bf16=False)
+    assert loss == pytest.approx(float(np.mean(excess)), rel=1e-9)
+    assert loss > 0
