@@ -34,6 +34,47 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def _cc(compiler):
+    import shutil
+    path = shutil.which(compiler)
+    if not path:
+        pytest.skip(f"{compiler} not available")
+    return path
+
+
+@pytest.mark.parametrize("compiler,std", [("gcc", "-std=c99"), ("g++", "-std=c++17")])
+def test_header_is_plain_c_and_cpp(compiler, std, tmp_path):
+    """include/seqaccel.h compiles warning-free as C99 and as C++17 (so the
+    boundary is usable without the Python binding)."""
+    import subprocess
+    src = tmp_path / ("use.c" if compiler == "gcc" else "use.cpp")
+    src.write_text('#include "seqaccel.h"\nint main(void) { return 0; }\n')
+    r = subprocess.run([_cc(compiler), std, "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-fsyntax-only", "-I", os.path.join(ROOT, "include"), str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
+def test_c_program_links_every_entry_point(tmp_path):
+    """A C program that takes the address of every declared entry point links
+    against the library (unmangled C symbols)."""
+    import subprocess
+    if not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2309_02156_gb300 import build
+    lib = build.build()
+    names = sorted(set(_declared()))
+    body = "\n".join(f"    (void)(uintptr_t)&{n};" for n in names)
+    src = tmp_path / "link.c"
+    src.write_text('#include <stdint.h>\n#include "seqaccel.h"\nint main(void) {\n'
+                   + body + "\n    return 0;\n}\n")
+    out = tmp_path / "link"
+    r = subprocess.run([_cc("gcc"), "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(out), lib, "-Wl,--unresolved-symbols=ignore-in-shared-libs"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_create_rejects_bad_config_without_gpu_work():
     """Argument validation happens on the host before any device call."""
     if not os.path.exists("/usr/local/cuda/bin/nvcc"):
