@@ -22,8 +22,10 @@ already meets the tolerance, Sections 4 and 5) can happen.  Conventions shared w
   polynomial preconditioners are the GPU-friendly members of the family the
   paper's runs use, ILU and AMG, Sections 4-5);
 * mixed refinement: r = b - A64 x in FP64; the correction d solves
-  A32 d = r / ||r|| by the same solver run entirely in float32, to a relative
-  residual max(inner_tol, theta * tol ||b|| / ||r||); x += ||r|| d in FP64.
+  A32 d = r (r rounded to float32; the same as solving for r / ||r|| and
+  scaling back, in exact arithmetic) by the same solver run entirely in
+  float32, to a relative residual max(inner_tol, theta * tol ||b|| / ||r||);
+  x += d in FP64.
   A GMRES inner solve is a single restart cycle, so every restart begins from
   a residual formed in FP64 (GMRES-based iterative refinement).
 
@@ -201,7 +203,7 @@ def mixed_refine(A64, A32, b, x, tol: float, inner: str, restart: int,
             return x, total, refinements, rn / bnorm, CONVERGED
         if (max_refinements is not None and refinements >= max_refinements) or total >= max_iters:
             return x, total, refinements, rn / bnorm, NOT_CONVERGED
-        rhs32 = (r / rn).astype(np.float32)
+        rhs32 = r.astype(np.float32)
         itol = max(inner_tol, theta * target / rn)
         d0 = np.zeros_like(rhs32)
         budget = max_iters - total
@@ -214,4 +216,4 @@ def mixed_refine(A64, A32, b, x, tol: float, inner: str, restart: int,
         refinements += 1
         if st == BREAKDOWN:
             return x, total, refinements, rn / bnorm, BREAKDOWN
-        x = x + rn * d.astype(np.float64)
+        x = x + d.astype(np.float64)
