@@ -59,3 +59,35 @@ def test_traffic_is_null_once_the_source_changes(tmp_path, monkeypatch):
     assert bench.profile_traffic("cgs_pass2", 1.0e6) is None
     os.remove(tmp_path / PROFILE)
     assert bench.profile_traffic("cgs_pass2", 1.0e6) is None
+
+
+def _run_reference(env_extra):
+    import json
+    import subprocess
+    env = dict(os.environ, **env_extra)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                       env=env, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    return [json.loads(l) for l in lines]
+
+
+def test_reference_arm_prints_one_line_with_the_contract_keys():
+    """`bench.py --impl reference` (the oracle on the host cores) prints one
+    JSON line with the main line's metric and unit, its own cpu_baseline and
+    an e2e object without host-device traffic."""
+    (line,) = _run_reference({"RANK": "0"})
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == "systems/s"
+    assert line["higher_is_better"] is True and line["n_gpus"] == 1
+    assert line["steps"] == 1 and line["warmup"] == 0
+    assert line["value"] > 0
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "systems/s",
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    assert _run_reference({"RANK": "1"}) == []
