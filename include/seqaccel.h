@@ -169,7 +169,7 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev,
  * inside FP64 iterative refinement of the true residual (a GMRES inner solve
  * is one restart cycle).  CG runs in one thread block for n < 65,536 and on
  * the whole GPU above (three kernels per iteration, captured as a CUDA graph
- * of 16 iterations); the iterations are the same either way.  With b = 0 the
+ * of 16 iterations); the algorithm and its stopping test are the same.  With b = 0 the
  * test is ||b - A x|| <= 0 and x = 0 passes it.  Does not push x.
  * Synchronises.
  * Errors: SEQ_EINVAL, SEQ_EBREAKDOWN (CG p^T A p <= 0, singular Hessenberg),
