@@ -117,6 +117,55 @@ def test_mixed_refinement_cg_inner():
     assert st == krylov.CONVERGED and rel <= 1e-10
 
 
+def _two_level_diagonal(k=8):
+    """A = diag(1, 3, 1, 3, ...) and b = ones (2k unknowns).  For a right-hand
+    side whose entries on the two halves have equal magnitude, the first CG
+    step has alpha = (r.r)/(r.Ar) = 1/2 exactly and leaves r1 = r0 (1 - lambda/2):
+    the magnitudes halve and the signs on the lambda = 3 half flip, so the
+    pattern repeats.  The second CG step solves exactly (two distinct
+    eigenvalues).  All values are powers of two, exact in float32."""
+    d = np.tile([1.0, 3.0], k)
+    A = scipy.sparse.diags(d).tocsr()
+    return A, A.astype(np.float32), np.ones(2 * k)
+
+
+@pytest.mark.parametrize("tol,theta,inner_tol,iters,refs", [
+    # inner tolerance max(0.1, 0.5 * 0.6) = 0.3 < 1/2: the inner CG takes both
+    # steps, one refinement suffices
+    (0.6, 0.5, 0.1, 2, 1),
+    # max(0.1, 0.9 * 0.6) = 0.54 >= 1/2: one inner step, residual 1/2 <= 0.6
+    (0.6, 0.9, 0.1, 1, 1),
+    # the floor 0.55 governs: one step, residual 1/2 <= 0.6
+    (0.6, 0.5, 0.55, 1, 1),
+    # one step per refinement: residuals 1/2 > 0.3, then 1/4 <= 0.3
+    (0.3, 0.5, 0.55, 2, 2),
+    # residual 2^-k after k refinements: ten to pass 1.5 * 2^-10
+    (1.5 * 2.0 ** -10, 0.5, 0.55, 10, 10),
+])
+def test_mixed_refinement_inner_tolerance_and_count(tol, theta, inner_tol, iters, refs):
+    """The inner relative tolerance is max(inner_tol, theta tol ||b|| / ||r||)
+    and every refinement is one inner solve from d = 0; on the two-level
+    diagonal system the CG residuals are known in closed form, so the inner
+    iterations and refinements of each case follow by hand (comments above)."""
+    A64, A32, b = _two_level_diagonal()
+    x, inner, nref, rel, st = krylov.mixed_refine(A64, A32, b, np.zeros_like(b), tol, "cg", 30,
+                                                  1000, inner_tol=inner_tol, theta=theta)
+    assert st == krylov.CONVERGED
+    assert (inner, nref) == (iters, refs)
+    if iters == refs:       # one halving step per refinement: exact residual 2^-refs
+        assert rel == 2.0 ** -refs
+
+
+def test_mixed_refinement_refinement_cap():
+    """max_refinements stops the loop with NOT_CONVERGED and the residual
+    reached: 2^-3 after three halving refinements."""
+    A64, A32, b = _two_level_diagonal()
+    x, inner, nref, rel, st = krylov.mixed_refine(A64, A32, b, np.zeros_like(b), 1e-6, "cg", 30,
+                                                  1000, inner_tol=0.55, max_refinements=3)
+    assert st == krylov.NOT_CONVERGED and nref == 3 and inner == 3 and rel == 2.0 ** -3
+    assert np.array_equal(np.abs(b - A64 @ x), np.full(b.size, 2.0 ** -3))
+
+
 def test_not_converged_status():
     A, b = _system(workloads.plain_nonsym(20), 1)
     x, it, rel, st = krylov.gmres(A, b, np.zeros_like(b), 1e-12, 30, 7)

@@ -145,3 +145,116 @@ def test_loss_is_the_excess_squared_relative_residual():
                                 round_bf16=False)
     assert loss == pytest.approx(float(np.mean(excess)), rel=1e-9)
     assert loss > 0
+
+
+# ---- Adam (Kingma and Ba, 2015): closed forms that a mistake in the update fails ----
+
+def _adam_run(grads, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, w0=0.0):
+    """Apply adam_update to one float64 scalar parameter for the gradient
+    sequence `grads`; returns the parameter after every step."""
+    w = [np.array([w0], dtype=np.float64)]
+    m = [np.zeros(1)]
+    v = [np.zeros(1)]
+    out = []
+    for t, g in enumerate(grads, start=1):
+        mlp.adam_update(w, [np.array([g])], m, v, t, lr=lr, b1=b1, b2=b2, eps=eps)
+        out.append(float(w[0][0]))
+    return out
+
+
+@pytest.mark.parametrize("g", [3.0, -0.25, 1e-8, -2e-9, 1e3])
+def test_adam_first_step_is_lr_times_g_over_abs_g_plus_eps(g):
+    """From zero moments the bias-corrected estimates after one step are g and
+    g^2 exactly, so the step is lr g / (|g| + eps).  Fails without the bias
+    correction (the step becomes about 3.16 lr sign(g)), with eps under the
+    square root (tiny g: g / sqrt(g^2 + eps) is far from g / (|g| + eps)), or
+    with a sign step lr sign(g)."""
+    lr, eps = 1e-3, 1e-8
+    w1 = _adam_run([g], lr=lr, eps=eps)[0]
+    assert w1 == pytest.approx(-lr * g / (abs(g) + eps), rel=1e-12)
+
+
+@pytest.mark.parametrize("g", [0.7, -5.0, 1e-8])
+def test_adam_constant_gradient_moves_at_a_constant_rate(g):
+    """A constant gradient keeps both bias-corrected moments exact (m_hat = g,
+    v_hat = g^2: the correction divides out the geometric weights), so every
+    step is the same lr g / (|g| + eps) and w_T = -T lr g / (|g| + eps).
+    Fails if beta1 and beta2 are swapped in either the decay or the correction."""
+    lr, eps, T = 1e-2, 1e-8, 40
+    ws = _adam_run([g] * T, lr=lr, eps=eps)
+    step = lr * g / (abs(g) + eps)
+    for t, w in enumerate(ws, start=1):
+        assert w == pytest.approx(-t * step, rel=1e-10)
+
+
+def test_adam_alternating_gradient_closed_form():
+    """g_t = (-1)^t c.  Then v_hat_t = c^2 (g^2 is constant) and, summing the
+    geometric series of the first moment,
+        m_hat_t = c (-1)^t (1 - b1) (1 - (-b1)^t) / ((1 + b1) (1 - b1^t)),
+    so the step at t is lr m_hat_t / (|c| + eps).  Pins beta1 on the first
+    moment and beta2 on the second: exchanging them, or decaying the second
+    moment with beta1, changes v_hat away from c^2."""
+    lr, b1, b2, eps, c, T = 1e-2, 0.9, 0.999, 1e-8, 0.5, 12
+    ws = _adam_run([(-1) ** t * c for t in range(1, T + 1)], lr=lr, b1=b1, b2=b2, eps=eps)
+    prev = 0.0
+    for t, w in enumerate(ws, start=1):
+        mhat = c * (-1) ** t * (1 - b1) * (1 - (-b1) ** t) / ((1 + b1) * (1 - b1 ** t))
+        assert (w - prev) == pytest.approx(-lr * mhat / (abs(c) + eps), rel=1e-9, abs=1e-15)
+        prev = w
+    # The first step is a full lr step against g_1 = -c; the second, against +c,
+    # is only a fraction of lr because the first moment still remembers -c.
+    assert ws[0] == pytest.approx(lr * c / (c + eps), rel=1e-12)
+    assert 0 < ws[0] - ws[1] < 0.1 * lr
+
+
+def test_adam_second_step_uses_normalised_moving_averages():
+    """After two steps with gradients a then c, each bias-corrected moment is
+    the average of the two samples with weights (beta, 1) normalised to sum 1:
+    m_hat = (b1 a + c) / (1 + b1) and v_hat = (b2 a^2 + c^2) / (1 + b2).
+    Gradients of different magnitude separate beta1 from beta2 in the second
+    moment (decaying and correcting it with beta1 fails here)."""
+    lr, b1, b2, eps, a, c = 1e-3, 0.9, 0.999, 1e-8, 1.0, 3.0
+    w1, w2 = _adam_run([a, c], lr=lr, b1=b1, b2=b2, eps=eps)
+    mhat = (b1 * a + c) / (1 + b1)
+    vhat = (b2 * a * a + c * c) / (1 + b2)
+    assert w2 - w1 == pytest.approx(-lr * mhat / (math.sqrt(vhat) + eps), rel=1e-9)
+
+
+def test_adam_float32_arrays_update_in_place():
+    """The update works in place on float32 parameter arrays (the GPU keeps
+    FP32 master weights) and leaves their dtype unchanged."""
+    w = [np.array([1.0, -1.0], dtype=np.float32)]
+    m = [np.zeros(2, np.float32)]
+    v = [np.zeros(2, np.float32)]
+    ref = w[0]
+    mlp.adam_update(w, [np.array([0.5, -0.5], np.float32)], m, v, 1, lr=0.1)
+    assert w[0] is ref and w[0].dtype == np.float32
+    assert np.allclose(w[0], [0.9, -0.9], rtol=1e-6)
+
+
+# ---- He-uniform initialisation: stream layout and distribution ----
+
+def test_he_uniform_stream_layout():
+    """Entry (i, j) of a fan_out x fan_in block takes SplitMix64 output
+    stream_offset + 1 + i fan_in + j: a block equals the rows of a longer
+    draw, row i of it equals row 0 of the draw offset by i fan_in, and the
+    scale is sqrt(6 / fan_in) on a common unit draw."""
+    W = mlp.he_uniform(7, 6, 10, 100)
+    flat = mlp.he_uniform(7, 1, 60, 100)                   # same outputs, other bound
+    scale = math.sqrt(6 / 10) / math.sqrt(6 / 60)
+    assert np.allclose(W.reshape(-1), flat.reshape(-1) * scale, rtol=1e-6, atol=0)
+    for i in range(6):
+        row = mlp.he_uniform(7, 1, 10, 100 + 10 * i)
+        assert np.array_equal(W[i], row[0])
+    assert not np.array_equal(mlp.he_uniform(8, 6, 10, 100), W)   # the seed matters
+
+
+def test_he_uniform_is_uniform_on_its_interval():
+    """Kolmogorov-Smirnov against U(-b, b), b = sqrt(6 / fan_in), on 40,960
+    draws; the variance is b^2 / 3 = 2 / fan_in (He et al., 2015)."""
+    from scipy import stats
+    fan_in = 160
+    W = mlp.he_uniform(123, 256, fan_in, 0).astype(np.float64).reshape(-1)
+    b = math.sqrt(6 / fan_in)
+    assert stats.kstest(W, stats.uniform(loc=-b, scale=2 * b).cdf).pvalue > 1e-3
+    assert W.var() == pytest.approx(2 / fan_in, rel=0.03)
