@@ -348,9 +348,10 @@ int seq_batch_set_schedule(seq_batch* batch, int32_t threads, int32_t blocks_per
 /* The sketched block W = S [A X | b] computed without allocating any device
  * memory.  The paper has no counterpart: this is a deployment variant of the
  * sketch step for callers that cannot call cudaMalloc where they need W --
- * code recorded into a CUDA graph by stream capture (allocation is not
- * capturable), host callbacks and real-time loops that must not block in the
- * allocator, and hosts that fix the library's memory budget up front.
+ * host callbacks and real-time loops that must not block in the allocator
+ * (cudaMalloc can synchronise the device and take milliseconds), and hosts
+ * that hand the GPU's memory to their own pool or fix the library's memory
+ * budget up front, so that a later allocation would fail.
  *
  * Inputs (device): CSR A (n rows, nnz entries), X (n x M, row i at
  * X[i * ldx .. i * ldx + M - 1], column k is the k-th history vector), b (n).
@@ -359,13 +360,14 @@ int seq_batch_set_schedule(seq_batch* batch, int32_t threads, int32_t blocks_per
  * of the library (entries +-1/sqrt(zeta)).
  * Limits: s * (M + 1) <= 4096, M <= 31, zeta <= min(s, 16); larger sizes
  * return SEQ_EINVAL before any GPU work.  Column indices outside [0, n) give
- * SEQ_EINVAL after the call.
+ * SEQ_EINVAL after the call; the next call starts from a cleared flag.
  * Scratch: a fixed device array of about 5 MB defined in the library, held by
  * every GPU that loads the library until the process exits.  All calls share
  * it and it keeps the last call's contents; calls that overlap on the GPU
  * race on it.  The first call on a device looks up the array's address
  * (cudaGetSymbolAddress) with that device current, so make that first call
- * before any stream capture.  Synchronises cuda_stream before returning. */
+ * before any stream capture.  Each call ends by reading the column-index
+ * flag back to the host and synchronising cuda_stream. */
 int seq_sketch_block_noalloc(int32_t n, int32_t nnz, const int32_t* rowptr, const int32_t* colind,
                              const double* values, const double* X, int32_t ldx, int32_t M,
                              const double* b, int32_t s, int32_t zeta, uint64_t seed,

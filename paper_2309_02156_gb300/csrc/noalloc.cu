@@ -2,12 +2,13 @@
 // without any device allocation.
 //
 // Who needs it: callers that cannot call cudaMalloc at the point where they
-// need W -- code running while a CUDA stream is being captured into a graph
-// (allocation calls are not capturable), code inside a host callback or a
-// real-time loop that must not block in the allocator, and hosts that hand
-// the library a fixed memory budget up front.  They pass their own inputs and
-// output; the only scratch the kernels use (one partial block of W per thread
-// block) lives in a file-scope device array of fixed size.
+// need W -- code inside a host callback or a real-time loop that must not
+// block in the allocator (cudaMalloc may synchronise the device), and hosts
+// that give the GPU's memory to their own pool or fix the library's memory
+// budget up front, so that an allocation made later would fail.  They pass
+// their own inputs and output; the only scratch the kernels use (one partial
+// block of W per thread block) lives in a file-scope device array of fixed
+// size.
 //
 // Limits and sharing:
 //   * s * (M + 1) <= kNoAllocSlots (4096: s <= 128 with M <= 31), zeta <= 16;
@@ -21,7 +22,9 @@
 //     clears the error word first, so nothing else needs clearing.
 //   * The first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress) with that device current; make that first call
-//     before any stream capture that will contain later calls.
+//     before any stream capture.
+//   * Each call ends by copying the column-index flag to the host and
+//     synchronising the caller's stream.
 //
 // The sketch is the same sparse-sign S as everywhere in the library (column
 // j: zeta distinct rows from SplitMix64 outputs 256 j + c + 1, row =
