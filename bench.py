@@ -148,26 +148,56 @@ def profile_traffic(kind, algorithmic_bytes):
     return vals["ratio"] * algorithmic_bytes
 
 
+def config_line(world=1):
+    """The `config` object of both arms' lines (same workload, same keys)."""
+    return {"workload": WORKLOAD, "form": "plain FP64", "history_primed": M_HIST,
+            "l2": "inputs larger than L2 (history 168 MB, basis 260 MB, new A(t_i) per step)",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+def _oracle_sample_step(A, b, hist, S, gmres_iters):
+    """One bounded oracle step: the sketched guess of Algorithm 1 from the
+    history, then `gmres_iters` GMRES(30) iterations from it (the tolerance is
+    unreachable, so exactly that many run); the iterate is pushed.  Returns
+    (guess seconds, seconds per iteration, iterations)."""
+    from oracle import krylov, method
+    t0 = time.perf_counter()
+    g = method.sketched_guess(A, b, hist.matrix(), S)
+    t1 = time.perf_counter()
+    xk, it, _, _ = krylov.gmres(A, b, g.x0, 1e-30, RESTART, gmres_iters)
+    t2 = time.perf_counter()
+    hist.push(xk)
+    return t1 - t0, (t2 - t1) / max(it, 1), it
+
+
+def _oracle_history(p, S, upto, gmres_iters):
+    """The oracle's own history for system `upto`: systems 0..upto-1 run through
+    _oracle_sample_step (guess + capped GMRES, iterate pushed)."""
+    from oracle import krylov, method
+    import workloads
+    hist = method.History(p.n, M_HIST)
+    for i in range(max(0, upto - M_HIST), upto):
+        rowptr, colind, vals, b = workloads.csr_system(p, i)
+        _oracle_sample_step(krylov.csr(rowptr, colind, vals, p.n), b, hist, S, gmres_iters)
+    return hist
+
+
 def cpu_baseline_worker(iters_per_system: float, gmres_iters: int) -> None:
     """Time the oracle on a bounded sample (with the BLAS threads the caller
     set) and print one JSON line."""
-    import numpy as np
     import workloads
-    from oracle import krylov, method, sketch
+    from oracle import krylov, sketch
     p = workloads.plain_nonsym(N_GRID)
+    S = sketch.sparse_sign_matrix(p.n, S_ROWS, ZETA, SEED)
     i = M_HIST + 3
+    hist = _oracle_history(p, S, i, 10)
     rowptr, colind, vals, b = workloads.csr_system(p, i)
     A = krylov.csr(rowptr, colind, vals, p.n)
-    X = np.stack([workloads.rhs(p, workloads.time_grid(p, k)) for k in range(i - M_HIST, i)], 1)
-    S = sketch.sparse_sign_matrix(p.n, S_ROWS, ZETA, SEED)
     t0 = time.perf_counter()
-    g = method.sketched_guess(A, b, X, S)
-    t_guess = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    _, it, _, _ = krylov.gmres(A, b, g.x0, 1e-30, RESTART, gmres_iters)
-    t_iter = (time.perf_counter() - t0) / max(it, 1)
-    per_system = t_guess + iters_per_system * t_iter
-    print(json.dumps({"t_guess": t_guess, "t_iter": t_iter, "iters_sampled": it,
+    tg, ti, it = _oracle_sample_step(A, b, hist, S, gmres_iters)
+    timed = time.perf_counter() - t0
+    per_system = tg + iters_per_system * ti
+    print(json.dumps({"t_guess": tg, "t_iter": ti, "iters_sampled": it, "timed_s": timed,
                       "per_system_s": per_system, "value": 1.0 / per_system}))
 
 
@@ -186,10 +216,16 @@ def run_cpu_baseline(iters_per_system: float, gmres_iters: int = 120, threads: i
     d = json.loads(r.stdout.strip().splitlines()[-1])
     where = "1 host thread" if threads == 1 else f"{threads} host threads"
     return {"value": d["value"], "unit": "systems/s", "cores": threads, "kind": "oracle",
-            "sample": (f"one 1024x1024 system: oracle sketched guess ({d['t_guess']:.2f} s) + "
+            "timed_s": d["timed_s"],
+            "extrapolated": {"timed_iterations": d["iters_sampled"],
+                             "iterations_per_system": iters_per_system,
+                             "formula": "1 / (guess seconds + iterations_per_system x seconds "
+                                        "per timed iteration)"},
+            "sample": (f"one 1024x1024 system (history: the oracle's own iterates of the 20 "
+                       f"systems before it): oracle sketched guess ({d['t_guess']:.2f} s) + "
                        f"{d['iters_sampled']} GMRES(30) iterations ({d['t_iter'] * 1e3:.1f} ms each) "
-                       f"on {where}, per-system time = guess + {iters_per_system:.1f} "
-                       f"iterations (mean of the GPU run)")}
+                       f"on {where}, timed {d['timed_s']:.1f} s; per-system time = guess + "
+                       f"{iters_per_system:.1f} iterations (mean of the GPU run)")}
 
 
 def oracle_iterations_per_system():
@@ -202,43 +238,52 @@ def oracle_iterations_per_system():
 
 
 def reference_arm(args):
-    """The oracle timed on the host cores, same metric and workload, bounded samples."""
+    """The oracle timed on the host cores, same metric and workload.  Each step
+    is a bounded sample of one system of the sequence: the oracle's sketched
+    guess from its own history, then 30 GMRES(30) iterations, the iterate
+    pushed into the history.  `steps` and `ms_per_step` describe exactly those
+    timed samples; `value` extrapolates them to whole systems with the oracle's
+    own recorded iteration count (field `extrapolated`)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     ips, src = oracle_iterations_per_system()
-    import numpy as np
     import workloads
-    from oracle import krylov, method, sketch
+    from oracle import krylov, sketch
     p = workloads.plain_nonsym(N_GRID)
     S = sketch.sparse_sign_matrix(p.n, S_ROWS, ZETA, SEED)
     gmres_iters = 30
-    times = []
+    hist = _oracle_history(p, S, M_HIST, gmres_iters)
+    rows = []
     for step in range(args.warmup + args.steps):
         i = M_HIST + step
         rowptr, colind, vals, b = workloads.csr_system(p, i)
         A = krylov.csr(rowptr, colind, vals, p.n)
-        X = np.stack([workloads.rhs(p, workloads.time_grid(p, k)) for k in range(i - M_HIST, i)], 1)
         t0 = time.perf_counter()
-        g = method.sketched_guess(A, b, X, S)
-        t1 = time.perf_counter()
-        _, it, _, _ = krylov.gmres(A, b, g.x0, 1e-30, RESTART, gmres_iters)
-        t2 = time.perf_counter()
+        tg, ti, it = _oracle_sample_step(A, b, hist, S, gmres_iters)
+        dt = time.perf_counter() - t0
         if step >= args.warmup:
-            times.append((t1 - t0, (t2 - t1) / max(it, 1)))
-    tg = statistics.mean(t[0] for t in times)
-    ti = statistics.mean(t[1] for t in times)
+            rows.append((tg, ti, dt))
+    tg = statistics.mean(r[0] for r in rows)
+    ti = statistics.mean(r[1] for r in rows)
+    ms_step = 1e3 * statistics.mean(r[2] for r in rows)
     iters = ips if ips else 0.0
     per = tg + iters * ti
     value = 1.0 / per
     cores = int(os.environ.get("OPENBLAS_NUM_THREADS", "0")) or os.cpu_count()
-    sample = (f"per step: oracle sketched guess + {gmres_iters} GMRES(30) iterations on a "
-              f"1024x1024 system; per-system time = guess + {iters:.1f} iterations ({src})")
+    sample = (f"per step: one 1024x1024 system, oracle sketched guess from the oracle's own "
+              f"history + {gmres_iters} GMRES(30) iterations ({ms_step:.0f} ms); per-system time "
+              f"= guess + {iters:.1f} iterations ({src})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "systems/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+            "config": config_line(1),
+            "extrapolated": {"timed_iterations_per_step": gmres_iters,
+                             "iterations_per_system": iters, "source": src,
+                             "guess_s": tg, "iteration_s": ti,
+                             "formula": "value = 1 / (guess_s + iterations_per_system x "
+                                        "iteration_s); ms_per_step is the timed sample"},
             "cpu_baseline": {"value": value, "unit": "systems/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0,
@@ -399,6 +444,22 @@ def _gen_learned(job):
 
 
 def learned_ablation(args):
+    """The learned form's ablation as a separate mode (one JSON line)."""
+    print(json.dumps(learned_run(args.learned_train, args.learned_eval, args.learned_grid,
+                                 args.learned_seqs, args.learned_epochs)), flush=True)
+
+
+def learned_bounded(args):
+    """A bounded ablation of the learned form for the default line: one 512 x 512
+    sequence, training on systems 0..119, evaluation on 120..159."""
+    out = learned_run(120, 40, 512, 1, args.learned_epochs)
+    out["bound"] = ("the least-squares y minimises the sketched residual, so the network can at "
+                    "best equal it on that measure (rho_s(net) >= rho_s(LS)); its guess is used "
+                    "when rho_s(net) <= 1.5 rho_s(LS)")
+    return out
+
+
+def learned_run(T, E, N, nseq, epochs):
     """Learned coefficient predictor against sketched least squares.
 
     Workload: advection-diffusion sequences as in the main line on a 512 x 512
@@ -409,7 +470,6 @@ def learned_ablation(args):
     least-squares path's solution is pushed into both); each evaluation system
     is solved from both guesses.  Prints one JSON line."""
     import numpy as np
-    T, E, N, nseq = args.learned_train, args.learned_eval, args.learned_grid, args.learned_seqs
     amps = __import__("workloads").learned_amplitudes(nseq, SEED)
     pool = mp.get_context("spawn").Pool(8)
     import torch
@@ -461,7 +521,7 @@ def learned_ablation(args):
     net.fit_normalization(St)
     torch.cuda.synchronize()
     t1 = time.time()
-    losses = net.train(St, epochs=args.learned_epochs, batch=32, lr=1e-3, seed=SEED)
+    losses = net.train(St, epochs=epochs, batch=32, lr=1e-3, seed=SEED)
     torch.cuda.synchronize()
     train_s = time.time() - t1
     rec = {"ls_guess": [], "net_guess": [], "ls_iters": [], "net_iters": [], "fallback": [],
@@ -507,7 +567,7 @@ def learned_ablation(args):
         "workload": "advection-diffusion %dx%d (n=%d), a ~ U[0.2,0.8] x %d sequences, M=20, s=80, "
                     "GMRES(30) to 1e-8; train steps 0..%d, evaluate %d..%d"
                     % (N, N, n, nseq, T - 1, T, T + E - 1),
-        "amplitudes": amps, "samples": int(St.shape[0]), "epochs": args.learned_epochs,
+        "amplitudes": amps, "samples": int(St.shape[0]), "epochs": epochs,
         "loss_first_epoch": float(losses[0]), "loss_last_epoch": float(losses[-1]),
         "train_seconds": train_s, "data_seconds": gen_s,
         "train_iters_mean": float(np.mean(train_iters)),
@@ -525,8 +585,8 @@ def learned_ablation(args):
         "ls_y_absmax_geomean": gm(rec["ymax"]),
         "net_over_ls_guess_relres_geomean": gm(np.asarray(rec["net_guess"]) / np.asarray(rec["ls_guess"])),
     }
-    print(json.dumps(out), flush=True)
     net.close()
+    return out
 
 
 def spd_small(steps=60):
@@ -857,6 +917,75 @@ def precision_form(args):
     print(json.dumps(out), flush=True)
 
 
+def precision_startup(hbm_peak):
+    """The precision form on the first five systems of the 2048 x 2048 sequence
+    (SEQ_MIXED: FP32 values, history, sketch and inner GMRES(30) right-
+    preconditioned by 8 damped Jacobi sweeps, FP64 refinement to 1e-10), with
+    the error of every solution against the oracle's direct solve recorded by
+    oracle/reference_solutions.py (sampled entries; see the error estimate
+    there).  Systems 0..4 have histories of 0..4 columns."""
+    import numpy as np
+    import torch
+    import paper_2309_02156_gb300 as sa
+    import workloads
+    path = os.path.join(ROOT, "tests", "golden", "reference_solutions_nonsym2048.json")
+    ref = json.load(open(path)) if os.path.exists(path) else None
+    N, tol, steps = 2048, 1e-10, 5
+    with mp.get_context("spawn").Pool(5) as pool:
+        systems = pool.map(_gen_nonsym, [(N, i) for i in range(steps)])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rowptr, colind, _ = workloads.pattern(N)
+    rp = torch.from_numpy(rowptr).to(dev)
+    ci = torch.from_numpy(colind).to(dev)
+    n = N * N
+    seq = sa.Sequence(n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, precision="mixed", krylov="gmres",
+                      restart=RESTART, max_iters=400000, precond_sweeps=8)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for i, (v, b) in enumerate(systems):
+        vd = torch.from_numpy(v).to(dev)
+        bd = torch.from_numpy(b).to(dev)
+        A = sa.CSR(rp, ci, vd)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g = seq.guess(A, bd, x)
+        info = seq.solve(A, bd, tol, x)
+        seq.push(x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        row = {"i": i, "history_cols": g["history_cols"], "guess_relres": g["guess_relres"],
+               "inner_iters": info["iters"], "refinements": info["refinements"],
+               "final_relres": info["final_relres"], "status": info["status"],
+               "ms": e0.elapsed_time(e1)}
+        if ref and i < len(ref["systems"]):
+            r = ref["systems"][i]
+            idx = torch.tensor(r["idx"], dtype=torch.int64, device=dev)
+            xs = x[idx].cpu().numpy()
+            xo = np.asarray(r["x"])
+            row["err_vs_oracle"] = float(math.sqrt(n / len(idx) * float(np.sum((xs - xo) ** 2)))
+                                         / r["norm2"])
+            row["err_max_sampled"] = float(np.max(np.abs(xs - xo)) / np.max(np.abs(xo)))
+            row["norm_rel_diff"] = abs(float(torch.linalg.vector_norm(x)) - r["norm2"]) / r["norm2"]
+        rows.append(row)
+    seq.close()
+    total = sum(r["ms"] for r in rows)
+    return {
+        "form": "precision: nonsym 2048x2048 (n=4194304), FP32 values/history/sketch/inner "
+                "GMRES(30) with 8 Jacobi sweeps, FP64 QR, refinement residual and test to 1e-10",
+        "systems": "0..4 (start of the sequence: histories of 0..4 columns)",
+        "value": 1e3 * steps / total, "unit": "systems/s", "ms_per_step": total / steps,
+        "all_converged": all(r["status"] == 0 for r in rows),
+        "error_reference": ("oracle.krylov.direct_solve (sparse LU + FP64 refinement), "
+                            "recorded by oracle/reference_solutions.py: err = sqrt(n/k sum "
+                            "(x - x_oracle)^2 over k = 4096 sampled entries) / ||x_oracle||")
+        if ref else "no recorded reference solutions",
+        "per_step": rows,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -897,6 +1026,8 @@ def main():
     ap.add_argument("--learned-grid", type=int, default=512)
     ap.add_argument("--learned-seqs", type=int, default=1)
     ap.add_argument("--learned-epochs", type=int, default=300)
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     if args.learned_ablation:
         learned_ablation(args)
@@ -932,8 +1063,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     K, W = args.steps, args.warmup
-    steps_dev = list(range(M_HIST + W + K))
-    steps_e2e = list(range(M_HIST + W + K, M_HIST + W + 2 * K))
+    KP = max(1, min(K, 3))          # steps of the separate per-kernel profiled pass
+    steps_dev = list(range(M_HIST + W + K + KP))
+    steps_e2e = list(range(steps_dev[-1] + 1, steps_dev[-1] + 1 + K))
     host = generate(steps_dev + steps_e2e)     # before any CUDA call (spawn pool)
 
     import numpy as np
@@ -964,68 +1096,88 @@ def main():
         seq.push(x)
         return g, info
 
-    prime = [step(i) for i in range(M_HIST)]
-    for i in range(M_HIST, M_HIST + W):
-        step(i)
     fp64_peak = sa.probe_fp64_peak()
     hbm_peak, hbm_src = peaks()
+    stream = torch.cuda.current_stream()
+    t_first = M_HIST + W
+    timed_steps = range(t_first, t_first + K)
+    prof_steps = range(t_first + K, t_first + K + KP)
+
+    def timed(steps):
+        """Device time (max over ranks) of seq steps, un-instrumented."""
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = [step(i) for i in steps]
+        b.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        return max_over_ranks(a.elapsed_time(b), dist, dev), out
+
+    def profiled(steps):
+        """Per-kernel statistics (CUDA events between the kernels of the
+        restart-cycle graph) over a separate pass of seq steps."""
+        seq.set_profiling(True)
+        seq.kernel_stats(reset=True)
+        out = [step(i) for i in steps]
+        torch.cuda.synchronize()
+        st = seq.kernel_stats(reset=True)
+        seq.set_profiling(False)
+        return st, out
+
+    def roofline(stats, label_steps):
+        dom = max(stats, key=lambda k: stats[k]["ms"])
+        st = stats[dom]
+        t_launch = st["ms"] / 1e3 / max(st["launches"], 1)
+        bytes_l = st["bytes"] / max(st["launches"], 1)
+        flops_l = st["flops"] / max(st["launches"], 1)
+        t_hbm = bytes_l / (hbm_peak * 1e9)
+        t_alu = flops_l / (fp64_peak * 1e12)
+        if t_alu > t_hbm:
+            roof = {"bound": "alu", "achieved": flops_l / t_launch / 1e12, "peak": fp64_peak,
+                    "unit": "TFLOP/s", "peak_source": "FP64 FMA probe measured in this run"}
+        else:
+            roof = {"bound": "hbm", "achieved": bytes_l / t_launch / 1e9, "peak": hbm_peak,
+                    "unit": "GB/s", "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["traffic"] = profile_traffic(dom, bytes_l)
+        roof["kernel"] = dom
+        roof["algorithmic_bytes_per_launch"] = bytes_l
+        roof["algorithmic_flops_per_launch"] = flops_l
+        roof["launch_us"] = t_launch * 1e6
+        roof["timing"] = ("CUDA events on the context's stream between the kernels of the "
+                          "restart-cycle graph, averaged over every launch of a separate "
+                          "profiled pass (systems %d..%d)" % (label_steps[0], label_steps[-1]))
+        total_ms = sum(v["ms"] for v in stats.values())
+        kernels = {k: {"launches": v["launches"],
+                       "share": v["ms"] / total_ms if total_ms else None,
+                       "GB/s": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] else None,
+                       "TFLOP/s": v["flops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] else None}
+                   for k, v in stats.items() if v["launches"]}
+        return roof, kernels
+
+    prime = [step(i) for i in range(M_HIST)]
+    for i in range(M_HIST, t_first):
+        step(i)
     gpu_index = local
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     if vis and vis.split(",")[local].strip().isdigit():
         gpu_index = int(vis.split(",")[local])
     sampler = ClockSampler(gpu_index)
-    seq.set_profiling(True)
-    seq.kernel_stats(reset=True)
-    stream = torch.cuda.current_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     sampler.start()
-    e0.record(stream)
-    infos = []
-    for i in range(M_HIST + W, M_HIST + W + K):
-        infos.append(step(i))
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, infos = timed(timed_steps)
     clocks = sampler.stop()
-    if dist:
-        dist.barrier()
-    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-    stats = seq.kernel_stats(reset=True)
-    seq.set_profiling(False)
+    stats, _ = profiled(prof_steps)
     value = whole_job_rate(K, ms, world)
     iters = [inf["iters"] for _, inf in infos]
     launches = sum(g["launches"] + inf["launches"] + 1 for g, inf in infos)
     worst = max(inf["final_relres"] for _, inf in infos)
     assert all(inf["status"] == 0 for _, inf in infos), "a timed solve did not converge"
-
-    # Dominant kernel and its roofline.
-    dom = max(stats, key=lambda k: stats[k]["ms"])
-    st = stats[dom]
-    t_launch = st["ms"] / 1e3 / max(st["launches"], 1)
-    bytes_l = st["bytes"] / max(st["launches"], 1)
-    flops_l = st["flops"] / max(st["launches"], 1)
-    t_hbm = bytes_l / (hbm_peak * 1e9)
-    t_alu = flops_l / (fp64_peak * 1e12)
-    if t_alu > t_hbm:
-        roof = {"bound": "alu", "achieved": flops_l / t_launch / 1e12, "peak": fp64_peak,
-                "unit": "TFLOP/s", "peak_source": "FP64 FMA probe measured in this run"}
-    else:
-        roof = {"bound": "hbm", "achieved": bytes_l / t_launch / 1e9, "peak": hbm_peak,
-                "unit": "GB/s", "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = profile_traffic(dom, bytes_l)
-    roof["kernel"] = dom
-    roof["algorithmic_bytes_per_launch"] = bytes_l
-    roof["algorithmic_flops_per_launch"] = flops_l
-    roof["launch_us"] = t_launch * 1e6
-    total_ms = sum(v["ms"] for v in stats.values())
-    kernels = {k: {"launches": v["launches"], "share": v["ms"] / total_ms if total_ms else None,
-                   "GB/s": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] else None,
-                   "TFLOP/s": v["flops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] else None}
-               for k, v in stats.items()}
+    roof, kernels = roofline(stats, list(prof_steps))
 
     # End to end: host inputs copied in each step, solution copied out.
     pin = {i: (torch.from_numpy(host[i][0]).pin_memory(), torch.from_numpy(host[i][1]).pin_memory())
@@ -1070,27 +1222,14 @@ def main():
         seq = sa.Sequence(n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, krylov="gmres",
                           restart=RESTART, max_iters=60000, precision=precision,
                           precond_sweeps=sweeps)
-        for i in range(M_HIST + W):
+        for i in range(t_first):
             step(i)
-        seq.set_profiling(True)
-        seq.kernel_stats(reset=True)
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        c0 = torch.cuda.Event(enable_timing=True)
-        c1 = torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        cinfos = [step(i) for i in range(M_HIST + W, M_HIST + W + K)]
-        c1.record(stream)
-        torch.cuda.synchronize()
-        cms = max_over_ranks(c0.elapsed_time(c1), dist, dev)
-        cst = seq.kernel_stats(reset=True)
-        seq.set_profiling(False)
+        cms, cinfos = timed(timed_steps)
+        cst, _ = profiled(prof_steps)
         assert all(inf["status"] == 0 for _, inf in cinfos), "a %s solve did not converge" % label
-        cdom = max(cst, key=lambda k: cst[k]["ms"])
-        cs = cst[cdom]
-        ct = cs["ms"] / 1e3 / max(cs["launches"], 1)
-        cb = cs["bytes"] / max(cs["launches"], 1)
+        croof, ckern = roofline(cst, list(prof_steps))
+        if croof["bound"] == "hbm":
+            croof.pop("traffic", None)
         return {
             "form": label, "value": whole_job_rate(K, cms, world), "unit": "systems/s",
             "ms_per_step": cms / K,
@@ -1098,13 +1237,7 @@ def main():
             "iters_per_system": float(np.mean([inf["iters"] for _, inf in cinfos])),
             "refinements_per_system": float(np.mean([inf["refinements"] for _, inf in cinfos])),
             "final_relres_max": max(inf["final_relres"] for _, inf in cinfos),
-            "vs_plain": whole_job_rate(K, cms, world) / value,
-            "roofline": {"bound": "hbm", "kernel": cdom, "achieved": cb / ct / 1e9,
-                         "peak": hbm_peak, "unit": "GB/s", "frac": cb / ct / 1e9 / hbm_peak,
-                         "launch_us": ct * 1e6, "algorithmic_bytes_per_launch": cb},
-            "kernels": {k: {"launches": v["launches"],
-                            "GB/s": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] else None}
-                        for k, v in cst.items() if v["launches"]},
+            "roofline": croof, "kernels": ckern,
             "gpu_launches": sum(g["launches"] + inf["launches"] + 1 for g, inf in cinfos),
         }
 
@@ -1114,6 +1247,7 @@ def main():
         chosen = run_form("FP64 history/sketch/QR/guess, FP32 GMRES(30)-CGS2 inner solves, FP64 "
                           "iterative refinement of the true residual to rel-res 1e-8",
                           "mixed_krylov", 0)
+        chosen["vs_plain_f64"] = chosen["value"] / value
         preconditioned = {
             "f64_jacobi4": run_form("FP64 GMRES(30) right-preconditioned by 4 damped Jacobi "
                                     "sweeps (omega 0.8), rel-res 1e-8", "f64", 4),
@@ -1121,15 +1255,31 @@ def main():
                                       "damped Jacobi sweeps, FP64 refinement to rel-res 1e-8",
                                       "mixed_krylov", 8),
         }
+        f64p = preconditioned["f64_jacobi4"]
+        mixp = preconditioned["mixed_jacobi8"]
+        f64p["vs_plain_f64"] = f64p["value"] / value
+        mixp["vs_plain_f64"] = mixp["value"] / value
+        mixp["vs_f64_jacobi4"] = mixp["value"] / f64p["value"]
+        preconditioned["note"] = ("precision gain like for like: chosen.vs_plain_f64 (both "
+                                  "unpreconditioned) and mixed_jacobi8.vs_f64_jacobi4 (both "
+                                  "preconditioned, each with its best sweep count)")
+    seq.close()
 
     batched = None
     if not args.no_batched:
-        seq.close()
         batched = batched_form(args.batched_steps, 2, hbm_peak)
 
     small = None
     if not args.no_chosen:
         small = spd_small()
+
+    precision = None
+    if not args.no_precision:
+        precision = precision_startup(hbm_peak)
+
+    learned = None
+    if not args.no_learned:
+        learned = learned_bounded(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1137,16 +1287,17 @@ def main():
         ncores = os.cpu_count() or 1
         if cpu.get("value") is not None and ncores > 1:
             allc = run_cpu_baseline(float(np.mean(iters)), threads=ncores)
-            cpu["all_cores"] = {k: allc.get(k) for k in ("value", "cores", "sample", "error")
-                                if k in allc}
+            cpu["all_cores"] = {k: allc.get(k) for k in ("value", "cores", "sample", "timed_s",
+                                                         "extrapolated", "error") if k in allc}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": world,
             "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": "plain FP64", "history_primed": M_HIST,
-                       "l2": "inputs larger than L2 (history 168 MB, basis 260 MB, new A(t_i) per step)",
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": config_line(world),
+            "timing": ("value: CUDA events around K un-instrumented steps (guess + solve + push); "
+                       "roofline and kernel shares: a separate profiled pass of %d further "
+                       "steps" % KP),
             "iters_per_system": float(np.mean(iters)),
             "iters_per_system_prev_steps": [inf["iters"] for _, inf in prime[-3:]],
             "guess_relres_mean": float(np.mean([g["guess_relres"] for g, _ in infos])),
@@ -1156,13 +1307,14 @@ def main():
             "preconditioned": preconditioned,
             "spd_4096": small,
             "batched": batched,
+            "precision_2048": precision,
+            "learned": learned,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "systems/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)
-    seq.close()
     if dist:
         dist.destroy_process_group()
 

@@ -292,11 +292,48 @@ int seq_mlp_train(seq_mlp* mlp, const float* samples_dev, int32_t count, int32_t
 /* y_hat (B x M, device) for B samples (device, sample stride; only the
  * features part is read). */
 int seq_mlp_predict(seq_mlp* mlp, const float* samples_dev, int32_t B, float* y_dev);
-/* Attach (or detach with NULL) a predictor to a context. */
+/* Attach (or detach with NULL) a predictor to a context.  The caller keeps
+ * ownership of mlp; a predictor the context created itself (seq_learned_train
+ * or seq_learned_load) is freed when it is detached or replaced. */
 int seq_set_learned(seq_ctx* ctx, seq_mlp* mlp);
 /* Sample of the last seq_guess into sample_dev (device); SEQ_EINVAL if that
  * guess had no full history or fewer than four previous guesses. */
 int seq_last_sample(seq_ctx* ctx, float* sample_dev);
+
+/* Context-level entry points of the learned form.  Not in the paper (its
+ * Algorithm 1 solves for y by least squares at every step); they wrap the
+ * seq_mlp object above for the common case of one network per sequence.
+ *
+ * Train the context's predictor on `count` samples (device, the
+ * seq_last_sample layout, stride (4M+s) + M + M*M + 1 floats): if none is
+ * attached, the context creates and owns one (hidden width 256, He-uniform
+ * initialisation from `seed`); then the normalisation is fitted to the
+ * samples and `epochs` epochs of Adam run (learning rate 1e-3, batches of
+ * min(32, count) samples shuffled with `seed`).  Equivalent to seq_mlp_create
+ * (M, s, 256, 32, seed) + seq_mlp_fit_normalization + seq_mlp_train(epochs,
+ * 32, 1e-3, seed) on a fresh network, and the trained network is attached
+ * (seq_set_learned).  Synchronises.
+ * Errors: SEQ_EINVAL (count < 1, epochs < 0, NULL samples, M < 2),
+ * SEQ_ENOMEM, SEQ_ECUDA. */
+int seq_learned_train(seq_ctx* ctx, const float* dataset_dev, int32_t count, int32_t epochs,
+                      uint64_t seed);
+
+/* Serialised predictor: a 16-byte header of four int32 (0x4C514553, M, s,
+ * hidden width H), then the seq_mlp_get_params parameters and normalisation
+ * as FP32 (param_count + 2(4M+s) + M floats), host byte order.
+ * seq_learned_save writes the attached predictor into weights_host (bytes
+ * available) and the size it needs into *needed (may be NULL; weights_host
+ * NULL only queries the size).  SEQ_EINVAL without a predictor or when bytes
+ * is too small. */
+int seq_learned_save(seq_ctx* ctx, void* weights_host, size_t bytes, size_t* needed);
+
+/* Load a serialised predictor (the seq_learned_save layout) into the
+ * context: into the attached network when its M, s and H match the header,
+ * else into a new network owned by the context (the one it replaces is
+ * detached; an owned one is freed).  The Adam state starts from zero.
+ * Errors: SEQ_EINVAL (bad header, M or s different from the context's, size
+ * not matching the header), SEQ_ENOMEM, SEQ_ECUDA. */
+int seq_learned_load(seq_ctx* ctx, const void* weights_host, size_t bytes);
 
 /* ---- Batched form: many independent sequences, one persistent launch per step ----
  *

@@ -110,6 +110,11 @@ _SIGS = {
     "seq_mlp_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "seq_set_learned": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "seq_last_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "seq_learned_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_uint64]),
+    "seq_learned_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                        ctypes.POINTER(ctypes.c_size_t)]),
+    "seq_learned_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "seq_rand_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p]),
     "seq_pod_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -252,6 +257,26 @@ class Sequence:
     def set_learned(self, mlp) -> None:
         self._check(self._lib.seq_set_learned(self._h, mlp._h if mlp is not None else None))
         self._mlp = mlp
+
+    def learned_train(self, samples: torch.Tensor, epochs: int, seed: int) -> None:
+        """seq_learned_train on (count, stride) CUDA float32 samples."""
+        self._check(self._lib.seq_learned_train(self._h, _ptr(samples, torch.float32),
+                                                samples.shape[0], epochs, seed), allow=(0,))
+        self._mlp = None
+
+    def learned_save(self) -> bytes:
+        """seq_learned_save: the attached predictor serialised (host bytes)."""
+        need = ctypes.c_size_t()
+        self._check(self._lib.seq_learned_save(self._h, None, 0, ctypes.byref(need)), allow=(0,))
+        buf = ctypes.create_string_buffer(need.value)
+        self._check(self._lib.seq_learned_save(self._h, buf, need.value, ctypes.byref(need)),
+                    allow=(0,))
+        return buf.raw
+
+    def learned_load(self, blob: bytes) -> None:
+        """seq_learned_load from host bytes."""
+        self._check(self._lib.seq_learned_load(self._h, blob, len(blob)), allow=(0,))
+        self._mlp = None
 
     def last_sample(self, out: torch.Tensor) -> None:
         """Write the training sample of the last guess into out (CUDA float32)."""

@@ -64,6 +64,7 @@ struct seq_ctx {
     int yring_valid = 0;             // consecutive full-history guesses in the ring
     long long yring_pushes = -1;     // pushes at the newest ring entry
     seq_mlp* mlp = nullptr;          // learned predictor (SEQ_GUESS_LEARNED)
+    seq_mlp* mlp_owned = nullptr;    // predictor created by seq_learned_train / _load
     float* sample = nullptr;         // features / target of the last full guess
     float* yhat = nullptr;
     int* used_net = nullptr;
@@ -562,6 +563,7 @@ int seq_destroy(seq_ctx* ctx) {
     if (ctx->cg_graph) cudaGraphExecDestroy(ctx->cg_graph);
     if (ctx->cycle_prof) cudaGraphExecDestroy(ctx->cycle_prof);
     for (auto e : ctx->ev) cudaEventDestroy(e);
+    if (ctx->mlp_owned) seq_mlp_destroy(ctx->mlp_owned);
     void* dev_ptrs[] = {ctx->X, ctx->sk, ctx->sk_partial, ctx->W, ctx->lsq, ctx->kpartial,
                         ctx->V, ctx->w, ctx->r, ctx->p, ctx->q, ctx->val32, ctx->rhs32, ctx->d,
                         ctx->d_args, ctx->d_args_in, ctx->ks, ctx->ks_in, ctx->sell_width,
@@ -786,8 +788,88 @@ int seq_set_learned(seq_ctx* ctx, seq_mlp* mlp) {
     if (!ctx) return SEQ_EINVAL;
     if (mlp && !mlp_dims_ok(mlp, ctx->cfg.M, ctx->cfg.s))
         return fail(ctx, SEQ_EINVAL, "predictor dimensions differ from the context's M and s");
+    if (ctx->mlp_owned && ctx->mlp_owned != mlp) {     // a network the context made itself
+        seq_mlp_destroy(ctx->mlp_owned);
+        ctx->mlp_owned = nullptr;
+    }
     ctx->mlp = mlp;
     return SEQ_OK;
+}
+
+namespace {
+constexpr int32_t kLearnedMagic = 0x4C514553;
+constexpr int kLearnedHidden = 256;
+constexpr int kLearnedBatch = 32;
+
+// FP32 values in a serialised predictor of hidden width H (parameters, then
+// feature mean, feature std and output scale).
+size_t learned_floats(int M, int s, int H) {
+    const size_t in = 4 * (size_t)M + s;
+    const size_t np = (size_t)H * in + H + (size_t)H * H + H + (size_t)M * H + M;
+    return np + 2 * in + M;
+}
+}  // namespace
+
+int seq_learned_train(seq_ctx* ctx, const float* dataset_dev, int32_t count, int32_t epochs,
+                      uint64_t seed) {
+    if (!ctx) return SEQ_EINVAL;
+    ctx->err.clear();
+    if (!dataset_dev || count < 1 || epochs < 0 || ctx->cfg.M < 2)
+        return fail(ctx, SEQ_EINVAL, "seq_learned_train: bad argument (or M < 2)");
+    seq_mlp* m = ctx->mlp;
+    if (!m) {
+        int rc = seq_mlp_create(ctx->cfg.M, ctx->cfg.s, kLearnedHidden, kLearnedBatch, seed,
+                                ctx->stream, &m);
+        if (rc) return fail(ctx, rc, "seq_learned_train: cannot create the predictor");
+        ctx->mlp = ctx->mlp_owned = m;
+    }
+    int batch = count < kLearnedBatch ? count : kLearnedBatch;
+    if (batch > mlp_max_batch(m)) batch = mlp_max_batch(m);
+    int rc = seq_mlp_fit_normalization(m, dataset_dev, count);
+    if (rc) return fail(ctx, rc, "seq_learned_train: normalisation failed");
+    rc = seq_mlp_train(m, dataset_dev, count, epochs, batch, 1e-3f, seed, nullptr);
+    if (rc) return fail(ctx, rc, "seq_learned_train: training failed");
+    return SEQ_OK;
+}
+
+int seq_learned_save(seq_ctx* ctx, void* weights_host, size_t bytes, size_t* needed) {
+    if (!ctx) return SEQ_EINVAL;
+    if (!ctx->mlp) return fail(ctx, SEQ_EINVAL, "seq_learned_save: no predictor attached");
+    const int M = ctx->cfg.M, s = ctx->cfg.s, H = mlp_hidden(ctx->mlp);
+    const size_t need = 16 + sizeof(float) * learned_floats(M, s, H);
+    if (needed) *needed = need;
+    if (!weights_host) return SEQ_OK;
+    if (bytes < need) return fail(ctx, SEQ_EINVAL, "seq_learned_save: buffer too small");
+    int32_t hdr[4] = {kLearnedMagic, M, s, H};
+    memcpy(weights_host, hdr, sizeof(hdr));
+    float* body = reinterpret_cast<float*>(static_cast<char*>(weights_host) + 16);
+    const int np = seq_mlp_param_count(ctx->mlp);
+    int rc = seq_mlp_get_params(ctx->mlp, body, body + np);
+    return rc ? fail(ctx, rc, "seq_learned_save: cannot read the parameters") : SEQ_OK;
+}
+
+int seq_learned_load(seq_ctx* ctx, const void* weights_host, size_t bytes) {
+    if (!ctx) return SEQ_EINVAL;
+    ctx->err.clear();
+    if (!weights_host || bytes < 16) return fail(ctx, SEQ_EINVAL, "seq_learned_load: no header");
+    int32_t hdr[4];
+    memcpy(hdr, weights_host, sizeof(hdr));
+    const int M = ctx->cfg.M, s = ctx->cfg.s, H = hdr[3];
+    if (hdr[0] != kLearnedMagic || hdr[1] != M || hdr[2] != s || H < 1 || H > 4096)
+        return fail(ctx, SEQ_EINVAL, "seq_learned_load: header does not match the context");
+    if (bytes != 16 + sizeof(float) * learned_floats(M, s, H))
+        return fail(ctx, SEQ_EINVAL, "seq_learned_load: size does not match the header");
+    seq_mlp* m = ctx->mlp;
+    if (!m || mlp_hidden(m) != H) {
+        int rc = seq_mlp_create(M, s, H, kLearnedBatch, 0, ctx->stream, &m);
+        if (rc) return fail(ctx, rc, "seq_learned_load: cannot create the predictor");
+        if (ctx->mlp_owned) seq_mlp_destroy(ctx->mlp_owned);
+        ctx->mlp = ctx->mlp_owned = m;
+    }
+    const float* body = reinterpret_cast<const float*>(static_cast<const char*>(weights_host) + 16);
+    const int np = seq_mlp_param_count(m);
+    int rc = seq_mlp_set_params(m, body, body + np);
+    return rc ? fail(ctx, rc, "seq_learned_load: cannot write the parameters") : SEQ_OK;
 }
 
 int seq_last_sample(seq_ctx* ctx, float* sample_dev) {

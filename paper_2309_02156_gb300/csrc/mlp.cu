@@ -385,6 +385,8 @@ void mlp_predict_dev(seq_mlp* m, const float* features, int B, float* y, cudaStr
 }
 int mlp_stride(const seq_mlp* m) { return m->stride; }
 int mlp_dims_ok(const seq_mlp* m, int M, int s) { return m && m->M == M && m->s == s; }
+int mlp_hidden(const seq_mlp* m) { return m ? m->hid : 0; }
+int mlp_max_batch(const seq_mlp* m) { return m ? m->bmax : 0; }
 }  // namespace sa
 
 extern "C" {

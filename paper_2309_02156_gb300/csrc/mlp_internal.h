@@ -16,4 +16,6 @@ void launch_yring_push(double* yring, const LsqOut* lo, int M, cudaStream_t st);
 void mlp_predict_dev(seq_mlp* m, const float* features, int B, float* y, cudaStream_t st);
 int mlp_stride(const seq_mlp* m);
 int mlp_dims_ok(const seq_mlp* m, int M, int s);
+int mlp_hidden(const seq_mlp* m);
+int mlp_max_batch(const seq_mlp* m);
 }  // namespace sa

@@ -87,6 +87,14 @@ def test_reference_arm_prints_one_line_with_the_contract_keys():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": "systems/s",
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # Same workload description as the GPU arm; the timed sample is what
+    # steps and ms_per_step describe, the extrapolation is a field of its own.
+    assert line["config"] == bench.config_line(1)
+    ex = line["extrapolated"]
+    assert ex["timed_iterations_per_step"] == 30 and ex["iterations_per_system"] > 30
+    per = ex["guess_s"] + ex["iterations_per_system"] * ex["iteration_s"]
+    assert line["value"] == pytest.approx(1.0 / per, rel=1e-9)
+    assert 1e3 * (ex["guess_s"] + 30 * ex["iteration_s"]) <= 1.5 * line["ms_per_step"]
 
 
 def test_reference_arm_other_ranks_exit_quietly():

@@ -341,3 +341,61 @@ def test_learned_gain_over_least_squares():
     c_ls.close()
     c_net.close()
     net.close()
+
+
+def test_context_learned_train_save_load():
+    """seq_learned_train on a context without a predictor equals
+    seq_mlp_create(M, s, 256, 32, seed) + seq_mlp_fit_normalization +
+    seq_mlp_train(epochs, 32, 1e-3, seed), bit for bit; seq_learned_save and
+    seq_learned_load carry the trained network into a second context, whose
+    parameters and learned-mode guesses then equal the first's."""
+    sa = _sa()
+    Mq, s, count, epochs, seed = 6, 40, 80, 3, 0xA11CE
+    rng = np.random.default_rng(17)
+    samples = _tensor(_synthetic_samples(rng, Mq, s, count), torch.float32)
+    n = 64
+    ctx = sa.Sequence(n, Mq, s, zeta=8, seed=SEED, guess="learned")
+    ctx.learned_train(samples, epochs, seed)
+    blob = ctx.learned_save()
+    ref = sa.MLP(Mq, s, hidden=256, max_batch=32, seed=seed)
+    ref.fit_normalization(samples)
+    ref.train(samples, epochs=epochs, batch=32, lr=1e-3, seed=seed)
+    p_ref, n_ref = ref.get_params()
+    hdr = np.frombuffer(blob[:16], dtype=np.int32)
+    assert list(hdr) == [0x4C514553, Mq, s, 256]
+    body = np.frombuffer(blob[16:], dtype=np.float32)
+    assert body.size == p_ref.size + n_ref.size
+    assert np.array_equal(body[:p_ref.size], p_ref)          # bit for bit
+    assert np.array_equal(body[p_ref.size:], n_ref)
+    # Load into a second context and read it back.
+    ctx2 = sa.Sequence(n, Mq, s, zeta=8, seed=SEED, guess="learned")
+    ctx2.learned_load(blob)
+    assert ctx2.learned_save() == blob
+    # A header for another history length is rejected.
+    bad = bytearray(blob)
+    bad[4:8] = np.int32(Mq + 1).tobytes()
+    with pytest.raises(sa.SeqError) as e:
+        ctx2.learned_load(bytes(bad))
+    assert e.value.code == -1
+    with pytest.raises(sa.SeqError):
+        ctx2.learned_load(blob[:-4])
+    # Both contexts guess the same from the same history with the loaded net.
+    p = workloads.plain_nonsym(8)
+    guesses = []
+    for c in (ctx, ctx2):
+        hist_rng = np.random.default_rng(3)
+        outs = []
+        for i in range(Mq + 6):
+            rowptr, colind, vals, b = workloads.csr_system(p, i)
+            A = sa.CSR(_tensor(rowptr, torch.int32), _tensor(colind, torch.int32), _tensor(vals))
+            x = torch.empty(n, dtype=torch.float64, device=DEV)
+            g = c.guess(A, _tensor(b), x)
+            outs.append((x.cpu().numpy(), g["net_resid"]))
+            c.push(_tensor(hist_rng.standard_normal(n)))
+        guesses.append(outs)
+    for (x1, r1), (x2, r2) in zip(*guesses):
+        assert np.array_equal(x1, x2) and r1 == r2
+    assert any(r > 0 for _, r in guesses[0])                 # the network was consulted
+    ref.close()
+    ctx.close()
+    ctx2.close()

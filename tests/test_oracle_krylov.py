@@ -252,3 +252,17 @@ def test_preconditioned_gmres_arnoldi_relation_and_gain():
     assert np.linalg.norm(AMV - V @ Hbar) <= 1e-12 * np.linalg.norm(AMV)
     _, it0, _, st0 = krylov.gmres(A, b, np.zeros_like(b), 1e-10, 30, 20000)
     assert st0 == krylov.CONVERGED and it < it0
+
+
+def test_direct_solve_matches_dense_lu_and_refines():
+    """The reference solver equals dense LU on a small nonsymmetric system
+    (to kappa times rounding) and its refined residual sits at rounding level."""
+    A, b = _system(workloads.plain_nonsym(18), 5)
+    x_ref = np.linalg.solve(A.toarray(), b)
+    x, rel = krylov.direct_solve(A, b)
+    kappa = np.linalg.cond(A.toarray())
+    assert np.linalg.norm(x - x_ref) <= 1e-15 * kappa * np.linalg.norm(x_ref)
+    assert rel <= 1e-14 and rel == pytest.approx(
+        np.linalg.norm(b - A @ x) / np.linalg.norm(b), rel=1e-12)
+    x0, rel0 = krylov.direct_solve(A, b, refinements=0)
+    assert rel <= rel0 + 1e-16
