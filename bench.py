@@ -291,12 +291,13 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def profile_run(iters: int, precision: str = "f64", guess: str = "sketch") -> None:
+def profile_run(iters: int, precision: str = "f64", guess: str = "sketch", sweeps: int = 0) -> None:
     """A bounded full-size command for ncu: one guess (`guess` mode; m = 10 for
     POD / RAND) from a synthetic 20-column history and `iters` GMRES(30)
-    iterations (`precision`: f64, or mixed_krylov = FP32 inner iterations) on
-    system 23 of the 1024 x 1024 sequence, so that a profiler can capture every
-    launch of the run."""
+    iterations (`precision`: f64, or mixed_krylov = FP32 inner iterations;
+    `sweeps` > 0: right-preconditioned by that many Jacobi sweeps) on system 23
+    of the 1024 x 1024 sequence, so that a profiler can capture every launch of
+    the run."""
     import numpy as np
     import torch
     import paper_2309_02156_gb300 as sa
@@ -309,7 +310,8 @@ def profile_run(iters: int, precision: str = "f64", guess: str = "sketch") -> No
     bd = torch.from_numpy(b).to(dev)
     kw = {"basis_m": 10} if guess in ("pod", "rand") else {}
     seq = sa.Sequence(p.n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, krylov="gmres",
-                      restart=RESTART, max_iters=iters, precision=precision, guess=guess, **kw)
+                      restart=RESTART, max_iters=iters, precision=precision, guess=guess,
+                      precond_sweeps=sweeps, **kw)
     rng = np.random.default_rng(1)
     for _ in range(M_HIST):
         seq.push(torch.from_numpy(rng.standard_normal(p.n)).to(dev))
@@ -980,7 +982,7 @@ def precision_startup(hbm_peak):
         "all_converged": all(r["status"] == 0 for r in rows),
         "error_reference": ("oracle.krylov.direct_solve (sparse LU + FP64 refinement), "
                             "recorded by oracle/reference_solutions.py: err = sqrt(n/k sum "
-                            "(x - x_oracle)^2 over k = 4096 sampled entries) / ||x_oracle||")
+                            "(x - x_oracle)^2 over k = 1024 sampled entries) / ||x_oracle||")
         if ref else "no recorded reference solutions",
         "per_step": rows,
     }
@@ -1002,6 +1004,7 @@ def main():
     ap.add_argument("--profile-run", type=int, default=0, metavar="ITERS")
     ap.add_argument("--profile-precision", default="f64", choices=["f64", "mixed_krylov"])
     ap.add_argument("--profile-guess", default="sketch", choices=["sketch", "pod", "rand"])
+    ap.add_argument("--profile-sweeps", type=int, default=0)
     ap.add_argument("--batched-only", action="store_true")
     ap.add_argument("--batched-count", type=int, default=512)
     ap.add_argument("--precond-form", action="store_true")
@@ -1045,7 +1048,8 @@ def main():
         precond_form(args)
         return
     if args.profile_run:
-        profile_run(args.profile_run, args.profile_precision, args.profile_guess)
+        profile_run(args.profile_run, args.profile_precision, args.profile_guess,
+                    args.profile_sweeps)
         return
     if args.batched_only:
         import torch

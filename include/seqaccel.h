@@ -129,7 +129,7 @@ typedef struct {
 } seq_info;
 
 /* Create a context for one sequence (Section 2: one history X per sequence).
- * Allocates the history ring (n x M), the sketch (2 bytes x zeta x n), the
+ * Allocates the history ring (n x M), per-block partial sketched blocks, the
  * Krylov workspace (GMRES: n x (restart+1) basis) and small device state.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
  * Errors: SEQ_EINVAL (cfg out of range), SEQ_ENOMEM, SEQ_ECUDA.  *out is NULL
@@ -208,7 +208,8 @@ int seq_pod_state(seq_ctx* ctx, double* V_host, double* lam_host, int32_t* dims)
  * (n, s, zeta, seed): for column j, rows_dev[j*zeta + k] and signs_dev[j*zeta + k]
  * (+1/-1) in acceptance order (see the oracle's definition: candidates are
  * SplitMix64 outputs 256 j + c + 1, row = ((h >> 32) s) >> 32, sign = bit 0,
- * duplicates skipped).  Device pointers; stream-ordered; synchronises. */
+ * duplicates skipped).  1 <= zeta <= min(s, 16), s <= 128 (SEQ_EINVAL otherwise).
+ * Device pointers; stream-ordered; synchronises. */
 int seq_sketch_columns(int32_t n, int32_t s, int32_t zeta, uint64_t seed,
                        int32_t* rows_dev, int8_t* signs_dev, void* cuda_stream);
 

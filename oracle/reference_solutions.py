@@ -46,7 +46,7 @@ def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--N", type=int, default=2048)
     ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--samples", type=int, default=4096)
+    ap.add_argument("--samples", type=int, default=1024)
     ap.add_argument("--out", required=True)
     a = ap.parse_args()
     p = workloads.plain_nonsym(a.N)

@@ -28,8 +28,7 @@ struct seq_ctx {
     int ldx = 0;
     void* X = nullptr;               // history ring, n x ldx (double or float)
     int pushes = 0;
-    uint16_t* sk = nullptr;          // packed sketch, n x zeta
-    void* sk_partial = nullptr;
+    double* sk_partial = nullptr;    // per-block partial sketched blocks
     int sk_nblk = 0;
     double* W = nullptr;             // s*(M+1) + 1
     LsqOut* lsq = nullptr;
@@ -474,9 +473,8 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
     ok = ok && cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) == cudaSuccess;
     ok = ok && cudaMalloc(&ctx->X, elh * (size_t)n * ctx->ldx) == cudaSuccess;
     ok = ok && cudaMemsetAsync(ctx->X, 0, elh * (size_t)n * ctx->ldx, ctx->stream) == cudaSuccess;
-    ok = ok && cudaMalloc(&ctx->sk, sizeof(uint16_t) * (size_t)n * c.zeta) == cudaSuccess;
     ctx->sk_nblk = sketch_grid(n);
-    ok = ok && cudaMalloc(&ctx->sk_partial, elh * (size_t)ctx->sk_nblk * (s * (M + 1) + 1)) == cudaSuccess;
+    ok = ok && cudaMalloc(&ctx->sk_partial, sizeof(double) * sketch_partial_doubles(n, s, M)) == cudaSuccess;
     ok = ok && cudaMalloc(&ctx->W, sizeof(double) * (s * (M + 1) + 1)) == cudaSuccess;
     ok = ok && cudaMalloc(&ctx->lsq, sizeof(LsqOut)) == cudaSuccess;
     ok = ok && cudaMallocHost(&ctx->lsq_host, sizeof(LsqOut)) == cudaSuccess;
@@ -543,10 +541,7 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
     ok = ok && cudaMallocHost(&ctx->h_ks, sizeof(KState)) == cudaSuccess;
     ok = ok && cudaMemsetAsync(ctx->ks, 0, sizeof(KState), ctx->stream) == cudaSuccess;
     ok = ok && cudaMemsetAsync(ctx->ks_in, 0, sizeof(KState), ctx->stream) == cudaSuccess;
-    if (ok) {
-        launch_sketch_columns(n, s, c.zeta, c.seed, ctx->sk, nullptr, nullptr, ctx->stream);
-        ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(ctx->stream) == cudaSuccess;
-    }
+    if (ok) ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(ctx->stream) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         seq_destroy(ctx);
@@ -564,7 +559,7 @@ int seq_destroy(seq_ctx* ctx) {
     if (ctx->cycle_prof) cudaGraphExecDestroy(ctx->cycle_prof);
     for (auto e : ctx->ev) cudaEventDestroy(e);
     if (ctx->mlp_owned) seq_mlp_destroy(ctx->mlp_owned);
-    void* dev_ptrs[] = {ctx->X, ctx->sk, ctx->sk_partial, ctx->W, ctx->lsq, ctx->kpartial,
+    void* dev_ptrs[] = {ctx->X, ctx->sk_partial, ctx->W, ctx->lsq, ctx->kpartial,
                         ctx->V, ctx->w, ctx->r, ctx->p, ctx->q, ctx->val32, ctx->rhs32, ctx->d,
                         ctx->d_args, ctx->d_args_in, ctx->ks, ctx->ks_in, ctx->sell_width,
                         ctx->sell_off, ctx->sell_col, ctx->sell_val, ctx->yring, ctx->sample,
@@ -651,8 +646,8 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
         if (mode == SEQ_GUESS_POD) {
             // Algorithm 2 in snapshot form; the reduced problem from W = S[AX|b].
             const int kk = mb < m ? mb : m;
-            launch_sketch_f64(A->rowptr, A->colind, A->values, X, ctx->ldx, b_dev, ctx->sk, n,
-                              A->nnz, M, c.s, c.zeta, (double*)ctx->sk_partial, ctx->sk_nblk,
+            launch_sketch_f64(A->rowptr, A->colind, A->values, X, ctx->ldx, b_dev, n, A->nnz, M,
+                              c.s, c.zeta, c.seed, ctx->sk_partial, ctx->sk_nblk,
                               ctx->W, bad, ctx->stream);
             launch_pod_basis(X, ctx->ldx, n, M, m, oldest, kk, ctx->gpart, ctx->gcount, ctx->G,
                              ctx->Vk, ctx->lam, ctx->sweeps, ctx->stream);
@@ -675,8 +670,8 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
                 ctx->om_updates = 0;
                 ctx->launches += 2;
             }
-            launch_sketch_f64(A->rowptr, A->colind, A->values, ctx->Om, ctx->ldo, b_dev, ctx->sk,
-                              n, A->nnz, mb, c.s, c.zeta, (double*)ctx->sk_partial, ctx->sk_nblk,
+            launch_sketch_f64(A->rowptr, A->colind, A->values, ctx->Om, ctx->ldo, b_dev, n,
+                              A->nnz, mb, c.s, c.zeta, c.seed, ctx->sk_partial, ctx->sk_nblk,
                               ctx->W, bad, ctx->stream);
             launch_lsq(ctx->W, c.s, mb, mb, 0, c.rank_tol, ctx->lsq, ctx->stream);
             launch_expand_f64(ctx->Om, ctx->ldo, n, mb, ctx->lsq, x0_dev, ctx->stream);
@@ -695,11 +690,11 @@ int seq_guess(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double* x0_de
             if (rc) return rc;
             const float* v32 = A->values_f32 ? A->values_f32 : ctx->val32;
             launch_sketch_f32(A->rowptr, A->colind, v32, (const float*)ctx->X, ctx->ldx, b_dev,
-                              ctx->sk, n, A->nnz, M, c.s, c.zeta, (float*)ctx->sk_partial,
-                              ctx->sk_nblk, ctx->W, bad, ctx->stream);
+                              n, A->nnz, M, c.s, c.zeta, c.seed, ctx->sk_partial, ctx->sk_nblk,
+                              ctx->W, bad, ctx->stream);
         } else {
             launch_sketch_f64(A->rowptr, A->colind, A->values, (const double*)ctx->X, ctx->ldx,
-                              b_dev, ctx->sk, n, A->nnz, M, c.s, c.zeta, (double*)ctx->sk_partial,
+                              b_dev, n, A->nnz, M, c.s, c.zeta, c.seed, ctx->sk_partial,
                               ctx->sk_nblk, ctx->W, bad, ctx->stream);
         }
         const int oldest = (ctx->pushes - m) % M;
@@ -1087,7 +1082,7 @@ int seq_pod_state(seq_ctx* ctx, double* V_host, double* lam_host, int32_t* dims)
 
 int seq_sketch_columns(int32_t n, int32_t s, int32_t zeta, uint64_t seed, int32_t* rows_dev,
                        int8_t* signs_dev, void* cuda_stream) {
-    if (n <= 0 || s < 1 || s > 32767 || zeta < 1 || zeta > s || zeta > kMaxZeta || !rows_dev ||
+    if (n <= 0 || s < 1 || s > kMaxS || zeta < 1 || zeta > s || zeta > kMaxZeta || !rows_dev ||
         !signs_dev)
         return SEQ_EINVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;

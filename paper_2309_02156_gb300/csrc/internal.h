@@ -10,14 +10,19 @@ namespace sa {
 
 // sketch.cu
 int sketch_grid(int n);
+size_t sketch_partial_doubles(int n, int s, int M);   // partial buffer of launch_sketch_*
 void launch_sketch_columns(int n, int s, int zeta, uint64_t seed, uint16_t* packed,
                            int32_t* rows, int8_t* signs, cudaStream_t st);
+// W = S [A X | b] (s x (M+1), row-major, scaled by 1/sqrt(zeta)) with the sparse-sign S
+// of (n, s, zeta, seed) generated on the fly; partial: sketch_partial_doubles doubles.
 void launch_sketch_f64(const int* rowptr, const int* colind, const double* val, const double* X,
-                       int ldx, const double* b, const uint16_t* sk, int n, int nnz, int M, int s,
-                       int zeta, double* partial, int nblk, double* W, int* bad, cudaStream_t st);
+                       int ldx, const double* b, int n, int nnz, int M, int s, int zeta,
+                       uint64_t seed, double* partial, int nblk, double* W, int* bad,
+                       cudaStream_t st);
 void launch_sketch_f32(const int* rowptr, const int* colind, const float* val, const float* X,
-                       int ldx, const double* b, const uint16_t* sk, int n, int nnz, int M, int s,
-                       int zeta, float* partial, int nblk, double* W, int* bad, cudaStream_t st);
+                       int ldx, const double* b, int n, int nnz, int M, int s, int zeta,
+                       uint64_t seed, double* partial, int nblk, double* W, int* bad,
+                       cudaStream_t st);
 
 // lsq.cu
 struct LsqOut {

@@ -161,3 +161,49 @@ def test_full_size_batch_sampled_residuals():
         assert r <= 1e-8 * (1 + 1e-3)
         assert abs(r - infos[k]["final_relres"]) <= 1e-11
     bt.close()
+
+
+def test_full_size_batch_guess_parity():
+    """The 512-sequence workload at its real shape (grid sides 48..384, M = 12,
+    s = 48, zeta = 8, sketch seed + k per sequence): every history is primed
+    with 12 + 3 seeded Gaussian columns (the ring wraps), then one step.  For
+    the largest sequence (n = 147,456 at this seed), the smallest and every
+    64th, rank, sketched residual and guess residual match the oracle's
+    sketched guess from the same history (well-conditioned history: y is
+    determined to working precision)."""
+    import paper_2309_02156_gb300 as sa
+    from workloads.torch_pde import BatchedSystems
+    seed = 0x5EEDBA5E
+    ps = workloads.batched_params(512, seed)
+    gen = BatchedSystems(ps, torch.device(DEV))
+    pats = [(torch.from_numpy(rp).to(DEV), torch.from_numpy(ci).to(DEV)) for rp, ci in gen.patterns]
+    M, s = 12, 48
+    bt = sa.Batch(pats, M=M, s=s, zeta=8, seed=seed, max_iters=200000)
+    ns = np.array([p.n for p in ps])
+    sample = sorted({int(np.argmax(ns)), int(np.argmin(ns))} | set(range(0, 512, 64)))
+    hists = {}
+    for k, p in enumerate(ps):
+        rng = np.random.default_rng(1000 + k)
+        cols = [rng.standard_normal(p.n) for _ in range(M + 3)]
+        for c in cols:
+            bt.push(k, torch.from_numpy(c).to(DEV))
+        if k in sample:
+            hists[k] = np.stack(cols[-M:], axis=1)
+    i = 20
+    v, b = gen.values(i), gen.rhs(i)
+    torch.cuda.synchronize()
+    xs = [torch.empty(p.n, dtype=torch.float64, device=DEV) for p in ps]
+    infos = bt.step(gen.split(v, gen.nnz_off), gen.split(b, gen.n_off), xs, 1e-8)
+    assert all(f["status"] == 0 for f in infos)
+    assert ps[max(sample, key=lambda k: ps[k].n)].n == ns.max()
+    for k in sample:
+        rowptr, colind = gen.patterns[k]
+        A = krylov.csr(rowptr, colind, gen.split(v, gen.nnz_off)[k].cpu().numpy(), ps[k].n)
+        bk = gen.split(b, gen.n_off)[k].cpu().numpy()
+        S = sketch.sparse_sign_matrix(ps[k].n, s, 8, seed + k)
+        g = method.sketched_guess(A, bk, hists[k], S)
+        f = infos[k]
+        assert f["history_cols"] == M and f["rank"] == g.rank, k
+        assert f["sketch_resid"] == pytest.approx(g.rho_s, rel=1e-9), k
+        assert f["guess_relres"] == pytest.approx(method.relres(A, bk, g.x0), rel=1e-9), k
+    bt.close()

@@ -237,6 +237,56 @@ def test_full_size_nonsymmetric_workload():
     seq.close()
 
 
+@pytest.mark.parametrize("N", [20, 100, 256, 1024])
+def test_gmres_cycles_match_oracle_residual_by_residual(N):
+    """GMRES(5) from x0 = 0: the true residual after each of the first two
+    restart cycles equals the oracle's to 1e-9 (first cycle) and 1e-6 (second),
+    up to the full 1024 x 1024 operator.  Short cycles keep the computed
+    Krylov basis well determined, so the two implementations (different
+    summation orders, the same algorithm) agree to rounding; with 30-step
+    cycles on these operators the oracle's own residual after one cycle moves
+    by 1-3% when b is perturbed by 1e-15 (test below), which is why iteration
+    counts of GMRES(30) are compared statistically rather than one by one."""
+    p = workloads.plain_nonsym(N)
+    rowptr, colind, vals, b = workloads.csr_system(p, 0)
+    A = krylov.csr(rowptr, colind, vals, p.n)
+    Ad, bd = _dev_system(rowptr, colind, vals, b)
+    seq = _sa().Sequence(p.n, 20, 80, seed=0x5EEDBA5E, krylov="gmres", restart=5, max_iters=5)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    xo = np.zeros(p.n)
+    for cycle, tol in enumerate((1e-9, 1e-6)):
+        info = seq.solve(Ad, bd, 1e-30, x, allow=(1,))
+        xo, it, rel, st = krylov.gmres(A, b, xo, 1e-30, 5, 5)
+        assert info["iters"] == it == 5
+        assert info["final_relres"] == pytest.approx(rel, rel=tol), (cycle, info["final_relres"], rel)
+    seq.close()
+
+
+def test_gmres30_count_within_the_oracles_rounding_spread():
+    """GMRES(30) to 1e-8 on a 40 x 40 system: the oracle is run on b and on
+    seven copies of b perturbed by 1e-15 relative (a rounding-level change);
+    the GPU's iteration count lies inside the range of those eight counts,
+    widened by 5% + 2."""
+    p = workloads.plain_nonsym(40)
+    rowptr, colind, vals, b = workloads.csr_system(p, 3)
+    A = krylov.csr(rowptr, colind, vals, p.n)
+    rng = np.random.default_rng(0)
+    counts = []
+    for trial in range(8):
+        bb = b if trial == 0 else b * (1 + 1e-15 * rng.standard_normal(p.n))
+        _, it, rel, st = krylov.gmres(A, bb, np.zeros(p.n), 1e-8, 30, 100000)
+        assert st == krylov.CONVERGED
+        counts.append(it)
+    Ad, bd = _dev_system(rowptr, colind, vals, b)
+    seq = _sa().Sequence(p.n, 20, 80, seed=1, krylov="gmres", restart=30, max_iters=100000)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    info = seq.solve(Ad, bd, 1e-8, x)
+    assert info["status"] == 0
+    assert 0.95 * min(counts) - 2 <= info["iters"] <= 1.05 * max(counts) + 2, (info["iters"], counts)
+    assert method.relres(A, b, x.cpu().numpy()) <= 1e-8 * (1 + 1e-9)
+    seq.close()
+
+
 def test_edge_cases():
     sa = _sa()
     p = workloads.plain_nonsym(7)        # n = 49: one ragged warp tile
