@@ -57,8 +57,10 @@ struct seq_ctx {
     int* sell_col = nullptr;
     void* sell_val = nullptr;
     size_t sell_cap = 0;             // entries allocated
-    int* h_int = nullptr;            // pinned scratch word
+    int* h_int = nullptr;            // pinned scratch words (SELL total and widest slice)
     bool sell_ok = false;
+    int sell_w = 0;                  // uniform SELL slice width (0: slices differ)
+    int sell_keep = 0;               // SELL arrays small enough to keep in L2 (evict-last loads)
     double* yring = nullptr;         // last four coefficient vectors (newest first)
     int yring_valid = 0;             // consecutive full-history guesses in the ring
     long long yring_pushes = -1;     // pushes at the newest ring entry
@@ -152,6 +154,8 @@ int set_args(seq_ctx* ctx, const seq_csr* A, const double* b, double* x, double 
     h->sell_off = ctx->sell_ok ? ctx->sell_off : nullptr;
     h->sell_col = ctx->sell_ok ? ctx->sell_col : nullptr;
     h->sell_val = ctx->sell_ok ? ctx->sell_val : nullptr;
+    h->sell_w = ctx->sell_ok ? ctx->sell_w : 0;
+    h->sell_keep = ctx->sell_ok ? ctx->sell_keep : 0;
     h->n = A->n;
     h->nnz = A->nnz;
     h->max_iters = max_iters;
@@ -188,11 +192,23 @@ int build_sell(seq_ctx* ctx, const seq_csr* A) {
     const int n = A->n, ns = (n + 31) / 32;
     launch_sell_layout(A->rowptr, n, A->nnz, ctx->sell_width, ctx->sell_off, ctx->stream);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(ctx->h_int, ctx->sell_off + ns, sizeof(int), cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(ctx->h_int, ctx->sell_off + ns, 2 * sizeof(int), cudaMemcpyDeviceToHost,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    const long long total = *ctx->h_int;
+    long long total = ctx->h_int[0];
+    const long long wmax = ctx->h_int[1];
+    ctx->sell_w = 0;
     if (total <= 0 || total >= 0x7fffffffLL || total > 2LL * A->nnz + 64LL * ns) return SEQ_OK;
+    // When padding every slice to the widest costs at most 5% more storage,
+    // use one width: the products then compute slice offsets instead of
+    // loading them (one dependent load less per slice).
+    if (wmax > 0 && 32LL * ns * wmax <= total + total / 20 && 32LL * ns * wmax < 0x7fffffffLL) {
+        launch_sell_uniform(n, (int)wmax, ctx->sell_off, ctx->stream);
+        ctx->launches += 1;
+        total = 32LL * ns * wmax;
+        ctx->h_int[0] = (int)total;
+        ctx->sell_w = (int)wmax;
+    }
     const size_t el = ctx->mixed ? sizeof(float) : sizeof(double);
     if ((size_t)total > ctx->sell_cap) {
         if (ctx->sell_col) cudaFree(ctx->sell_col);
@@ -218,6 +234,12 @@ int build_sell(seq_ctx* ctx, const seq_csr* A) {
     ctx->launches += 3;
     CK(cudaGetLastError());
     ctx->sell_ok = true;
+    // Every Arnoldi step reads the matrix several times (the product and, when
+    // preconditioned, every sweep): keep it in L2 when it takes at most half.
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->dev);
+    const double sell_bytes = (4.0 + (double)el) * (double)total + 4.0 * (ns + 1);
+    ctx->sell_keep = l2 > 0 && sell_bytes <= 0.5 * (double)l2;
     return SEQ_OK;
 }
 
@@ -496,9 +518,9 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
     if (c.krylov == SEQ_GMRES || n >= kGridCgMinRows) {     // SELL-32 copy for the cycles
         const int ns = (n + 31) / 32;
         ok = ok && cudaMalloc(&ctx->sell_width, sizeof(int) * (size_t)ns) == cudaSuccess;
-        ok = ok && cudaMalloc(&ctx->sell_off, sizeof(int) * (size_t)(ns + 1)) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->sell_off, sizeof(int) * (size_t)(ns + 2)) == cudaSuccess;
     }
-    ok = ok && cudaMallocHost(&ctx->h_int, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&ctx->h_int, 2 * sizeof(int)) == cudaSuccess;
     {
         const int in = 4 * M + s, stride = in + M + M * M + 1;
         ok = ok && cudaMalloc(&ctx->yring, sizeof(double) * 4 * kMaxM) == cudaSuccess;

@@ -760,7 +760,7 @@ int seq_batch_create(int32_t count, const seq_csr* patterns, int32_t M, int32_t 
         rc = batch_alloc(bt, &p, sizeof(int) * (size_t)ns);
         if (rc) break;
         int* width = (int*)p;
-        rc = batch_alloc(bt, &p, sizeof(int) * (size_t)(ns + 1));
+        rc = batch_alloc(bt, &p, sizeof(int) * (size_t)(ns + 2));     // + total, widest slice
         if (rc) break;
         int* off = (int*)p;
         launch_sell_layout(q.rowptr, q.n, q.nnz, width, off, bt->stream);

@@ -22,10 +22,13 @@ struct CgProduct {                   // q[r] = (A p)[r], acc += p[r] (A p)[r]
     T* q;
     const T* p;
     T* acc;
-    __device__ void operator()(int r, T ax) const {
+    struct Pre { T p; };
+    __device__ Pre pre(int r) const { return {p[r]}; }
+    __device__ void operator()(int r, T ax, const Pre& o) const {
         q[r] = ax;
-        *acc = fma(p[r], ax, *acc);
+        *acc = fma(o.p, ax, *acc);
     }
+    __device__ void operator()(int r, T ax) const { (*this)(r, ax, pre(r)); }
 };
 
 template <typename T>
@@ -34,12 +37,15 @@ struct CgResidual {                  // r[i] = b[i] - (A x)[i] (and p = r), acc 
     T* p;
     const T* b;
     T* acc;
-    __device__ void operator()(int i, T ax) const {
-        const T ri = b[i] - ax;
+    struct Pre { T b; };
+    __device__ Pre pre(int i) const { return {b[i]}; }
+    __device__ void operator()(int i, T ax, const Pre& o) const {
+        const T ri = o.b - ax;
         r[i] = ri;
         if (p) p[i] = ri;
         *acc = fma(ri, ri, *acc);
     }
+    __device__ void operator()(int i, T ax) const { (*this)(i, ax, pre(i)); }
 };
 
 // Product over the block's rows [lo, hi): the SELL-32 copy when present,
@@ -52,7 +58,7 @@ __device__ __forceinline__ void cg_product(const DevArgs* __restrict__ a, KState
     const int n = a->n;
     if (a->sell_off) {
         sell_rows<T>(a->sell_off, a->sell_col, reinterpret_cast<const T*>(a->sell_val), x, n, lo,
-                     hi, kWarps, &ks->bad_index, epi);
+                     hi, kWarps, a->sell_w, a->sell_keep, &ks->bad_index, epi);
         return;
     }
     const T* val = Sys::val(a);

@@ -40,7 +40,9 @@ struct DevArgs {
     int n;
     int nnz;
     int max_iters;
-    int pad0;
+    int sell_w;         // every SELL slice has this width (offsets = 32 w s); 0: read them
+    int sell_keep;      // 1: load the SELL arrays with L2 evict-last priority (they fit in L2)
+    int pad1;
     double tol;         // relative tolerance of this solve
 };
 
@@ -70,6 +72,34 @@ struct KState {
     int pad1;
     unsigned counter[8];            // last-block counters, one per kernel kind
 };
+
+// Loads with an L2 eviction priority (createpolicy + ld.global.nc.L2::cache_hint):
+// evict_last keeps a matrix that is read again by the next kernels (the
+// sweeps and products of one Arnoldi step) resident in L2 while vectors
+// stream past it.
+__device__ __forceinline__ uint64_t l2_policy(bool keep) {
+    uint64_t p;
+    if (keep)
+        asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    else
+        asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ int ld_hint(const int* ptr, uint64_t pol) {
+    int v;
+    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ld_hint(const float* ptr, uint64_t pol) {
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_hint(const double* ptr, uint64_t pol) {
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

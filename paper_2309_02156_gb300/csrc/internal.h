@@ -126,7 +126,10 @@ void launch_cgg_true_residual_f64(const DevArgs* a, KState* ks, double* r, doubl
 void launch_cgg_true_residual_f32(const DevArgs* a, KState* ks, float* r, float* p,
                                   float* partial, int nblk, int check, cudaStream_t st);
 // CSR -> SELL-32 (slice widths and offsets, then the padded arrays).
+// off needs (n + 31) / 32 + 2 entries: off[ns] = total, off[ns + 1] = widest slice.
 void launch_sell_layout(const int* rowptr, int n, int nnz, int* width, int* off, cudaStream_t st);
+// Re-layout with every slice of width w (off[s] = 32 w s).
+void launch_sell_uniform(int n, int w, int* off, cudaStream_t st);
 void launch_sell_fill_f64(const int* rowptr, const int* colind, const double* val, int n, int nnz,
                           const int* off, int* col, double* v, cudaStream_t st);
 void launch_sell_fill_f32(const int* rowptr, const int* colind, const float* val, int n, int nnz,

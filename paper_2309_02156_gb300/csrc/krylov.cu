@@ -103,12 +103,18 @@ __global__ void sell_width_kernel(const int* __restrict__ rowptr, int n, int nnz
     if (lane == 0) width[s] = len;
 }
 
-// Exclusive scan of 32 * width over the slices by one block (off[ns] = total).
+// Exclusive scan of 32 * width over the slices by one block (off[ns] = total,
+// off[ns + 1] = the widest slice).
 __global__ void sell_scan_kernel(const int* __restrict__ width, int ns, int* off) {
     __shared__ long long wsum[32];
     __shared__ long long carry;
-    if (threadIdx.x == 0) carry = 0;
+    __shared__ int wmax;
+    if (threadIdx.x == 0) {
+        carry = 0;
+        wmax = 0;
+    }
     __syncthreads();
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) atomicMax(&wmax, width[s]);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int base = 0; base < ns; base += blockDim.x) {
         const int s = base + threadIdx.x;
@@ -133,7 +139,16 @@ __global__ void sell_scan_kernel(const int* __restrict__ width, int ns, int* off
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) off[ns] = (int)min(carry, (long long)0x7fffffff);
+    if (threadIdx.x == 0) {
+        off[ns] = (int)min(carry, (long long)0x7fffffff);
+        off[ns + 1] = wmax;
+    }
+}
+
+// Every slice padded to width w: off[s] = 32 w s for s <= ns.
+__global__ void sell_uniform_kernel(int ns, int w, int* off) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= ns; s += gridDim.x * blockDim.x)
+        off[s] = 32 * w * s;
 }
 
 template <typename VT>
@@ -163,6 +178,11 @@ void launch_sell_layout(const int* rowptr, int n, int nnz, int* width, int* off,
     const int ns = (n + 31) / 32;
     sell_width_kernel<<<(ns + 7) / 8, 256, 0, st>>>(rowptr, n, nnz, width);
     sell_scan_kernel<<<1, 1024, 0, st>>>(width, ns, off);
+}
+
+void launch_sell_uniform(int n, int w, int* off, cudaStream_t st) {
+    const int ns = (n + 31) / 32;
+    sell_uniform_kernel<<<(ns + 256) / 256, 256, 0, st>>>(ns, w, off);
 }
 
 void launch_sell_fill_f64(const int* rowptr, const int* colind, const double* val, int n, int nnz,

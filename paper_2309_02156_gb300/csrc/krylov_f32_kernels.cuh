@@ -136,7 +136,8 @@ f32_spmv_dot_kernel(const DevArgs* __restrict__ a, KState* ks, const float* __re
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
     if (a->sell_off) {
         sell_spmv_rows<float>(a->sell_off, a->sell_col, reinterpret_cast<const float*>(a->sell_val),
-                              vj, n, lo, hi, sig, w, kWarps, &ks->bad_index);
+                              vj, n, lo, hi, sig, w, kWarps, a->sell_w, a->sell_keep,
+                              &ks->bad_index);
     } else {                                      // no SELL copy: CSR, one row per thread
         const float* val = a->val32;
         int flag = 0;

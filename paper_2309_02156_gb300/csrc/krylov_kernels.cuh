@@ -173,12 +173,15 @@ constexpr int kSpmvWarps = kSpmvBlock / 32;
 
 // SELL-32 product: warp per 32-row slice (lane = row), the slice's entries
 // stored column-major and padded to its widest row (padding has column -1).
-// Two slices per warp and iteration: all index and value loads of both are
-// issued first (coalesced, independent), then all gathers, then each row is
-// summed in CSR order with exactly one fused multiply-add per stored entry
-// (the FMA chain is unrolled for the slice's exact width, so padding costs
-// no FP64 instruction).  Slices wider than kSellW use a plain loop.
-constexpr int kSellW = 6;
+// G slices per warp and iteration (3 in FP32, 2 in FP64): the slice offsets
+// (or, when every slice has the same width, offsets computed from the slice
+// index, with no load), then all index and value loads of the G slices and
+// the epilogue's own row operands (issued before the gathers, so they are in
+// flight together), then all gathers, then each row is summed in CSR order
+// with exactly one fused multiply-add per stored entry (the FMA chain is
+// unrolled for the slice's exact width, so padding costs no arithmetic).
+// Slices wider than kSellW use a plain loop.
+constexpr int kSellW = 5;
 
 template <typename T, int W>
 __device__ __forceinline__ T sell_dot(const T (&v)[kSellW], const T (&xv)[kSellW]) {
@@ -196,7 +199,6 @@ __device__ __forceinline__ T sell_dot_w(int w, const T (&v)[kSellW], const T (&x
         case 3: return sell_dot<T, 3>(v, xv);
         case 4: return sell_dot<T, 4>(v, xv);
         case 5: return sell_dot<T, 5>(v, xv);
-        case 6: return sell_dot<T, 6>(v, xv);
         default: return (T)0;
     }
 }
@@ -214,12 +216,18 @@ __device__ __forceinline__ T sell_row_loop(const int* __restrict__ col, const T*
     return a;
 }
 
-// Row results of a SELL product go through an epilogue epi(row, (A x)_row).
+// Row results of a SELL product go through an epilogue: pre(row) loads the
+// row operands the epilogue needs (issued early), epi(row, (A x)_row, pre)
+// writes the results.
+struct NoPre {};
+
 template <typename T>
 struct ScaleEpi {
     T* y;
     T scale;
-    __device__ void operator()(int r, T ax) const { y[r] = ax * scale; }
+    using Pre = NoPre;
+    __device__ Pre pre(int) const { return {}; }
+    __device__ void operator()(int r, T ax, const Pre&) const { y[r] = ax * scale; }
 };
 
 template <typename T, typename Epi>
@@ -227,49 +235,74 @@ __device__ __forceinline__ void sell_rows(const int* __restrict__ off,
                                           const int* __restrict__ col,
                                           const T* __restrict__ val,
                                           const T* __restrict__ x, int n, int lo, int hi,
-                                          int nwarps, int* bad, const Epi& epi) {
+                                          int nwarps, int ellw, int keep, int* bad,
+                                          const Epi& epi) {
     // An empty range (a trailing block when the grid covers more than n rows)
     // has no slice: lo = hi = n would otherwise map to the last partial slice
     // and repeat rows that another block owns.
     if (lo >= hi) return;
+    constexpr int G = sizeof(T) == 4 ? 3 : 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s_lo = lo >> 5, s_hi = (hi + 31) >> 5;
+    const uint64_t pol = l2_policy(keep != 0);
     int flag = 0;
-    for (int s = s_lo + warp; s < s_hi; s += 2 * nwarps) {
-        const int s2 = s + nwarps;
-        const bool two = s2 < s_hi;
-        const int o1 = __ldg(off + s), w1 = (__ldg(off + s + 1) - o1) >> 5;
-        const int o2 = two ? __ldg(off + s2) : 0;
-        const int w2 = two ? ((__ldg(off + s2 + 1) - o2) >> 5) : 0;
-        T a1, a2 = 0;
-        if (w1 <= kSellW && w2 <= kSellW) {
-            int c1[kSellW], c2[kSellW];
-            T v1[kSellW], v2[kSellW], x1[kSellW], x2[kSellW];
+    for (int s0 = s_lo + warp; s0 < s_hi; s0 += G * nwarps) {
+        int o[G], w[G], r[G];
+        bool row_ok[G];
+        typename Epi::Pre pre[G];
 #pragma unroll
-            for (int k = 0; k < kSellW; ++k) {
-                c1[k] = k < w1 ? __ldg(col + o1 + k * 32 + lane) : -1;
-                c2[k] = k < w2 ? __ldg(col + o2 + k * 32 + lane) : -1;
+        for (int g = 0; g < G; ++g) {
+            const int sl = s0 + g * nwarps;
+            const bool live = sl < s_hi;
+            r[g] = sl * 32 + lane;
+            row_ok[g] = live && r[g] < hi;
+            if (ellw > 0) {
+                o[g] = live ? sl * 32 * ellw : 0;
+                w[g] = live ? ellw : 0;
+            } else {
+                o[g] = live ? __ldg(off + sl) : 0;
+                w[g] = live ? (__ldg(off + sl + 1) - o[g]) >> 5 : 0;
             }
-#pragma unroll
-            for (int k = 0; k < kSellW; ++k) {
-                v1[k] = k < w1 ? __ldg(val + o1 + k * 32 + lane) : (T)0;
-                v2[k] = k < w2 ? __ldg(val + o2 + k * 32 + lane) : (T)0;
-            }
-#pragma unroll
-            for (int k = 0; k < kSellW; ++k) {
-                x1[k] = (unsigned)c1[k] < (unsigned)n ? x[c1[k]] : (T)0;
-                x2[k] = (unsigned)c2[k] < (unsigned)n ? x[c2[k]] : (T)0;
-                if (c1[k] >= n || c2[k] >= n) flag = 1;
-            }
-            a1 = sell_dot_w<T>(w1, v1, x1);
-            if (two) a2 = sell_dot_w<T>(w2, v2, x2);
-        } else {
-            a1 = sell_row_loop<T>(col, val, x, n, o1, w1, flag);
-            if (two) a2 = sell_row_loop<T>(col, val, x, n, o2, w2, flag);
         }
-        const int r1 = s * 32 + lane, r2 = s2 * 32 + lane;
-        if (r1 < hi) epi(r1, a1);
-        if (two && r2 < hi) epi(r2, a2);
+        bool fast = true;
+#pragma unroll
+        for (int g = 0; g < G; ++g) fast = fast && w[g] <= kSellW;
+        T ax[G];
+        if (fast) {
+            int c[G][kSellW];
+            T v[G][kSellW], xv[G][kSellW];
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int k = 0; k < kSellW; ++k)
+                    c[g][k] = k < w[g] ? ld_hint(col + o[g] + k * 32 + lane, pol) : -1;
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int k = 0; k < kSellW; ++k)
+                    v[g][k] = k < w[g] ? ld_hint(val + o[g] + k * 32 + lane, pol) : (T)0;
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                if (row_ok[g]) pre[g] = epi.pre(r[g]);
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int k = 0; k < kSellW; ++k) {
+                    xv[g][k] = (unsigned)c[g][k] < (unsigned)n ? x[c[g][k]] : (T)0;
+                    if (c[g][k] >= n) flag = 1;
+                }
+#pragma unroll
+            for (int g = 0; g < G; ++g) ax[g] = sell_dot_w<T>(w[g], v[g], xv[g]);
+        } else {
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                if (row_ok[g]) pre[g] = epi.pre(r[g]);
+                ax[g] = w[g] > 0 ? sell_row_loop<T>(col, val, x, n, o[g], w[g], flag) : (T)0;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (row_ok[g]) epi(r[g], ax[g], pre[g]);
     }
     if (flag) atomicOr(bad, 1);
 }
@@ -279,8 +312,9 @@ __device__ __forceinline__ void sell_spmv_rows(const int* __restrict__ off,
                                                const int* __restrict__ col,
                                                const T* __restrict__ val,
                                                const T* __restrict__ x, int n, int lo, int hi,
-                                               T scale, T* __restrict__ y, int nwarps, int* bad) {
-    sell_rows<T>(off, col, val, x, n, lo, hi, nwarps, bad, ScaleEpi<T>{y, scale});
+                                               T scale, T* __restrict__ y, int nwarps, int ellw,
+                                               int keep, int* bad) {
+    sell_rows<T>(off, col, val, x, n, lo, hi, nwarps, ellw, keep, bad, ScaleEpi<T>{y, scale});
 }
 
 template <class Sys>
@@ -303,7 +337,8 @@ arnoldi_spmv_kernel(const DevArgs* __restrict__ a, const KState* __restrict__ ks
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
     if (a->sell_off) {
         sell_spmv_rows<T>(a->sell_off, a->sell_col, reinterpret_cast<const T*>(a->sell_val), vj, n,
-                          lo, hi, sig, w, kSpmvWarps, const_cast<int*>(&ks->bad_index));
+                          lo, hi, sig, w, kSpmvWarps, a->sell_w, a->sell_keep,
+                          const_cast<int*>(&ks->bad_index));
         return;
     }
     const int step = kSpmvWarps * 32;

@@ -56,9 +56,12 @@ struct SweepEpi {
     const T* dinv;
     T sc, om;
     T* zout;
-    __device__ void operator()(int r, T ax) const {
-        zout[r] = zin[r] + (om * dinv[r]) * (sc * u[r] - ax);
+    struct Pre { T z, u, d; };
+    __device__ Pre pre(int r) const { return {zin[r], u[r], dinv[r]}; }
+    __device__ void operator()(int r, T ax, const Pre& o) const {
+        zout[r] = o.z + (om * o.d) * (sc * o.u - ax);
     }
+    __device__ void operator()(int r, T ax) const { (*this)(r, ax, pre(r)); }
 };
 
 // z_out = z_in + (omega dinv) (s u - A z_in).
@@ -77,7 +80,7 @@ precond_sweep_kernel(const DevArgs* __restrict__ a, KState* ks, const typename S
     const SweepEpi<T> epi{zin, u, dinv, sc, om, zout};
     if (a->sell_off) {
         sell_rows<T>(a->sell_off, a->sell_col, reinterpret_cast<const T*>(a->sell_val), zin, n, lo,
-                     hi, kSpmvWarps, &ks->bad_index, epi);
+                     hi, kSpmvWarps, a->sell_w, a->sell_keep, &ks->bad_index, epi);
         return;
     }
     const T* val = Sys::val(a);
