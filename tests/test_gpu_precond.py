@@ -146,3 +146,46 @@ def test_preconditioned_gmres_on_wide_rows(restart, d):
     assert abs(info["iters"] - it_ref) <= max(2, 0.03 * it_ref)
     assert method.relres(A_ref, b, x.cpu().numpy()) <= 1e-9 * (1 + 1e-9)
     seq.close()
+
+
+def _irregular(N, i, far):
+    """The N x N advection-diffusion matrix plus extra entries: every 7th row
+    gets one more entry (so SELL slices differ in width) and, with far, a
+    column more than 32767 away from its row.  The extra values are 1% of the
+    row's diagonal, which keeps the matrix diagonally dominant."""
+    import scipy.sparse as sp
+    p = workloads.plain_nonsym(N)
+    rowptr, colind, vals, b = workloads.csr_system(p, i)
+    A = krylov.csr(rowptr, colind, vals, p.n).tolil()
+    d = A.diagonal()
+    for r in range(0, p.n, 7):
+        c = (r * 13 + 5) % p.n
+        if far and r < p.n // 4:
+            c = p.n - 1 - (r % 17)
+        if c != r:
+            A[r, c] = A[r, c] + 0.01 * d[r]
+    A = sp.csr_matrix(A)
+    A.sort_indices()
+    return p, A, b
+
+
+@pytest.mark.parametrize("N,far", [(40, False), (190, True)])
+def test_preconditioned_gmres_on_irregular_rows(N, far):
+    """Right-preconditioned GMRES on a matrix whose SELL slices have different
+    widths (N = 40; with far, N = 190, n = 36,100, also columns more than 32767
+    from their row) and rows longer than the unrolled SELL path handles (the
+    products then take the plain loop).  Same parity as above."""
+    p, A_ref, b = _irregular(N, 2, far)
+    assert (np.abs(A_ref.tocoo().col - A_ref.tocoo().row).max() > 32767) == far
+    minv = krylov.jacobi_sweeps(A_ref, 4, 0.8)
+    x_ref, it_ref, rel_ref, st_ref = krylov.gmres(A_ref, b, np.zeros(p.n), 1e-9, 30, 50000, minv=minv)
+    A = _sa().CSR(_t(A_ref.indptr.astype(np.int32), torch.int32),
+                  _t(A_ref.indices.astype(np.int32), torch.int32), _t(A_ref.data))
+    seq = _sa().Sequence(p.n, 4, 16, krylov="gmres", restart=30, max_iters=50000,
+                         precond_sweeps=4)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    info = seq.solve(A, _t(b), 1e-9, x)
+    assert info["status"] == 0 and st_ref == 0
+    assert abs(info["iters"] - it_ref) <= max(2, 0.03 * it_ref)
+    assert method.relres(A_ref, b, x.cpu().numpy()) <= 1e-9 * (1 + 1e-9)
+    seq.close()
