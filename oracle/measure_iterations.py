@@ -15,8 +15,14 @@ per second.
 solution (the paper's baseline), each in its own sequence; the benchmark
 quotes the means over the systems with a full history beside its own.
 
+--workload spread: GMRES(30) from x0 = 0 on system 0 of the 1024 x 1024
+sequence to 1e-8, with b multiplied entrywise by 1 + 1e-15 g (g seeded
+standard normal, one seed per trial): how far the iteration count of
+restarted GMRES moves under a rounding-level change of its input.
+
     python -m oracle.measure_iterations --steps 26 --out tests/golden/oracle_iterations_nonsym1024.json
     python -m oracle.measure_iterations --workload spd --out tests/golden/oracle_iterations_spd64.json
+    python -m oracle.measure_iterations --workload spread --trial 1 --out spread_1.json  (trials 1..3)
 """
 from __future__ import annotations
 
@@ -61,9 +67,26 @@ def spd(out_path: str, N: int = 64, M: int = 10, s: int = 40, steps: int = 60,
         json.dump(doc, f, indent=1)
 
 
+def spread(out_path: str, trial: int, N: int = 1024) -> None:
+    p = workloads.plain_nonsym(N)
+    rowptr, colind, vals, b = workloads.csr_system(p, 0)
+    A = krylov.csr(rowptr, colind, vals, p.n)
+    g = np.random.default_rng(trial).standard_normal(p.n)
+    bb = b * (1 + 1e-15 * g) if trial else b
+    t0 = time.perf_counter()
+    _, it, rel, st = krylov.gmres(A, bb, np.zeros(p.n), 1e-8, 30, 60000)
+    doc = {"workload": f"nonsym {N}x{N} system 0, GMRES(30) from 0 to 1e-8, b (1 + 1e-15 g)",
+           "trial": trial, "iters": int(it), "relres": rel, "status": int(st),
+           "seconds": time.perf_counter() - t0, "host": platform.machine()}
+    print(json.dumps(doc), flush=True)
+    with open(out_path, "w") as f:
+        json.dump(doc, f, indent=1)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=("nonsym", "spd"), default="nonsym")
+    ap.add_argument("--workload", choices=("nonsym", "spd", "spread"), default="nonsym")
+    ap.add_argument("--trial", type=int, default=1)
     ap.add_argument("--N", type=int, default=1024)
     ap.add_argument("--M", type=int, default=20)
     ap.add_argument("--s", type=int, default=80)
@@ -72,6 +95,9 @@ def main() -> None:
     a = ap.parse_args()
     if a.workload == "spd":
         spd(a.out)
+        return
+    if a.workload == "spread":
+        spread(a.out, a.trial, a.N)
         return
     p = workloads.plain_nonsym(a.N)
     S = sketch.sparse_sign_matrix(p.n, a.s, 8, 0x5EEDBA5E)

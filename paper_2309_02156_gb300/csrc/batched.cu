@@ -337,37 +337,61 @@ constexpr int kBW = 5;      // 5-point stencils: every slice fits; wider rows ta
 template <typename Epi>
 __device__ __forceinline__ void bsell_spmv(const BatchSeq& q, const float* __restrict__ x, int nw,
                                            int* bad, Epi& epi) {
+    // Two slices per warp and iteration: both slices' index and value loads
+    // and the epilogue's row operand are in flight together, then the gathers.
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n = q.n;
     const int ns = (n + 31) >> 5;
     int flag = 0;
-    for (int sl = warp; sl < ns; sl += nw) {
-        const int o = q.soff[sl], w = (q.soff[sl + 1] - o) >> 5;
-        float a = 0.f;
-        if (w <= kBW) {
-            int c[kBW];
-            float v[kBW], xv[kBW];
+    for (int sl0 = warp; sl0 < ns; sl0 += 2 * nw) {
+        int o[2], w[2], r[2];
+        bool live[2];
 #pragma unroll
-            for (int k = 0; k < kBW; ++k) {
-                c[k] = k < w ? q.scol[o + k * 32 + lane] : -1;
-                v[k] = k < w ? q.sval[o + k * 32 + lane] : 0.f;
-            }
-#pragma unroll
-            for (int k = 0; k < kBW; ++k) {
-                xv[k] = (unsigned)c[k] < (unsigned)n ? x[c[k]] : 0.f;
-                flag |= c[k] >= n;
-            }
-#pragma unroll
-            for (int k = 0; k < kBW; ++k)
-                if (k < w) a = fmaf(v[k], xv[k], a);
-        } else {
-            for (int k = 0; k < w; ++k) {
-                const int cc = q.scol[o + k * 32 + lane];
-                if ((unsigned)cc < (unsigned)n) a = fmaf(q.sval[o + k * 32 + lane], x[cc], a);
-                else flag |= cc >= n;
-            }
+        for (int g = 0; g < 2; ++g) {
+            const int sl = sl0 + g * nw;
+            live[g] = sl < ns;
+            o[g] = live[g] ? q.soff[sl] : 0;
+            w[g] = live[g] ? (q.soff[sl + 1] - o[g]) >> 5 : 0;
+            r[g] = sl * 32 + lane;
         }
-        const int r = sl * 32 + lane;
-        if (r < n) epi(r, a);
+        float a[2] = {0.f, 0.f};
+        typename Epi::Pre pre[2];
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+            if (live[g] && r[g] < n) pre[g] = epi.pre(r[g]);
+        if (w[0] <= kBW && w[1] <= kBW) {
+            int c[2][kBW];
+            float v[2][kBW], xv[2][kBW];
+#pragma unroll
+            for (int g = 0; g < 2; ++g)
+#pragma unroll
+                for (int k = 0; k < kBW; ++k) {
+                    c[g][k] = k < w[g] ? q.scol[o[g] + k * 32 + lane] : -1;
+                    v[g][k] = k < w[g] ? q.sval[o[g] + k * 32 + lane] : 0.f;
+                }
+#pragma unroll
+            for (int g = 0; g < 2; ++g)
+#pragma unroll
+                for (int k = 0; k < kBW; ++k) {
+                    xv[g][k] = (unsigned)c[g][k] < (unsigned)n ? x[c[g][k]] : 0.f;
+                    flag |= c[g][k] >= n;
+                }
+#pragma unroll
+            for (int g = 0; g < 2; ++g)
+#pragma unroll
+                for (int k = 0; k < kBW; ++k)
+                    if (k < w[g]) a[g] = fmaf(v[g][k], xv[g][k], a[g]);
+        } else {
+#pragma unroll
+            for (int g = 0; g < 2; ++g)
+                for (int k = 0; k < w[g]; ++k) {
+                    const int cc = q.scol[o[g] + k * 32 + lane];
+                    if ((unsigned)cc < (unsigned)n) a[g] = fmaf(q.sval[o[g] + k * 32 + lane], x[cc], a[g]);
+                    else flag |= cc >= n;
+                }
+        }
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+            if (live[g] && r[g] < n) epi(r[g], a[g], pre[g]);
     }
     if (flag) atomicOr(bad, 1);
 }
@@ -376,9 +400,11 @@ struct CgProductEpi {
     float* qv;
     const float* p;
     float acc;
-    __device__ void operator()(int r, float a) {
+    using Pre = float;
+    __device__ float pre(int r) const { return p[r]; }
+    __device__ void operator()(int r, float a, float pr) {
         qv[r] = a;
-        acc = fmaf(p[r], a, acc);
+        acc = fmaf(pr, a, acc);
     }
 };
 
