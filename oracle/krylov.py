@@ -18,9 +18,11 @@ already meets the tolerance, Sections 4 and 5) can happen.  Conventions shared w
 * preconditioned GMRES (optional): right preconditioning, GMRES on A M^{-1}
   with x = x0 + M^{-1} V y, so the minimised residual is the true one and the
   stopping test is unchanged; M^{-1} = a fixed number of damped Jacobi sweeps
-  on A z = u from z = 0 (a polynomial in D^{-1} A times D^{-1}; Jacobi and
+  on A z = u from z = 0, or the Chebyshev polynomial of the same degree on an
+  interval [lmax / ratio, lmax] of the spectrum of D^{-1} A (lmax from
+  Gershgorin's theorem) -- polynomials in D^{-1} A times D^{-1}; Jacobi and
   polynomial preconditioners are the GPU-friendly members of the family the
-  paper's runs use, ILU and AMG, Sections 4-5);
+  paper's runs use, ILU and AMG, Sections 4-5;
 * mixed refinement: r = b - A64 x in FP64; the correction d solves
   A32 d = r (r rounded to float32; the same as solving for r / ||r|| and
   scaling back, in exact arithmetic) by the same solver run entirely in
@@ -108,6 +110,60 @@ def jacobi_sweeps(A, sweeps: int, omega: float):
         z = (om * dinv) * u
         for _ in range(sweeps - 1):
             z = z + (om * dinv) * (u - A @ z)
+        return z
+    return minv
+
+
+def gershgorin_bound(A) -> float:
+    """max_i (sum_j |a_ij|) / |a_ii| -- by Gershgorin's theorem every eigenvalue
+    of D^{-1} A lies in a disc of that radius about the origin, so it bounds the
+    spectrum from above.  Row sums in CSR order, FP64."""
+    A = scipy.sparse.csr_matrix(A)
+    absrow = np.add.reduceat(np.abs(A.data.astype(np.float64)), A.indptr[:-1]) \
+        if A.nnz else np.zeros(A.shape[0])
+    absrow[np.diff(A.indptr) == 0] = 0.0
+    d = np.abs(A.diagonal().astype(np.float64))
+    d[d == 0] = 1.0
+    return float(np.max(absrow / d))
+
+
+def chebyshev_sweeps(A, degree: int, lmin: float, lmax: float, dinv=None):
+    """M^{-1} u = p(D^{-1} A) D^{-1} u for the degree-`degree` polynomial whose
+    residual polynomial 1 - lam p(lam) is T_d((theta - lam) / delta) / T_d(theta /
+    delta) (theta, delta the centre and half-width of [lmin, lmax]): among
+    polynomials of that degree it has the smallest maximum of |1 - lam p(lam)|
+    on [lmin, lmax] (Chebyshev).  Applied by the three-term recurrence of the
+    Chebyshev iteration on A z = u from z = 0, with D^{-1} A as the operator:
+        sigma = theta / delta, rho_0 = 1 / sigma,
+        d_0 = D^{-1} u / theta, z_1 = d_0,
+        for k = 1 .. degree - 1:
+            r_k = u - A z_k,  rho_k = 1 / (2 sigma - rho_{k-1}),
+            d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / delta) D^{-1} r_k,
+            z_{k+1} = z_k + d_k.
+    That is degree applications of D^{-1} and degree - 1 products with A, the
+    cost of `degree` damped Jacobi sweeps.  `dinv` replaces 1 / diag(A) (tests
+    use it to evaluate the polynomial on a diagonal operator).  degree = 0:
+    identity."""
+    if degree <= 0:
+        return None
+    if dinv is None:
+        dinv = 1.0 / A.diagonal()
+    theta = 0.5 * (lmax + lmin)
+    delta = 0.5 * (lmax - lmin)
+    sigma = theta / delta
+
+    def minv(u):
+        dt = u.dtype.type
+        dv = dinv.astype(u.dtype, copy=False)
+        d = (dv * u) * dt(1.0 / theta)
+        z = d.copy()
+        rho_prev = 1.0 / sigma
+        for _ in range(degree - 1):
+            r = u - A @ z
+            rho = 1.0 / (2.0 * sigma - rho_prev)
+            d = dt(rho * rho_prev) * d + dt(2.0 * rho / delta) * (dv * r)
+            z = z + d
+            rho_prev = rho
         return z
     return minv
 
@@ -216,7 +272,8 @@ def mixed_refine(A64, A32, b, x, tol: float, inner: str, restart: int,
         if inner == "cg":
             d, it, _, st = cg(A32, rhs32, d0, itol, budget)
         else:
-            minv = jacobi_sweeps(A32, *precond) if precond else None
+            minv = (precond(A32) if callable(precond) else jacobi_sweeps(A32, *precond)) \
+                if precond else None
             d, it, _, st = gmres(A32, rhs32, d0, itol, restart, min(restart, budget), minv=minv)
         total += it
         refinements += 1

@@ -266,3 +266,103 @@ def test_direct_solve_matches_dense_lu_and_refines():
         np.linalg.norm(b - A @ x) / np.linalg.norm(b), rel=1e-12)
     x0, rel0 = krylov.direct_solve(A, b, refinements=0)
     assert rel <= rel0 + 1e-16
+
+
+# ---- Chebyshev polynomial preconditioner ----
+
+def _cheb_T(d, x):
+    """T_d(x) from its trigonometric / hyperbolic closed form."""
+    x = np.asarray(x, dtype=np.float64)
+    inside = np.abs(x) <= 1
+    out = np.empty_like(x)
+    out[inside] = np.cos(d * np.arccos(x[inside]))
+    xo = x[~inside]
+    out[~inside] = np.sign(xo) ** d * np.cosh(d * np.arccosh(np.abs(xo)))
+    return out
+
+
+@pytest.mark.parametrize("degree,lo,hi", [(1, 0.2, 1.8), (2, 0.05, 2.0), (5, 0.1, 1.9), (8, 0.02, 2.0)])
+def test_chebyshev_residual_polynomial_closed_form(degree, lo, hi):
+    """On a diagonal operator (D^{-1} taken as the identity) the residual
+    1 - lam p(lam) left by the recurrence equals T_d((theta - lam) / delta) /
+    T_d(theta / delta) at every eigenvalue, inside and outside [lo, hi]."""
+    lam = np.concatenate([np.linspace(lo, hi, 41), [0.5 * lo, 1.2 * hi]])
+    A = scipy.sparse.diags(lam).tocsr()
+    minv = krylov.chebyshev_sweeps(A, degree, lo, hi, dinv=np.ones(lam.size))
+    u = np.random.default_rng(degree).standard_normal(lam.size)
+    res = (u - A @ minv(u)) / u
+    theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    want = _cheb_T(degree, (theta - lam) / delta) / _cheb_T(degree, np.array(theta / delta))
+    assert np.all(np.abs(res - want) <= 1e-13 * np.maximum(1.0, np.abs(want)))
+
+
+@pytest.mark.parametrize("degree", [2, 4, 8])
+def test_chebyshev_is_the_minimax_polynomial_on_the_interval(degree):
+    """max over [lo, hi] of |1 - lam p(lam)| equals 1 / T_d(theta / delta), reached
+    with alternating signs at the d + 1 points theta - delta cos(j pi / d)
+    (equioscillation, hence optimal among degree-d polynomials with p's
+    residual equal to 1 at 0), and it beats the residual (1 - omega lam)^d of d
+    damped Jacobi sweeps for every omega."""
+    lo, hi = 0.05, 2.0
+    theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    grid = np.linspace(lo, hi, 4001)
+    A = scipy.sparse.diags(grid).tocsr()
+    minv = krylov.chebyshev_sweeps(A, degree, lo, hi, dinv=np.ones(grid.size))
+    u = np.ones(grid.size)
+    res = u - A @ minv(u)
+    bound = 1.0 / _cheb_T(degree, np.array(theta / delta))
+    assert np.abs(res).max() == pytest.approx(bound, rel=1e-9)
+    ext = theta - delta * np.cos(np.arange(degree + 1) * np.pi / degree)
+    Ae = scipy.sparse.diags(ext).tocsr()
+    me = krylov.chebyshev_sweeps(Ae, degree, lo, hi, dinv=np.ones(ext.size))
+    re = 1.0 - Ae @ me(np.ones(ext.size))
+    assert np.allclose(np.abs(re), bound, rtol=1e-9)
+    assert np.all(np.sign(re[1:]) == -np.sign(re[:-1]))
+    for omega in np.linspace(0.1, 1.9, 37):
+        assert np.abs((1 - omega * grid) ** degree).max() > bound
+
+
+def test_chebyshev_degree_one_is_scaled_jacobi():
+    A, b = _system(workloads.plain_nonsym(12), 3)
+    minv = krylov.chebyshev_sweeps(A, 1, 0.1, 1.9)
+    assert np.allclose(minv(b), b / A.diagonal() / 1.0, rtol=1e-15)
+
+
+def test_chebyshev_operator_equals_the_matrix_chebyshev_polynomial():
+    """On a real system: I - M^{-1} A equals T_d(X) / T_d(sigma) with
+    X = (theta I - D^{-1} A) / delta, T_d formed by the matrix recurrence
+    T_{k+1} = 2 X T_k - T_{k-1} in dense algebra (not the recurrence the
+    operator uses)."""
+    A, _ = _system(workloads.plain_nonsym(9), 2)
+    n = A.shape[0]
+    lo, hi, d = 0.1, 1.9, 6
+    minv = krylov.chebyshev_sweeps(A, d, lo, hi)
+    MA = np.column_stack([minv(A[:, j].toarray().ravel()) for j in range(n)])
+    theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    B = np.diag(1.0 / A.diagonal()) @ A.toarray()
+    X = (theta * np.eye(n) - B) / delta
+    T_prev, T_cur = np.eye(n), X.copy()
+    for _ in range(d - 1):
+        T_prev, T_cur = T_cur, 2 * X @ T_cur - T_prev
+    want = T_cur / _cheb_T(d, np.array(theta / delta))
+    assert np.abs((np.eye(n) - MA) - want).max() <= 1e-12
+
+
+def test_gershgorin_bound():
+    """The bound is the largest absolute row sum of D^{-1} A (dense algebra)
+    and every eigenvalue of D^{-1} A lies within it."""
+    A, _ = _system(workloads.plain_nonsym(15), 4)
+    B = np.diag(1.0 / A.diagonal()) @ A.toarray()
+    g = krylov.gershgorin_bound(A)
+    assert g == pytest.approx(np.abs(B).sum(axis=1).max(), rel=1e-14)
+    assert np.abs(np.linalg.eigvals(B)).max() <= g * (1 + 1e-12)
+
+
+def test_mixed_refinement_accepts_a_chebyshev_preconditioner():
+    A, b = _system(workloads.plain_nonsym(24), 3)
+    A32 = A.astype(np.float32)
+    lmax = krylov.gershgorin_bound(A32)
+    pc = lambda M: krylov.chebyshev_sweeps(M, 6, lmax / 30, lmax)
+    x, inner, nref, rel, st = krylov.mixed_refine(A, A32, b, np.zeros_like(b), 1e-10, "gmres", 30,
+                                                  20000, precond=pc)
+    assert st == krylov.CONVERGED and rel <= 1e-10
