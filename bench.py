@@ -1009,6 +1009,8 @@ def main():
     ap.add_argument("--batched-count", type=int, default=512)
     ap.add_argument("--precond-form", action="store_true")
     ap.add_argument("--precond-sweeps", type=int, default=4)
+    ap.add_argument("--precond-ratio", type=float, default=0.0,
+                    help="Chebyshev interval ratio lmax/lmin (0: the library default)")
     ap.add_argument("--e1", action="store_true")
     ap.add_argument("--e1-grid", type=int, default=100)
     ap.add_argument("--e1-steps", type=int, default=200)
@@ -1243,12 +1245,13 @@ def main():
     # form (FP64 history, sketch and guess, FP32 GMRES(30) inner solves inside
     # FP64 refinement) and right-preconditioned GMRES (damped Jacobi sweeps),
     # all to the same 1e-8 on the FP64 true residual.
-    def run_form(label, precision, sweeps):
+    def run_form(label, precision, sweeps, kind="jacobi"):
         nonlocal seq
         seq.close()
         seq = sa.Sequence(n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, krylov="gmres",
                           restart=RESTART, max_iters=60000, precision=precision,
-                          precond_sweeps=sweeps)
+                          precond_sweeps=sweeps, precond_kind=kind,
+                          precond_ratio=args.precond_ratio)
         for i in range(t_first):
             step(i)
         cms, cinfos = timed(timed_steps)
@@ -1282,14 +1285,24 @@ def main():
                                       "damped Jacobi sweeps, FP64 refinement to rel-res 1e-8",
                                       "mixed_krylov", 8),
         }
-        f64p = preconditioned["f64_jacobi4"]
-        mixp = preconditioned["mixed_jacobi8"]
-        f64p["vs_plain_f64"] = f64p["value"] / value
-        mixp["vs_plain_f64"] = mixp["value"] / value
-        mixp["vs_f64_jacobi4"] = mixp["value"] / f64p["value"]
+        preconditioned["f64_cheb4"] = run_form(
+            "FP64 GMRES(30) right-preconditioned by the degree-4 Chebyshev polynomial on "
+            "[lmax/%g, lmax] of D^-1 A (lmax: Gershgorin), rel-res 1e-8" % args.precond_ratio,
+            "f64", 4, "chebyshev")
+        preconditioned["mixed_cheb8"] = run_form(
+            "FP32 GMRES(30) inner solves right-preconditioned by the degree-8 Chebyshev "
+            "polynomial on [lmax/%g, lmax] of D^-1 A, FP64 refinement to rel-res 1e-8"
+            % args.precond_ratio, "mixed_krylov", 8, "chebyshev")
+        for k, f in preconditioned.items():
+            f["vs_plain_f64"] = f["value"] / value
+        preconditioned["mixed_jacobi8"]["vs_f64_jacobi4"] = (
+            preconditioned["mixed_jacobi8"]["value"] / preconditioned["f64_jacobi4"]["value"])
+        preconditioned["mixed_cheb8"]["vs_f64_cheb4"] = (
+            preconditioned["mixed_cheb8"]["value"] / preconditioned["f64_cheb4"]["value"])
         preconditioned["note"] = ("precision gain like for like: chosen.vs_plain_f64 (both "
-                                  "unpreconditioned) and mixed_jacobi8.vs_f64_jacobi4 (both "
-                                  "preconditioned, each with its best sweep count)")
+                                  "unpreconditioned), mixed_jacobi8.vs_f64_jacobi4 and "
+                                  "mixed_cheb8.vs_f64_cheb4 (both preconditioned, each with its "
+                                  "best degree)")
     seq.close()
 
     batched = None

@@ -111,6 +111,15 @@ typedef struct {
                              at most 32); the minimised and tested residual stays
                              the true one (x = x0 + M^{-1} V y)                   */
     double precond_omega; /* sweep weight omega in (0, 2); 0 selects 0.8          */
+    int32_t precond_kind; /* 0: the damped Jacobi sweeps above; 1: the Chebyshev
+                             polynomial of degree precond_sweeps on the interval
+                             [lmax / precond_ratio, lmax] of the spectrum of
+                             D^{-1} A (the minimax residual polynomial on it,
+                             applied by the Chebyshev iteration from z = 0: the
+                             cost of as many sweeps plus one vector)           */
+    double precond_ratio; /* Chebyshev: lmax / lmin > 1; 0 selects 30             */
+    double precond_lmax;  /* Chebyshev: lmax; 0: Gershgorin's bound
+                             max_i sum_j |a_ij| / |a_ii|, formed at every solve   */
 } seq_config;
 
 typedef struct {

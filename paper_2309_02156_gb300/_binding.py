@@ -39,7 +39,10 @@ class _Config(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("rank_tol", ctypes.c_double), ("basis_m", ctypes.c_int32),
                 ("refresh", ctypes.c_int32), ("precond_sweeps", ctypes.c_int32),
-                ("precond_omega", ctypes.c_double)]
+                ("precond_omega", ctypes.c_double), ("precond_kind", ctypes.c_int32),
+                ("precond_ratio", ctypes.c_double), ("precond_lmax", ctypes.c_double)]
+
+PRECOND = {"jacobi": 0, "chebyshev": 1}
 
 
 class SeqInfo(ctypes.Structure):
@@ -190,11 +193,14 @@ class Sequence:
                  precision: str = "f64", guess: str = "sketch", krylov: str = "gmres",
                  restart: int = 30, max_iters: int = 30000, inner_tol: float = 0.0,
                  rank_tol: float = 0.0, basis_m: int = 0, refresh: int = 0,
-                 precond_sweeps: int = 0, precond_omega: float = 0.0):
+                 precond_sweeps: int = 0, precond_omega: float = 0.0,
+                 precond_kind: str = "jacobi", precond_ratio: float = 0.0,
+                 precond_lmax: float = 0.0):
         self._lib = load()
         cfg = _Config(n, M, s, zeta, seed, PRECISION[precision], GUESS[guess], KRYLOV[krylov],
                       restart, max_iters, inner_tol, rank_tol, basis_m, refresh,
-                      precond_sweeps, precond_omega)
+                      precond_sweeps, precond_omega, PRECOND[precond_kind], precond_ratio,
+                      precond_lmax)
         h = ctypes.c_void_p()
         rc = self._lib.seq_create(ctypes.byref(cfg), ctypes.c_void_p(_stream()), ctypes.byref(h))
         if rc != 0:

@@ -91,6 +91,8 @@ struct seq_ctx {
     void* za = nullptr;
     void* zb = nullptr;
     void* tprec = nullptr;
+    void* pc_d = nullptr;            // Chebyshev recurrence vector
+    unsigned long long* pc_bound = nullptr;   // Gershgorin bound of D^{-1} A (bits of a double)
     cudaGraphExec_t cycle = nullptr;
     cudaGraphExec_t cg_graph = nullptr;     // grid-wide CG iterations (large systems)
     cudaGraphExec_t cycle_prof = nullptr;   // same cycle with timing events between kernels
@@ -259,18 +261,21 @@ int capture_cycle(seq_ctx* ctx, bool prof) {
         }
         ev = ctx->ev.data();
     }
+    const ChebConfig cheb{ctx->cfg.precond_kind == 1, ctx->cfg.precond_lmax, ctx->cfg.precond_ratio,
+                          ctx->pc_bound};
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
     if (!ctx->mixed)
         launch_gmres_cycle_f64(ctx->d_args, ctx->ks, (double*)ctx->V, ctx->ldv, (double*)ctx->w,
                                ctx->kpartial, ctx->nblk, R, ctx->cap, &ctx->cycle_launches, ev, sw,
                                om, (const double*)ctx->dinv, (double*)ctx->za, (double*)ctx->zb,
-                               (double*)ctx->tprec);
+                               (double*)ctx->tprec, &cheb, (double*)ctx->pc_d);
     else
         launch_gmres_cycle_f32(ctx->d_args_in, ctx->ks_in, (float*)ctx->V, ctx->ldv,
                                (float*)ctx->w, (float*)ctx->kpartial, ctx->nblk, R, ctx->cap,
                                &ctx->cycle_launches, ev, sw, om, (const float*)ctx->dinv,
-                               (float*)ctx->za, (float*)ctx->zb, (float*)ctx->tprec);
+                               (float*)ctx->za, (float*)ctx->zb, (float*)ctx->tprec, &cheb,
+                               (float*)ctx->pc_d);
     CK(cudaStreamEndCapture(ctx->cap, &g));
     cudaError_t e = cudaGraphInstantiate(exec, g, 0);
     cudaGraphDestroy(g);
@@ -306,11 +311,14 @@ void account_cycle(seq_ctx* ctx, bool f32, int jd, bool updated, int nnz) {
     const int sw = ctx->cfg.precond_sweeps;
     const int S = step_kernels(f32) + sw;
     // Preconditioner: the scale reads u, dinv and writes z; a sweep reads the
-    // matrix, z (gathered), u, dinv and writes the next z.
+    // matrix, z (gathered), u, dinv and writes the next z.  Chebyshev also
+    // writes d at the scale and reads and writes it at every sweep.
+    const double cv = ctx->cfg.precond_kind == 1 ? 1.0 : 0.0;
     auto precond = [&](int ev0) {
-        add_stat(ctx, SEQ_K_PRECOND, ev0, 3.0 * E * n, 2.0 * n);
+        add_stat(ctx, SEQ_K_PRECOND, ev0, (3.0 + cv) * E * n, 2.0 * n);
         for (int k = 1; k < sw; ++k)
-            add_stat(ctx, SEQ_K_PRECOND, ev0 + k, spmv_mat + 4.0 * E * n, 2.0 * nnz + 4.0 * n);
+            add_stat(ctx, SEQ_K_PRECOND, ev0 + k, spmv_mat + (4.0 + 2.0 * cv) * E * n,
+                     2.0 * nnz + (4.0 + 3.0 * cv) * n);
     };
     for (int j = 0; j < jd; ++j) {
         const double nk = j + 1;
@@ -475,7 +483,9 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
     if (compressed && (c.basis_m < 1 || c.basis_m > c.M || c.refresh < 0 || c.precision == SEQ_MIXED))
         return SEQ_EINVAL;
     if (c.precond_sweeps < 0 || c.precond_sweeps > 32 || c.precond_omega < 0.0 ||
-        c.precond_omega >= 2.0 || (c.precond_sweeps > 0 && c.krylov != SEQ_GMRES))
+        c.precond_omega >= 2.0 || (c.precond_sweeps > 0 && c.krylov != SEQ_GMRES) ||
+        c.precond_kind < 0 || c.precond_kind > 1 || !(c.precond_ratio == 0.0 || c.precond_ratio > 1.0) ||
+        !(c.precond_lmax >= 0.0))
         return SEQ_EINVAL;
     seq_ctx* ctx = new seq_ctx();
     memset(ctx->stats, 0, sizeof(ctx->stats));
@@ -484,6 +494,7 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
     if (ctx->cfg.rank_tol <= 0) ctx->cfg.rank_tol = c.precision == SEQ_MIXED ? 1e-5 : 1e-12;
     if (ctx->cfg.refresh <= 0) ctx->cfg.refresh = 50;
     if (ctx->cfg.precond_omega <= 0.0) ctx->cfg.precond_omega = 0.8;
+    if (ctx->cfg.precond_ratio <= 0.0) ctx->cfg.precond_ratio = 30.0;
     ctx->mixed = c.precision != SEQ_F64;
     ctx->hist32 = c.precision == SEQ_MIXED;
     ctx->stream = (cudaStream_t)cuda_stream;
@@ -535,6 +546,9 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
         ok = ok && cudaMalloc(&ctx->za, el * (size_t)n) == cudaSuccess;
         ok = ok && cudaMalloc(&ctx->zb, el * (size_t)n) == cudaSuccess;
         ok = ok && cudaMalloc(&ctx->tprec, el * (size_t)n) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->pc_bound, sizeof(unsigned long long)) == cudaSuccess;
+        if (c.precond_kind == 1)
+            ok = ok && cudaMalloc(&ctx->pc_d, el * (size_t)n) == cudaSuccess;
     }
     if (c.guess == SEQ_GUESS_RAND) {
         ctx->ldo = round_up(c.basis_m, 4);
@@ -587,7 +601,7 @@ int seq_destroy(seq_ctx* ctx) {
                         ctx->sell_off, ctx->sell_col, ctx->sell_val, ctx->yring, ctx->sample,
                         ctx->yhat, ctx->used_net, ctx->Om, ctx->Zs, ctx->gpart, ctx->gcount,
                         ctx->G, ctx->Vk, ctx->lam, ctx->sweeps, ctx->Wp, ctx->lsq_red,
-                        ctx->dinv, ctx->za, ctx->zb, ctx->tprec};
+                        ctx->dinv, ctx->za, ctx->zb, ctx->tprec, ctx->pc_d, ctx->pc_bound};
     for (void* p : dev_ptrs)
         if (p) cudaFree(p);
     void* host_ptrs[] = {ctx->lsq_host, ctx->h_args, ctx->h_args_in, ctx->h_ks, ctx->h_int,
@@ -925,10 +939,11 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
     rc = set_args(ctx, A, b_dev, x_dev, tol, c.max_iters);
     if (rc) return rc;
     if (c.precond_sweeps > 0) {
+        CK(cudaMemsetAsync(ctx->pc_bound, 0, sizeof(unsigned long long), ctx->stream));
         if (!ctx->mixed)
-            launch_diag_inv_f64(ctx->d_args, (double*)ctx->dinv, c.n, ctx->stream);
+            launch_diag_inv_f64(ctx->d_args, (double*)ctx->dinv, c.n, ctx->stream, ctx->pc_bound);
         else
-            launch_diag_inv_f32(ctx->d_args_in, (float*)ctx->dinv, c.n, ctx->stream);
+            launch_diag_inv_f32(ctx->d_args_in, (float*)ctx->dinv, c.n, ctx->stream, ctx->pc_bound);
         ctx->launches += 1;
         CK(cudaGetLastError());
     }

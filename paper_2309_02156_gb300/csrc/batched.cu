@@ -437,11 +437,14 @@ __device__ int block_cg32(const BatchSeq& q, double itol, int max_iters, float* 
         rr_l = fmaf(ri, ri, rr_l);
     }
     float rr = btotal(rr_l, sred);
-    const double target = itol * sqrt((double)rr);
+    // The stopping test ||r|| <= itol ||rhs|| on squares in FP32 (an FP64
+    // square root per thread and iteration would cost microseconds of the
+    // FP64 pipe on this GPU).
+    const float target2 = (float)(itol * itol * (double)rr);
     int it = 0;
     status = kOk;
     if (!(rr > 0.f)) return 0;
-    while (sqrt((double)rr) > target) {
+    while (rr > target2) {
         if (it >= max_iters) {
             status = 1;
             break;

@@ -22,6 +22,7 @@ struct CgProduct {                   // q[r] = (A p)[r], acc += p[r] (A p)[r]
     T* q;
     const T* p;
     T* acc;
+    static constexpr int kSlices = 0;
     struct Pre { T p; };
     __device__ Pre pre(int r) const { return {p[r]}; }
     __device__ void operator()(int r, T ax, const Pre& o) const {
@@ -37,6 +38,7 @@ struct CgResidual {                  // r[i] = b[i] - (A x)[i] (and p = r), acc 
     T* p;
     const T* b;
     T* acc;
+    static constexpr int kSlices = 0;
     struct Pre { T b; };
     __device__ Pre pre(int i) const { return {b[i]}; }
     __device__ void operator()(int i, T ax, const Pre& o) const {

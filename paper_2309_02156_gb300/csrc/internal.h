@@ -80,13 +80,26 @@ void launch_residual_norm(const DevArgs* a, KState* ks, double* partial, int nbl
 void launch_gmres_start_f64(const DevArgs* a, KState* ks, double* V, size_t ldv, double* partial,
                             int nblk, int first, cudaStream_t st);
 // Right preconditioning (sweeps > 0): M^{-1} = `sweeps` damped Jacobi sweeps
-// with weight omega and dinv = 1 / diag(A); za, zb, t: n-vectors of scratch.
+// with weight omega and dinv = 1 / diag(A), or (cheb->on) the Chebyshev
+// polynomial of degree `sweeps` on [lmax / ratio, lmax] of D^{-1} A (lmax =
+// cheb->lmax, or the Gershgorin bound the dinv kernel leaves in *cheb->bound);
+// za, zb, t, dvec: n-vectors of scratch.
+struct ChebConfig {
+    int on;
+    double lmax;                          // 0: the Gershgorin bound
+    double ratio;                         // lmax / lmin
+    const unsigned long long* bound;      // written by launch_diag_inv_*
+};
 void launch_gmres_cycle_f64(const DevArgs* a, KState* ks, double* V, size_t ldv, double* w,
                             double* partial, int nblk, int R, cudaStream_t st, int* launches,
                             cudaEvent_t* ev = nullptr, int sweeps = 0, double omega = 1.0,
                             const double* dinv = nullptr, double* za = nullptr,
-                            double* zb = nullptr, double* t = nullptr);
-void launch_diag_inv_f64(const DevArgs* a, double* dinv, int n, cudaStream_t st);
+                            double* zb = nullptr, double* t = nullptr,
+                            const ChebConfig* cheb = nullptr, double* dvec = nullptr);
+// dinv = 1 / diag(A); with bound (zeroed by the caller) also the Gershgorin
+// bound max_i sum_j |a_ij| / |a_ii| as the bits of a double.
+void launch_diag_inv_f64(const DevArgs* a, double* dinv, int n, cudaStream_t st,
+                         unsigned long long* bound = nullptr);
 // Same on the FP32 inner system A32 d = rhs32 (mixed precision).
 void launch_gmres_start_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, float* partial,
                             int nblk, int first, cudaStream_t st);
@@ -94,8 +107,10 @@ void launch_gmres_cycle_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, 
                             float* partial, int nblk, int R, cudaStream_t st, int* launches,
                             cudaEvent_t* ev = nullptr, int sweeps = 0, double omega = 1.0,
                             const float* dinv = nullptr, float* za = nullptr,
-                            float* zb = nullptr, float* t = nullptr);
-void launch_diag_inv_f32(const DevArgs* a, float* dinv, int n, cudaStream_t st);
+                            float* zb = nullptr, float* t = nullptr,
+                            const ChebConfig* cheb = nullptr, float* dvec = nullptr);
+void launch_diag_inv_f32(const DevArgs* a, float* dinv, int n, cudaStream_t st,
+                         unsigned long long* bound = nullptr);
 // Mixed precision outer step: x += scale * d (FP64 += FP32), then the FP64
 // residual r = b - A64 x, its norm, and rhs32 = r / ||r||.
 void launch_refine_residual(const DevArgs* a, KState* ks, float* rhs32, double* partial, int nblk,

@@ -66,7 +66,7 @@ void launch_gmres_start_f64(const DevArgs* a, KState* ks, double* V, size_t, dou
 void launch_gmres_cycle_f64(const DevArgs* a, KState* ks, double* V, size_t ldv, double* w,
                             double* partial, int nblk, int R, cudaStream_t st, int* launches,
                             cudaEvent_t* ev, int sweeps, double omega, const double* dinv,
-                            double* za, double* zb, double* t) {
+                            double* za, double* zb, double* t, const ChebConfig* cheb, double* dvec) {
     PrecondArgs<double> pc;
     pc.sweeps = sweeps;
     pc.omega = omega;
@@ -74,12 +74,20 @@ void launch_gmres_cycle_f64(const DevArgs* a, KState* ks, double* V, size_t ldv,
     pc.za = za;
     pc.zb = zb;
     pc.t = t;
+    if (cheb && cheb->on) {
+        pc.cheb = 1;
+        pc.bound = cheb->bound;
+        pc.lfix = cheb->lmax;
+        pc.ratio = cheb->ratio;
+        pc.dvec = dvec;
+    }
     launch_cycle<SysF64>(a, ks, V, ldv, w, partial, nblk, R, st, launches, ev, pc);
 }
-void launch_diag_inv_f64(const DevArgs* a, double* dinv, int n, cudaStream_t st) {
+void launch_diag_inv_f64(const DevArgs* a, double* dinv, int n, cudaStream_t st,
+                         unsigned long long* bound) {
     int b = (n + 255) / 256;
     if (b > 152 * 8) b = 152 * 8;
-    diag_inv_kernel<SysF64><<<b > 0 ? b : 1, 256, 0, st>>>(a, dinv);
+    diag_inv_kernel<SysF64><<<b > 0 ? b : 1, 256, 0, st>>>(a, dinv, bound);
 }
 // ---------------------------------------------------------------------------
 // CSR -> SELL-32 conversion (once per solve; the GMRES cycles then run ~10^3

@@ -11,7 +11,7 @@ void launch_gmres_start_f32(const DevArgs* a, KState* ks, float* V, size_t, floa
 void launch_gmres_cycle_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, float* w,
                             float* partial, int nblk, int R, cudaStream_t st, int* launches,
                             cudaEvent_t* ev, int sweeps, double omega, const float* dinv,
-                            float* za, float* zb, float* t) {
+                            float* za, float* zb, float* t, const ChebConfig* cheb, float* dvec) {
     PrecondArgs<float> pc;
     pc.sweeps = sweeps;
     pc.omega = omega;
@@ -19,12 +19,20 @@ void launch_gmres_cycle_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, 
     pc.za = za;
     pc.zb = zb;
     pc.t = t;
+    if (cheb && cheb->on) {
+        pc.cheb = 1;
+        pc.bound = cheb->bound;
+        pc.lfix = cheb->lmax;
+        pc.ratio = cheb->ratio;
+        pc.dvec = dvec;
+    }
     launch_cycle<SysF32>(a, ks, V, ldv, w, partial, nblk, R, st, launches, ev, pc);
 }
-void launch_diag_inv_f32(const DevArgs* a, float* dinv, int n, cudaStream_t st) {
+void launch_diag_inv_f32(const DevArgs* a, float* dinv, int n, cudaStream_t st,
+                         unsigned long long* bound) {
     int b = (n + 255) / 256;
     if (b > 152 * 8) b = 152 * 8;
-    diag_inv_kernel<SysF32><<<b > 0 ? b : 1, 256, 0, st>>>(a, dinv);
+    diag_inv_kernel<SysF32><<<b > 0 ? b : 1, 256, 0, st>>>(a, dinv, bound);
 }
 
 }  // namespace sa

@@ -218,13 +218,15 @@ __device__ __forceinline__ T sell_row_loop(const int* __restrict__ col, const T*
 
 // Row results of a SELL product go through an epilogue: pre(row) loads the
 // row operands the epilogue needs (issued early), epi(row, (A x)_row, pre)
-// writes the results.
+// writes the results; kSlices > 0 overrides the slices per warp and
+// iteration (epilogues with many row operands take fewer).
 struct NoPre {};
 
 template <typename T>
 struct ScaleEpi {
     T* y;
     T scale;
+    static constexpr int kSlices = 0;    // slices per warp and iteration: the default
     using Pre = NoPre;
     __device__ Pre pre(int) const { return {}; }
     __device__ void operator()(int r, T ax, const Pre&) const { y[r] = ax * scale; }
@@ -241,7 +243,7 @@ __device__ __forceinline__ void sell_rows(const int* __restrict__ off,
     // has no slice: lo = hi = n would otherwise map to the last partial slice
     // and repeat rows that another block owns.
     if (lo >= hi) return;
-    constexpr int G = sizeof(T) == 4 ? 3 : 2;
+    constexpr int G = Epi::kSlices > 0 ? Epi::kSlices : (sizeof(T) == 4 ? 3 : 2);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s_lo = lo >> 5, s_hi = (hi + 31) >> 5;
     const uint64_t pol = l2_policy(keep != 0);
@@ -706,13 +708,20 @@ static const typename Sys::T* launch_precond(const DevArgs* a, KState* ks,
                                              int nblk, cudaStream_t st, cudaEvent_t* ev, int* k) {
     using T = typename Sys::T;
     precond_scale_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, u, sig_idx, pc.dinv, pc.omega,
-                                                             pc.za, phase);
+                                                             pc.za, phase, pc.cheb, pc.bound,
+                                                             pc.lfix, pc.ratio, pc.dvec);
     mark(ev, k, st);
     T* cur = pc.za;
     T* nxt = pc.zb;
     for (int sw = 1; sw < pc.sweeps; ++sw) {
-        precond_sweep_kernel<Sys><<<nblk, kSpmvBlock, 0, st>>>(a, ks, u, sig_idx, pc.dinv, pc.omega,
-                                                               cur, nxt, phase);
+        if (pc.cheb)
+            precond_sweep_kernel<Sys, 1><<<nblk, kSpmvBlock, 0, st>>>(
+                a, ks, u, sig_idx, pc.dinv, pc.omega, cur, nxt, phase, sw, pc.bound, pc.lfix,
+                pc.ratio, pc.dvec);
+        else
+            precond_sweep_kernel<Sys, 0><<<nblk, kSpmvBlock, 0, st>>>(
+                a, ks, u, sig_idx, pc.dinv, pc.omega, cur, nxt, phase, sw, pc.bound, pc.lfix,
+                pc.ratio, pc.dvec);
         mark(ev, k, st);
         T* tmp = cur;
         cur = nxt;

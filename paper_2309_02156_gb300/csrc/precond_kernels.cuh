@@ -9,7 +9,16 @@
 // correction is x += M^{-1} (V y), so the residual GMRES minimises and tests
 // is the true one.  M^{-1} u = `sweeps` damped Jacobi sweeps on A z = u from
 // z = 0:  z_1 = omega D^{-1} u,  z_{k+1} = z_k + omega D^{-1} (u - A z_k)
-// (a fixed polynomial in D^{-1} A times D^{-1}).  Phase 0 kernels belong to an
+// (a fixed polynomial in D^{-1} A times D^{-1}), or the Chebyshev polynomial
+// of the same degree on [lmax / ratio, lmax] of the spectrum of D^{-1} A,
+// applied by the Chebyshev iteration's three-term recurrence (one product
+// with A per step, like a sweep; one more vector d):
+//   d_0 = D^{-1} u / theta, z_1 = d_0,
+//   d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / delta) D^{-1} (u - A z_k), z_{k+1} = z_k + d_k,
+// with theta, delta the centre and half-width of the interval, sigma =
+// theta / delta, rho_0 = 1 / sigma, rho_k = 1 / (2 sigma - rho_{k-1}); lmax is
+// Gershgorin's bound max_i sum_j |a_ij| / |a_ii| unless the caller fixes it.
+// Phase 0 kernels belong to an
 // Arnoldi step (skipped once the cycle is over), phase 1 kernels to the basis
 // update (skipped like the update).
 __device__ __forceinline__ bool update_skipped(const KState* ks) {
@@ -20,33 +29,81 @@ __device__ __forceinline__ bool precond_skipped(const KState* ks, int phase) {
 }
 
 // dinv = 1 / diag(A) in the system's precision (1 where the diagonal is
-// missing or zero).
+// missing or zero); with bound != NULL also max_i (sum_j |a_ij|) / |a_ii| in
+// FP64 (row sums in CSR order; the maximum is taken on the bit patterns of
+// the non-negative doubles, which order like the values; *bound starts at 0).
 template <class Sys>
 __global__ void __launch_bounds__(kStreamBlock)
-diag_inv_kernel(const DevArgs* __restrict__ a, typename Sys::T* __restrict__ dinv) {
+diag_inv_kernel(const DevArgs* __restrict__ a, typename Sys::T* __restrict__ dinv,
+                unsigned long long* bound) {
     using T = typename Sys::T;
     const T* val = Sys::val(a);
     const int n = a->n;
+    unsigned long long mx = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         T d = 0;
-        for (int e = a->rowptr[i]; e < a->rowptr[i + 1]; ++e)
+        double rs = 0.0;
+        for (int e = a->rowptr[i]; e < a->rowptr[i + 1]; ++e) {
             if (a->colind[e] == i) d = val[e];
+            rs += fabs((double)val[e]);
+        }
         dinv[i] = d != (T)0 ? (T)1 / d : (T)1;
+        const double g = rs / (d != (T)0 ? fabs((double)d) : 1.0);
+        const unsigned long long gb = (unsigned long long)__double_as_longlong(g);
+        mx = gb > mx ? gb : mx;
     }
+    if (bound) atomicMax(bound, mx);
 }
 
-// z = (omega dinv) (s u), s = sigma_{sig_idx} (a stored basis column) or 1.
+// Chebyshev coefficients of step k (k >= 1): c1 = rho_k rho_{k-1}, c2 = 2 rho_k
+// / delta; step 0 scales by 1 / theta (c2 = 1 / theta).  FP64, from the
+// interval [lmax / ratio, lmax].
+struct ChebStep {
+    double c1, c2;
+};
+__device__ __forceinline__ ChebStep cheb_step(double lmax, double ratio, int k) {
+    const double lmin = lmax / ratio;
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+    if (k == 0) return {0.0, 1.0 / theta};
+    const double sigma = theta / delta;
+    double rho_prev = 1.0 / sigma, rho = rho_prev;
+    for (int i = 1; i <= k; ++i) {
+        rho = 1.0 / (2.0 * sigma - rho_prev);
+        if (i < k) rho_prev = rho;
+    }
+    return {rho * rho_prev, 2.0 * rho / delta};
+}
+
+// Interval end of the Chebyshev preconditioner: the caller's value, or the
+// Gershgorin bound the dinv kernel left in *bound.
+__device__ __forceinline__ double cheb_lmax(const unsigned long long* bound, double fixed) {
+    return fixed > 0.0 ? fixed : __longlong_as_double((long long)*bound);
+}
+
+// Jacobi: z = (omega dinv) (s u); Chebyshev: d = z = dinv (s u) / theta.
+// s = sigma_{sig_idx} (a stored basis column) or 1.
 template <class Sys>
 __global__ void __launch_bounds__(kStreamBlock)
 precond_scale_kernel(const DevArgs* __restrict__ a, const KState* __restrict__ ks,
                      const typename Sys::T* __restrict__ u, int sig_idx,
                      const typename Sys::T* __restrict__ dinv, double omega,
-                     typename Sys::T* __restrict__ z, int phase) {
+                     typename Sys::T* __restrict__ z, int phase, int cheb,
+                     const unsigned long long* __restrict__ bound, double lfix, double ratio,
+                     typename Sys::T* __restrict__ dvec) {
     using T = typename Sys::T;
     if (precond_skipped(ks, phase)) return;
-    const T sc = sig_idx >= 0 ? (T)ks->sigma[sig_idx] : (T)1, om = (T)omega;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a->n; i += gridDim.x * blockDim.x)
-        z[i] = (om * dinv[i]) * (sc * u[i]);
+    const T sc = sig_idx >= 0 ? (T)ks->sigma[sig_idx] : (T)1;
+    // The coefficient is formed once per block (FP64 division is slow on this
+    // GPU: once per thread it would cost more than the vector pass).
+    __shared__ T om_s;
+    if (threadIdx.x == 0) om_s = cheb ? (T)cheb_step(cheb_lmax(bound, lfix), ratio, 0).c2 : (T)omega;
+    __syncthreads();
+    const T om = om_s;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a->n; i += gridDim.x * blockDim.x) {
+        const T zi = (om * dinv[i]) * (sc * u[i]);
+        z[i] = zi;
+        if (cheb) dvec[i] = zi;
+    }
 }
 
 template <typename T>
@@ -56,6 +113,7 @@ struct SweepEpi {
     const T* dinv;
     T sc, om;
     T* zout;
+    static constexpr int kSlices = 0;
     struct Pre { T z, u, d; };
     __device__ Pre pre(int r) const { return {zin[r], u[r], dinv[r]}; }
     __device__ void operator()(int r, T ax, const Pre& o) const {
@@ -64,20 +122,33 @@ struct SweepEpi {
     __device__ void operator()(int r, T ax) const { (*this)(r, ax, pre(r)); }
 };
 
-// z_out = z_in + (omega dinv) (s u - A z_in).
-template <class Sys>
-__global__ void __launch_bounds__(kSpmvBlock, 1)
-precond_sweep_kernel(const DevArgs* __restrict__ a, KState* ks, const typename Sys::T* __restrict__ u,
-                     int sig_idx, const typename Sys::T* __restrict__ dinv, double omega,
-                     const typename Sys::T* __restrict__ zin, typename Sys::T* __restrict__ zout,
-                     int phase) {
+// Chebyshev step: d = c1 d + c2 dinv (s u - A z_in), z_out = z_in + d.
+template <typename T>
+struct ChebEpi {
+    const T* zin;
+    const T* u;
+    const T* dinv;
+    T* dvec;
+    T sc, c1, c2;
+    T* zout;
+    static constexpr int kSlices = 2;
+    struct Pre { T z, u, d, dv; };
+    __device__ Pre pre(int r) const { return {zin[r], u[r], dinv[r], dvec[r]}; }
+    __device__ void operator()(int r, T ax, const Pre& o) const {
+        const T dn = c1 * o.dv + c2 * (o.d * (sc * o.u - ax));
+        dvec[r] = dn;
+        zout[r] = o.z + dn;
+    }
+    __device__ void operator()(int r, T ax) const { (*this)(r, ax, pre(r)); }
+};
+
+template <class Sys, typename Epi>
+__device__ __forceinline__ void precond_rows(const DevArgs* __restrict__ a, KState* ks,
+                                             const typename Sys::T* __restrict__ zin, const Epi& epi) {
     using T = typename Sys::T;
-    if (precond_skipped(ks, phase)) return;
-    const T sc = sig_idx >= 0 ? (T)ks->sigma[sig_idx] : (T)1, om = (T)omega;
     const int n = a->n;
     int lo, hi;
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
-    const SweepEpi<T> epi{zin, u, dinv, sc, om, zout};
     if (a->sell_off) {
         sell_rows<T>(a->sell_off, a->sell_col, reinterpret_cast<const T*>(a->sell_val), zin, n, lo,
                      hi, kSpmvWarps, a->sell_w, a->sell_keep, &ks->bad_index, epi);
@@ -95,6 +166,33 @@ precond_sweep_kernel(const DevArgs* __restrict__ a, KState* ks, const typename S
         epi(r, ax);
     }
     if (flag) atomicOr(&ks->bad_index, 1);
+}
+
+// Sweep k (k >= 1) of the preconditioner.  Jacobi: z_out = z_in + (omega
+// dinv) (s u - A z_in); Chebyshev: the recurrence step above.
+template <class Sys, int CHEB>
+__global__ void __launch_bounds__(kSpmvBlock, 1)
+precond_sweep_kernel(const DevArgs* __restrict__ a, KState* ks, const typename Sys::T* __restrict__ u,
+                     int sig_idx, const typename Sys::T* __restrict__ dinv, double omega,
+                     const typename Sys::T* __restrict__ zin, typename Sys::T* __restrict__ zout,
+                     int phase, int k, const unsigned long long* __restrict__ bound,
+                     double lfix, double ratio, typename Sys::T* __restrict__ dvec) {
+    using T = typename Sys::T;
+    if (precond_skipped(ks, phase)) return;
+    const T sc = sig_idx >= 0 ? (T)ks->sigma[sig_idx] : (T)1;
+    if constexpr (CHEB != 0) {
+        // Coefficients once per block (k FP64 divisions).
+        __shared__ T c1_s, c2_s;
+        if (threadIdx.x == 0) {
+            const ChebStep c = cheb_step(cheb_lmax(bound, lfix), ratio, k);
+            c1_s = (T)c.c1;
+            c2_s = (T)c.c2;
+        }
+        __syncthreads();
+        precond_rows<Sys>(a, ks, zin, ChebEpi<T>{zin, u, dinv, dvec, sc, c1_s, c2_s, zout});
+    } else {
+        precond_rows<Sys>(a, ks, zin, SweepEpi<T>{zin, u, dinv, sc, (T)omega, zout});
+    }
 }
 
 // t = V_stored cy (the cycle's correction before preconditioning).
@@ -138,6 +236,11 @@ struct PrecondArgs {
     T* za = nullptr;           // sweep ping-pong vectors
     T* zb = nullptr;
     T* t = nullptr;            // correction before preconditioning
+    int cheb = 0;              // 1: Chebyshev polynomial instead of Jacobi sweeps
+    const unsigned long long* bound = nullptr;   // Gershgorin bound left by the dinv kernel
+    double lfix = 0.0;         // caller's lmax (0: the bound)
+    double ratio = 30.0;       // lmax / lmin
+    T* dvec = nullptr;         // Chebyshev recurrence vector
 };
 
 // Applies M^{-1} to s u (phase 0: u = basis column sig_idx; phase 1: u = t);
