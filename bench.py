@@ -291,7 +291,8 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def profile_run(iters: int, precision: str = "f64", guess: str = "sketch", sweeps: int = 0) -> None:
+def profile_run(iters: int, precision: str = "f64", guess: str = "sketch", sweeps: int = 0,
+                precond: str = "jacobi") -> None:
     """A bounded full-size command for ncu: one guess (`guess` mode; m = 10 for
     POD / RAND) from a synthetic 20-column history and `iters` GMRES(30)
     iterations (`precision`: f64, or mixed_krylov = FP32 inner iterations;
@@ -311,7 +312,7 @@ def profile_run(iters: int, precision: str = "f64", guess: str = "sketch", sweep
     kw = {"basis_m": 10} if guess in ("pod", "rand") else {}
     seq = sa.Sequence(p.n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, krylov="gmres",
                       restart=RESTART, max_iters=iters, precision=precision, guess=guess,
-                      precond_sweeps=sweeps, **kw)
+                      precond_sweeps=sweeps, precond_kind=precond, **kw)
     rng = np.random.default_rng(1)
     for _ in range(M_HIST):
         seq.push(torch.from_numpy(rng.standard_normal(p.n)).to(dev))
@@ -865,7 +866,7 @@ def precision_form(args):
     n = N * N
     seq = sa.Sequence(n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, precision=args.precision_kind,
                       krylov="gmres", restart=RESTART, max_iters=400000,
-                      precond_sweeps=args.precision_sweeps)
+                      precond_sweeps=args.precision_sweeps, precond_kind=args.precision_precond)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     total = P + W + K
     nxt = pool.map_async(_gen_nonsym, [(N, i) for i in range(0, min(4, total))])
@@ -905,7 +906,8 @@ def precision_form(args):
         "workload": "nonsym advection-diffusion %dx%d (n=%d), M=20, s=80, %s: FP32 values/history/"
                     "inner GMRES(30)%s, FP64 refinement to rel-res 1e-10"
                     % (N, N, n, args.precision_kind,
-                       " right-preconditioned by %d Jacobi sweeps" % args.precision_sweeps
+                       " right-preconditioned by %s of degree %d" % (args.precision_precond,
+                                                                       args.precision_sweeps)
                        if args.precision_sweeps else ""),
         "value": 1e3 * K / sum(timed_ms), "unit": "systems/s", "ms_per_step": sum(timed_ms) / K,
         "steps": K, "warmup": W, "prime": P,
@@ -922,7 +924,8 @@ def precision_form(args):
 def precision_startup(hbm_peak):
     """The precision form on the first five systems of the 2048 x 2048 sequence
     (SEQ_MIXED: FP32 values, history, sketch and inner GMRES(30) right-
-    preconditioned by 8 damped Jacobi sweeps, FP64 refinement to 1e-10), with
+    preconditioned by the degree-8 Chebyshev polynomial of D^-1 A, FP64
+    refinement to 1e-10), with
     the error of every solution against the oracle's direct solve recorded by
     oracle/reference_solutions.py (sampled entries; see the error estimate
     there).  Systems 0..4 have histories of 0..4 columns."""
@@ -941,7 +944,8 @@ def precision_startup(hbm_peak):
     ci = torch.from_numpy(colind).to(dev)
     n = N * N
     seq = sa.Sequence(n, M_HIST, S_ROWS, zeta=ZETA, seed=SEED, precision="mixed", krylov="gmres",
-                      restart=RESTART, max_iters=400000, precond_sweeps=8)
+                      restart=RESTART, max_iters=400000, precond_sweeps=8,
+                      precond_kind="chebyshev")
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
     rows = []
@@ -976,7 +980,8 @@ def precision_startup(hbm_peak):
     total = sum(r["ms"] for r in rows)
     return {
         "form": "precision: nonsym 2048x2048 (n=4194304), FP32 values/history/sketch/inner "
-                "GMRES(30) with 8 Jacobi sweeps, FP64 QR, refinement residual and test to 1e-10",
+                "GMRES(30) with the degree-8 Chebyshev preconditioner, FP64 QR, refinement "
+                "residual and test to 1e-10",
         "systems": "0..4 (start of the sequence: histories of 0..4 columns)",
         "value": 1e3 * steps / total, "unit": "systems/s", "ms_per_step": total / steps,
         "all_converged": all(r["status"] == 0 for r in rows),
@@ -1005,6 +1010,7 @@ def main():
     ap.add_argument("--profile-precision", default="f64", choices=["f64", "mixed_krylov"])
     ap.add_argument("--profile-guess", default="sketch", choices=["sketch", "pod", "rand"])
     ap.add_argument("--profile-sweeps", type=int, default=0)
+    ap.add_argument("--profile-precond", default="jacobi", choices=["jacobi", "chebyshev"])
     ap.add_argument("--batched-only", action="store_true")
     ap.add_argument("--batched-count", type=int, default=512)
     ap.add_argument("--precond-form", action="store_true")
@@ -1025,6 +1031,7 @@ def main():
     ap.add_argument("--precision-warmup", type=int, default=1)
     ap.add_argument("--precision-steps", type=int, default=5)
     ap.add_argument("--precision-sweeps", type=int, default=0)
+    ap.add_argument("--precision-precond", default="jacobi", choices=["jacobi", "chebyshev"])
     ap.add_argument("--learned-ablation", action="store_true")
     ap.add_argument("--learned-train", type=int, default=400)
     ap.add_argument("--learned-eval", type=int, default=400)
@@ -1051,7 +1058,7 @@ def main():
         return
     if args.profile_run:
         profile_run(args.profile_run, args.profile_precision, args.profile_guess,
-                    args.profile_sweeps)
+                    args.profile_sweeps, args.profile_precond)
         return
     if args.batched_only:
         import torch

@@ -92,7 +92,7 @@ struct seq_ctx {
     void* zb = nullptr;
     void* tprec = nullptr;
     void* pc_d = nullptr;            // Chebyshev recurrence vector
-    unsigned long long* pc_bound = nullptr;   // Gershgorin bound of D^{-1} A (bits of a double)
+    double* pc_tab = nullptr;        // Chebyshev: Gershgorin bound (bits) and coefficients
     cudaGraphExec_t cycle = nullptr;
     cudaGraphExec_t cg_graph = nullptr;     // grid-wide CG iterations (large systems)
     cudaGraphExec_t cycle_prof = nullptr;   // same cycle with timing events between kernels
@@ -261,8 +261,7 @@ int capture_cycle(seq_ctx* ctx, bool prof) {
         }
         ev = ctx->ev.data();
     }
-    const ChebConfig cheb{ctx->cfg.precond_kind == 1, ctx->cfg.precond_lmax, ctx->cfg.precond_ratio,
-                          ctx->pc_bound};
+    const ChebConfig cheb{ctx->cfg.precond_kind == 1, ctx->pc_tab};
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
     if (!ctx->mixed)
@@ -546,7 +545,7 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
         ok = ok && cudaMalloc(&ctx->za, el * (size_t)n) == cudaSuccess;
         ok = ok && cudaMalloc(&ctx->zb, el * (size_t)n) == cudaSuccess;
         ok = ok && cudaMalloc(&ctx->tprec, el * (size_t)n) == cudaSuccess;
-        ok = ok && cudaMalloc(&ctx->pc_bound, sizeof(unsigned long long)) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->pc_tab, sizeof(double) * kChebTab) == cudaSuccess;
         if (c.precond_kind == 1)
             ok = ok && cudaMalloc(&ctx->pc_d, el * (size_t)n) == cudaSuccess;
     }
@@ -601,7 +600,7 @@ int seq_destroy(seq_ctx* ctx) {
                         ctx->sell_off, ctx->sell_col, ctx->sell_val, ctx->yring, ctx->sample,
                         ctx->yhat, ctx->used_net, ctx->Om, ctx->Zs, ctx->gpart, ctx->gcount,
                         ctx->G, ctx->Vk, ctx->lam, ctx->sweeps, ctx->Wp, ctx->lsq_red,
-                        ctx->dinv, ctx->za, ctx->zb, ctx->tprec, ctx->pc_d, ctx->pc_bound};
+                        ctx->dinv, ctx->za, ctx->zb, ctx->tprec, ctx->pc_d, ctx->pc_tab};
     for (void* p : dev_ptrs)
         if (p) cudaFree(p);
     void* host_ptrs[] = {ctx->lsq_host, ctx->h_args, ctx->h_args_in, ctx->h_ks, ctx->h_int,
@@ -939,11 +938,17 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
     rc = set_args(ctx, A, b_dev, x_dev, tol, c.max_iters);
     if (rc) return rc;
     if (c.precond_sweeps > 0) {
-        CK(cudaMemsetAsync(ctx->pc_bound, 0, sizeof(unsigned long long), ctx->stream));
+        unsigned long long* bound = reinterpret_cast<unsigned long long*>(ctx->pc_tab);
+        CK(cudaMemsetAsync(ctx->pc_tab, 0, sizeof(double) * kChebTab, ctx->stream));
         if (!ctx->mixed)
-            launch_diag_inv_f64(ctx->d_args, (double*)ctx->dinv, c.n, ctx->stream, ctx->pc_bound);
+            launch_diag_inv_f64(ctx->d_args, (double*)ctx->dinv, c.n, ctx->stream, bound);
         else
-            launch_diag_inv_f32(ctx->d_args_in, (float*)ctx->dinv, c.n, ctx->stream, ctx->pc_bound);
+            launch_diag_inv_f32(ctx->d_args_in, (float*)ctx->dinv, c.n, ctx->stream, bound);
+        if (c.precond_kind == 1) {
+            launch_cheb_table(ctx->pc_tab, c.precond_lmax, c.precond_ratio, c.precond_sweeps,
+                              ctx->stream);
+            ctx->launches += 1;
+        }
         ctx->launches += 1;
         CK(cudaGetLastError());
     }

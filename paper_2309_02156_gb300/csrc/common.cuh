@@ -21,6 +21,7 @@ constexpr int kKernelsPerStep = 4; // SpMV, first-pass dots, CGS pass 2, CGS pas
 constexpr int kStreamBlock = 384; // threads per block of the streaming kernels (one block per SM)
 constexpr int kTileChunks = 8;    // CSR entries of a 32-row tile loaded up front: 8 x 32
 constexpr int kTileStage = 2 * kTileChunks * 32;   // shared staging per warp (values, x)
+constexpr int kChebTab = 2 + 2 * 32;   // Chebyshev coefficient table (degree <= 32)
 
 // Device-side copy of the per-call arguments.  The CUDA graphs of a context
 // take a pointer to this struct, so one captured graph serves every call.

@@ -81,15 +81,15 @@ void launch_gmres_start_f64(const DevArgs* a, KState* ks, double* V, size_t ldv,
                             int nblk, int first, cudaStream_t st);
 // Right preconditioning (sweeps > 0): M^{-1} = `sweeps` damped Jacobi sweeps
 // with weight omega and dinv = 1 / diag(A), or (cheb->on) the Chebyshev
-// polynomial of degree `sweeps` on [lmax / ratio, lmax] of D^{-1} A (lmax =
-// cheb->lmax, or the Gershgorin bound the dinv kernel leaves in *cheb->bound);
-// za, zb, t, dvec: n-vectors of scratch.
+// polynomial of degree `sweeps` on [lmax / ratio, lmax] of D^{-1} A, whose
+// coefficients launch_cheb_table writes into cheb->tab once per solve (after
+// launch_diag_inv_* has left the Gershgorin bound in its first word); za, zb,
+// t, dvec: n-vectors of scratch.
 struct ChebConfig {
     int on;
-    double lmax;                          // 0: the Gershgorin bound
-    double ratio;                         // lmax / lmin
-    const unsigned long long* bound;      // written by launch_diag_inv_*
+    const double* tab;                    // kChebTab doubles
 };
+void launch_cheb_table(double* tab, double lfix, double ratio, int sweeps, cudaStream_t st);
 void launch_gmres_cycle_f64(const DevArgs* a, KState* ks, double* V, size_t ldv, double* w,
                             double* partial, int nblk, int R, cudaStream_t st, int* launches,
                             cudaEvent_t* ev = nullptr, int sweeps = 0, double omega = 1.0,

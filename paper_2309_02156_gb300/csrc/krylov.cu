@@ -76,12 +76,13 @@ void launch_gmres_cycle_f64(const DevArgs* a, KState* ks, double* V, size_t ldv,
     pc.t = t;
     if (cheb && cheb->on) {
         pc.cheb = 1;
-        pc.bound = cheb->bound;
-        pc.lfix = cheb->lmax;
-        pc.ratio = cheb->ratio;
+        pc.tab = cheb->tab;
         pc.dvec = dvec;
     }
     launch_cycle<SysF64>(a, ks, V, ldv, w, partial, nblk, R, st, launches, ev, pc);
+}
+void launch_cheb_table(double* tab, double lfix, double ratio, int sweeps, cudaStream_t st) {
+    cheb_table_kernel<<<1, 32, 0, st>>>(tab, lfix, ratio, sweeps);
 }
 void launch_diag_inv_f64(const DevArgs* a, double* dinv, int n, cudaStream_t st,
                          unsigned long long* bound) {

@@ -21,9 +21,7 @@ void launch_gmres_cycle_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, 
     pc.t = t;
     if (cheb && cheb->on) {
         pc.cheb = 1;
-        pc.bound = cheb->bound;
-        pc.lfix = cheb->lmax;
-        pc.ratio = cheb->ratio;
+        pc.tab = cheb->tab;
         pc.dvec = dvec;
     }
     launch_cycle<SysF32>(a, ks, V, ldv, w, partial, nblk, R, st, launches, ev, pc);

@@ -708,20 +708,18 @@ static const typename Sys::T* launch_precond(const DevArgs* a, KState* ks,
                                              int nblk, cudaStream_t st, cudaEvent_t* ev, int* k) {
     using T = typename Sys::T;
     precond_scale_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, u, sig_idx, pc.dinv, pc.omega,
-                                                             pc.za, phase, pc.cheb, pc.bound,
-                                                             pc.lfix, pc.ratio, pc.dvec);
+                                                             pc.za, phase, pc.cheb, pc.tab,
+                                                             pc.dvec);
     mark(ev, k, st);
     T* cur = pc.za;
     T* nxt = pc.zb;
     for (int sw = 1; sw < pc.sweeps; ++sw) {
         if (pc.cheb)
             precond_sweep_kernel<Sys, 1><<<nblk, kSpmvBlock, 0, st>>>(
-                a, ks, u, sig_idx, pc.dinv, pc.omega, cur, nxt, phase, sw, pc.bound, pc.lfix,
-                pc.ratio, pc.dvec);
+                a, ks, u, sig_idx, pc.dinv, pc.omega, cur, nxt, phase, sw, pc.tab, pc.dvec);
         else
             precond_sweep_kernel<Sys, 0><<<nblk, kSpmvBlock, 0, st>>>(
-                a, ks, u, sig_idx, pc.dinv, pc.omega, cur, nxt, phase, sw, pc.bound, pc.lfix,
-                pc.ratio, pc.dvec);
+                a, ks, u, sig_idx, pc.dinv, pc.omega, cur, nxt, phase, sw, pc.tab, pc.dvec);
         mark(ev, k, st);
         T* tmp = cur;
         cur = nxt;

@@ -74,35 +74,55 @@ __device__ __forceinline__ ChebStep cheb_step(double lmax, double ratio, int k) 
     return {rho * rho_prev, 2.0 * rho / delta};
 }
 
-// Interval end of the Chebyshev preconditioner: the caller's value, or the
-// Gershgorin bound the dinv kernel left in *bound.
-__device__ __forceinline__ double cheb_lmax(const unsigned long long* bound, double fixed) {
-    return fixed > 0.0 ? fixed : __longlong_as_double((long long)*bound);
+// Coefficient table of the Chebyshev preconditioner, formed once per solve by
+// one thread (FP64 divisions are slow on this GPU: the sweeps only load it):
+// tab[0] the Gershgorin bound (bits, from the dinv kernel), tab[1] = 1 / theta,
+// tab[2k] = c1_k and tab[2k + 1] = c2_k for steps k = 1 .. sweeps - 1; lmax =
+// lfix when the caller fixes it, else the bound.
+static __global__ void cheb_table_kernel(double* tab, double lfix, double ratio, int sweeps) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double bound = __longlong_as_double(*reinterpret_cast<const long long*>(tab));
+    const double lmax = lfix > 0.0 ? lfix : bound;
+    tab[1] = cheb_step(lmax, ratio, 0).c2;
+    for (int k = 1; k < sweeps && 2 * k + 1 < kChebTab; ++k) {
+        const ChebStep c = cheb_step(lmax, ratio, k);
+        tab[2 * k] = c.c1;
+        tab[2 * k + 1] = c.c2;
+    }
 }
 
 // Jacobi: z = (omega dinv) (s u); Chebyshev: d = z = dinv (s u) / theta.
-// s = sigma_{sig_idx} (a stored basis column) or 1.
+// s = sigma_{sig_idx} (a stored basis column) or 1.  Four independent
+// elements per thread and iteration.
 template <class Sys>
 __global__ void __launch_bounds__(kStreamBlock)
 precond_scale_kernel(const DevArgs* __restrict__ a, const KState* __restrict__ ks,
                      const typename Sys::T* __restrict__ u, int sig_idx,
                      const typename Sys::T* __restrict__ dinv, double omega,
                      typename Sys::T* __restrict__ z, int phase, int cheb,
-                     const unsigned long long* __restrict__ bound, double lfix, double ratio,
-                     typename Sys::T* __restrict__ dvec) {
+                     const double* __restrict__ tab, typename Sys::T* __restrict__ dvec) {
     using T = typename Sys::T;
     if (precond_skipped(ks, phase)) return;
     const T sc = sig_idx >= 0 ? (T)ks->sigma[sig_idx] : (T)1;
-    // The coefficient is formed once per block (FP64 division is slow on this
-    // GPU: once per thread it would cost more than the vector pass).
-    __shared__ T om_s;
-    if (threadIdx.x == 0) om_s = cheb ? (T)cheb_step(cheb_lmax(bound, lfix), ratio, 0).c2 : (T)omega;
-    __syncthreads();
-    const T om = om_s;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a->n; i += gridDim.x * blockDim.x) {
-        const T zi = (om * dinv[i]) * (sc * u[i]);
-        z[i] = zi;
-        if (cheb) dvec[i] = zi;
+    const T om = cheb ? (T)tab[1] : (T)omega;
+    const int n = a->n, stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        T uu[4], dd[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + q * stride;
+            uu[q] = i < n ? u[i] : (T)0;
+            dd[q] = i < n ? dinv[i] : (T)0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + q * stride;
+            if (i < n) {
+                const T zi = (om * dd[q]) * (sc * uu[q]);
+                z[i] = zi;
+                if (cheb) dvec[i] = zi;
+            }
+        }
     }
 }
 
@@ -175,21 +195,14 @@ __global__ void __launch_bounds__(kSpmvBlock, 1)
 precond_sweep_kernel(const DevArgs* __restrict__ a, KState* ks, const typename Sys::T* __restrict__ u,
                      int sig_idx, const typename Sys::T* __restrict__ dinv, double omega,
                      const typename Sys::T* __restrict__ zin, typename Sys::T* __restrict__ zout,
-                     int phase, int k, const unsigned long long* __restrict__ bound,
-                     double lfix, double ratio, typename Sys::T* __restrict__ dvec) {
+                     int phase, int k, const double* __restrict__ tab,
+                     typename Sys::T* __restrict__ dvec) {
     using T = typename Sys::T;
     if (precond_skipped(ks, phase)) return;
     const T sc = sig_idx >= 0 ? (T)ks->sigma[sig_idx] : (T)1;
     if constexpr (CHEB != 0) {
-        // Coefficients once per block (k FP64 divisions).
-        __shared__ T c1_s, c2_s;
-        if (threadIdx.x == 0) {
-            const ChebStep c = cheb_step(cheb_lmax(bound, lfix), ratio, k);
-            c1_s = (T)c.c1;
-            c2_s = (T)c.c2;
-        }
-        __syncthreads();
-        precond_rows<Sys>(a, ks, zin, ChebEpi<T>{zin, u, dinv, dvec, sc, c1_s, c2_s, zout});
+        precond_rows<Sys>(a, ks, zin,
+                          ChebEpi<T>{zin, u, dinv, dvec, sc, (T)tab[2 * k], (T)tab[2 * k + 1], zout});
     } else {
         precond_rows<Sys>(a, ks, zin, SweepEpi<T>{zin, u, dinv, sc, (T)omega, zout});
     }
@@ -237,9 +250,7 @@ struct PrecondArgs {
     T* zb = nullptr;
     T* t = nullptr;            // correction before preconditioning
     int cheb = 0;              // 1: Chebyshev polynomial instead of Jacobi sweeps
-    const unsigned long long* bound = nullptr;   // Gershgorin bound left by the dinv kernel
-    double lfix = 0.0;         // caller's lmax (0: the bound)
-    double ratio = 30.0;       // lmax / lmin
+    const double* tab = nullptr;   // its coefficient table (cheb_table_kernel)
     T* dvec = nullptr;         // Chebyshev recurrence vector
 };
 
