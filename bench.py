@@ -127,23 +127,46 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def profile_traffic(kind, algorithmic_bytes):
-    """Per-launch DRAM traffic of `kind`: the DRAM/algorithmic byte ratio that the
-    committed ncu summary measured (one full-set capture at Arnoldi step 15)
-    times this launch's algorithmic bytes; null when the summary was taken on
-    a different kernel source."""
-    path = os.path.join(ROOT, "profiles", "arnoldi_kernels_nonsym1024.txt")
-    src = os.path.join(ROOT, "paper_2309_02156_gb300", "csrc", "krylov_kernels.cuh")
+# Committed ncu summaries that record DRAM/algorithmic byte ratios, by the
+# precision of the Krylov kernels: the summary and the kernel sources (in
+# csrc/) its counters were taken on; its source_sha256_16 line is the first 16
+# hex digits of the SHA-256 of those sources concatenated in this order.
+TRAFFIC_PROFILES = {
+    "f64": ("arnoldi_kernels_nonsym1024.txt", ("krylov_kernels.cuh",)),
+    "f32": ("arnoldi_fp32_kernels_nonsym1024.txt",
+            ("krylov_f32_kernels.cuh", "krylov_kernels.cuh")),
+    "f32_precond": ("precond_sweeps_nonsym1024.txt",
+                    ("precond_kernels.cuh", "krylov_kernels.cuh")),
+}
+
+
+def sources_digest(sources):
+    h = hashlib.sha256()
+    for name in sources:
+        with open(os.path.join(ROOT, "paper_2309_02156_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kind, algorithmic_bytes, precision="f64"):
+    """Per-launch DRAM traffic of `kind` in the given precision ("f64" or "f32"):
+    the DRAM/algorithmic byte ratio that the committed ncu summary measured
+    times this launch's algorithmic bytes; null when no summary covers the
+    kernel or it was taken on different kernel sources."""
+    key = "f32_precond" if (precision == "f32" and kind == "precond") else precision
+    if key not in TRAFFIC_PROFILES:
+        return None
+    name, sources = TRAFFIC_PROFILES[key]
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(path):
         if line.startswith("source_sha256_16:"):
             vals["sha"] = line.split(":", 1)[1].strip()
         if line.startswith(f"traffic_ratio[{kind}]:"):
             vals["ratio"] = float(line.split(":", 1)[1].split()[0])
-    if vals.get("sha") != digest or "ratio" not in vals:
+    if vals.get("sha") != sources_digest(sources) or "ratio" not in vals:
         return None
     return vals["ratio"] * algorithmic_bytes
 
@@ -1160,7 +1183,7 @@ def main():
             roof = {"bound": "hbm", "achieved": bytes_l / t_launch / 1e9, "peak": hbm_peak,
                     "unit": "GB/s", "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_src})"}
         roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["traffic"] = profile_traffic(dom, bytes_l)
+        roof["traffic"] = profile_traffic(dom, bytes_l, "f64" if fp64 else "f32")
         roof["kernel"] = dom
         roof["algorithmic_bytes_per_launch"] = bytes_l
         roof["algorithmic_flops_per_launch"] = flops_l
@@ -1265,8 +1288,6 @@ def main():
         cst, _ = profiled(prof_steps)
         assert all(inf["status"] == 0 for _, inf in cinfos), "a %s solve did not converge" % label
         croof, ckern = roofline(cst, list(prof_steps), fp64=precision == "f64")
-        if croof["bound"] == "hbm":
-            croof.pop("traffic", None)
         return {
             "form": label, "value": whole_job_rate(K, cms, world), "unit": "systems/s",
             "ms_per_step": cms / K,

@@ -308,20 +308,30 @@ void account_cycle(seq_ctx* ctx, bool f32, int jd, bool updated, int nnz) {
     const double ns = (ctx->cfg.n + 31) / 32;
     const double spmv_mat = ctx->sell_ok ? 4.0 * (ns + 1) + (4.0 + E) * (double)*ctx->h_int : csr;
     const int sw = ctx->cfg.precond_sweeps;
-    const int S = step_kernels(f32) + sw;
-    // Preconditioner: the scale reads u, dinv and writes z; a sweep reads the
-    // matrix, z (gathered), u, dinv and writes the next z.  Chebyshev also
-    // writes d at the scale and reads and writes it at every sweep.
+    const int pk = precond_kernels(sw);
+    const int S = step_kernels(f32) + pk;
+    // Preconditioner of degree d > 1: the first sweep reads the matrix, u
+    // (gathered; the same array as its row operand) and dinv and writes z;
+    // each later sweep reads the matrix, z (gathered), u, dinv and writes the
+    // next z.  Chebyshev also writes d at every sweep but the last and reads
+    // it at every sweep but the first.  Degree 1: the scale reads u, dinv and
+    // writes z (and d).
     const double cv = ctx->cfg.precond_kind == 1 ? 1.0 : 0.0;
     auto precond = [&](int ev0) {
-        add_stat(ctx, SEQ_K_PRECOND, ev0, (3.0 + cv) * E * n, 2.0 * n);
-        for (int k = 1; k < sw; ++k)
-            add_stat(ctx, SEQ_K_PRECOND, ev0 + k, spmv_mat + (4.0 + 2.0 * cv) * E * n,
-                     2.0 * nnz + (4.0 + 3.0 * cv) * n);
+        if (sw == 1) {
+            add_stat(ctx, SEQ_K_PRECOND, ev0, (3.0 + cv) * E * n, 2.0 * n);
+            return;
+        }
+        for (int k = 1; k < sw; ++k) {
+            const double dv = cv * ((k > 1 ? 1.0 : 0.0) + (k < sw - 1 ? 1.0 : 0.0));
+            add_stat(ctx, SEQ_K_PRECOND, ev0 + k - 1,
+                     spmv_mat + ((k == 1 ? 3.0 : 4.0) + dv) * E * n,
+                     2.0 * nnz + (k == 1 ? 6.0 + 2.0 * cv : 4.0 + 3.0 * cv) * n);
+        }
     };
     for (int j = 0; j < jd; ++j) {
         const double nk = j + 1;
-        int e = S * j + sw;
+        int e = S * j + pk;
         if (sw > 0) precond(S * j);
         if (f32) {
             // fused SpMV + first-pass dots: matrix, gathered vector, w written
@@ -340,9 +350,9 @@ void account_cycle(seq_ctx* ctx, bool f32, int jd, bool updated, int nnz) {
         if (updated) {
             add_stat(ctx, SEQ_K_UPDATE, u, E * n * (jd + 1), 2.0 * n * jd);
             precond(u + 1);
-            add_stat(ctx, SEQ_K_UPDATE, u + 1 + sw, 3.0 * E * n, n);
+            add_stat(ctx, SEQ_K_UPDATE, u + 1 + pk, 3.0 * E * n, n);
         }
-        u += sw + 2;
+        u += pk + 2;
     } else {
         if (updated) add_stat(ctx, SEQ_K_UPDATE, u, E * n * (jd + 2), 2.0 * n * jd);
         u += 1;

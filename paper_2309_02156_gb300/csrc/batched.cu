@@ -459,23 +459,44 @@ __device__ int block_cg32(const BatchSeq& q, double itol, int max_iters, float* 
         }
         const float alpha = rr / pq;
         float rn_l = 0.f;
-        for (int i = tid; i < n4; i += bd) {
-            const float4 pv = p4[i], qv = q4[i];
-            float4 dv = d4[i], rv = r4[i];
-            dv.x = fmaf(alpha, pv.x, dv.x);
-            dv.y = fmaf(alpha, pv.y, dv.y);
-            dv.z = fmaf(alpha, pv.z, dv.z);
-            dv.w = fmaf(alpha, pv.w, dv.w);
-            rv.x = fmaf(-alpha, qv.x, rv.x);
-            rv.y = fmaf(-alpha, qv.y, rv.y);
-            rv.z = fmaf(-alpha, qv.z, rv.z);
-            rv.w = fmaf(-alpha, qv.w, rv.w);
-            d4[i] = dv;
-            r4[i] = rv;
-            rn_l = fmaf(rv.x, rv.x, rn_l);
-            rn_l = fmaf(rv.y, rv.y, rn_l);
-            rn_l = fmaf(rv.z, rv.z, rn_l);
-            rn_l = fmaf(rv.w, rv.w, rn_l);
+        // Two float4 groups per thread and iteration, all loads issued before
+        // the stores, so that twice the bytes are in flight per thread.
+        for (int i = tid; i < n4; i += 2 * bd) {
+            const int i1 = i + bd;
+            const bool two = i1 < n4;
+            float4 pv[2], qv[2], dv[2], rv[2];
+            pv[0] = p4[i];
+            qv[0] = q4[i];
+            dv[0] = d4[i];
+            rv[0] = r4[i];
+            if (two) {
+                pv[1] = p4[i1];
+                qv[1] = q4[i1];
+                dv[1] = d4[i1];
+                rv[1] = r4[i1];
+            }
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                if (g == 1 && !two) break;
+                dv[g].x = fmaf(alpha, pv[g].x, dv[g].x);
+                dv[g].y = fmaf(alpha, pv[g].y, dv[g].y);
+                dv[g].z = fmaf(alpha, pv[g].z, dv[g].z);
+                dv[g].w = fmaf(alpha, pv[g].w, dv[g].w);
+                rv[g].x = fmaf(-alpha, qv[g].x, rv[g].x);
+                rv[g].y = fmaf(-alpha, qv[g].y, rv[g].y);
+                rv[g].z = fmaf(-alpha, qv[g].z, rv[g].z);
+                rv[g].w = fmaf(-alpha, qv[g].w, rv[g].w);
+                rn_l = fmaf(rv[g].x, rv[g].x, rn_l);
+                rn_l = fmaf(rv[g].y, rv[g].y, rn_l);
+                rn_l = fmaf(rv[g].z, rv[g].z, rn_l);
+                rn_l = fmaf(rv[g].w, rv[g].w, rn_l);
+            }
+            d4[i] = dv[0];
+            r4[i] = rv[0];
+            if (two) {
+                d4[i1] = dv[1];
+                r4[i1] = rv[1];
+            }
         }
         for (int i = 4 * n4 + tid; i < n; i += bd) {
             q.d[i] = fmaf(alpha, q.p[i], q.d[i]);
@@ -487,14 +508,25 @@ __device__ int block_cg32(const BatchSeq& q, double itol, int max_iters, float* 
         ++it;
         const float beta = rr_new / rr;
         rr = rr_new;
-        for (int i = tid; i < n4; i += bd) {
-            const float4 rv = r4[i];
-            float4 pv = p4[i];
-            pv.x = fmaf(beta, pv.x, rv.x);
-            pv.y = fmaf(beta, pv.y, rv.y);
-            pv.z = fmaf(beta, pv.z, rv.z);
-            pv.w = fmaf(beta, pv.w, rv.w);
-            p4[i] = pv;
+        for (int i = tid; i < n4; i += 2 * bd) {
+            const int i1 = i + bd;
+            const bool two = i1 < n4;
+            float4 rv[2], pv[2];
+            rv[0] = r4[i];
+            pv[0] = p4[i];
+            if (two) {
+                rv[1] = r4[i1];
+                pv[1] = p4[i1];
+            }
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                pv[g].x = fmaf(beta, pv[g].x, rv[g].x);
+                pv[g].y = fmaf(beta, pv[g].y, rv[g].y);
+                pv[g].z = fmaf(beta, pv[g].z, rv[g].z);
+                pv[g].w = fmaf(beta, pv[g].w, rv[g].w);
+            }
+            p4[i] = pv[0];
+            if (two) p4[i1] = pv[1];
         }
         for (int i = 4 * n4 + tid; i < n; i += bd) q.p[i] = fmaf(beta, q.p[i], q.r[i]);
     }
@@ -514,8 +546,11 @@ size_t batch_smem_bytes(int s, int M) {
 
 // One time step of every sequence.  Blocks take sequences from the queue
 // until it is empty; each sequence is processed by one block from start to
-// end (no inter-block waiting).
-__global__ void __launch_bounds__(1024, 1)
+// end (no inter-block waiting).  MAXT: the largest block size the
+// instantiation is launched with at one block per SM, which sets its register
+// budget (65,536 / MAXT, at most 255): 1024 -> 64, 512 -> 128, 256 -> 255.
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
 batched_step_kernel(BatchSeq* seqs, const int* __restrict__ order, int count, int* queue,
                     const BatchParams* __restrict__ prm) {
     extern __shared__ double smem[];
@@ -632,6 +667,15 @@ batched_step_kernel(BatchSeq* seqs, const int* __restrict__ order, int count, in
     }
 }
 
+// The instantiation whose register budget fits `threads` x `blocks_per_sm`
+// threads on one SM.
+using StepKernel = void (*)(BatchSeq*, const int*, int, int*, const BatchParams*);
+StepKernel step_kernel_for(int threads, int blocks_per_sm) {
+    const int t = threads * blocks_per_sm;
+    return t <= 256 ? batched_step_kernel<256> : t <= 512 ? batched_step_kernel<512>
+                                                           : batched_step_kernel<1024>;
+}
+
 __global__ void batch_push_kernel(const double* __restrict__ x, int n, double* X, int ldx, int slot) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         X[(size_t)i * ldx + slot] = x[i];
@@ -689,7 +733,8 @@ int batch_capture(seq_batch* bt) {
         cudaGraphExecDestroy(bt->graph);
         bt->graph = nullptr;
     }
-    if (cudaFuncSetAttribute(batched_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const StepKernel kern = step_kernel_for(bt->threads, bt->blocks_per_sm);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bt->smem) != cudaSuccess) {
         cudaGetLastError();
         return SEQ_ECUDA;
@@ -698,7 +743,7 @@ int batch_capture(seq_batch* bt) {
     if (cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return SEQ_ECUDA;
     cudaMemsetAsync(bt->d_queue, 0, sizeof(int), bt->cap);
-    batched_step_kernel<<<bt->sms * bt->blocks_per_sm, bt->threads, bt->smem, bt->cap>>>(
+    kern<<<bt->sms * bt->blocks_per_sm, bt->threads, bt->smem, bt->cap>>>(
         bt->d_seqs, bt->d_order, bt->count, bt->d_queue, bt->d_prm);
     if (cudaStreamEndCapture(bt->cap, &g) != cudaSuccess) {
         cudaGetLastError();
@@ -906,10 +951,10 @@ int seq_batch_autotune(seq_batch* bt, const double* const* values, const double*
                 bt->threads = thr[ti];
                 bt->blocks_per_sm = bps;
                 bt->order_kind = oi;
-                if (cudaFuncSetAttribute(batched_step_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                const StepKernel kern = step_kernel_for(thr[ti], bps);
+                if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bt->smem) != cudaSuccess ||
-                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_step_kernel, thr[ti],
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, thr[ti],
                                                                   bt->smem) != cudaSuccess ||
                     nb < bps) {
                     cudaGetLastError();

@@ -64,12 +64,16 @@ int stream_grid(int n);
 // Arnoldi kernels per step: FP64 SpMV, first-pass dots, pass 2, pass 3; FP32
 // fuses the SpMV with the first-pass dots.
 inline int step_kernels(bool f32) { return f32 ? kKernelsPerStep - 1 : kKernelsPerStep; }
-// Kernels of one restart cycle: per Arnoldi step the preconditioner's
-// `sweeps` kernels (scale + sweeps - 1 sweeps) and the Arnoldi kernels; then
-// the update (combine, preconditioner, axpy; or one update kernel) and the
-// restart residual.
+// Kernels of one preconditioner application of degree `sweeps`: the scale
+// kernel alone for one sweep, else sweeps - 1 sweep kernels (the first forms
+// the scaled start vector itself).
+inline int precond_kernels(int sweeps) { return sweeps <= 1 ? sweeps : sweeps - 1; }
+// Kernels of one restart cycle: per Arnoldi step the preconditioner's kernels
+// and the Arnoldi kernels; then the update (combine, preconditioner, axpy; or
+// one update kernel) and the restart residual.
 inline int cycle_kernels(int R, int sweeps, bool f32) {
-    return (step_kernels(f32) + sweeps) * R + (sweeps > 0 ? sweeps + 2 : 1) + 1;
+    const int pk = precond_kernels(sweeps);
+    return (step_kernels(f32) + pk) * R + (sweeps > 0 ? pk + 2 : 1) + 1;
 }
 // ||b - A x|| and ||b|| of FP64 vectors; results in st->beta, st->bnorm and
 // st->first_relres = beta / bnorm.

@@ -203,14 +203,16 @@ __device__ __forceinline__ T sell_dot_w(int w, const T (&v)[kSellW], const T (&x
     }
 }
 
+// x2 != NULL: the gathered operand is x[c] * x2[c].
 template <typename T>
 __device__ __forceinline__ T sell_row_loop(const int* __restrict__ col, const T* __restrict__ val,
-                                           const T* __restrict__ x, int n, int o, int w, int& flag) {
+                                           const T* __restrict__ x, const T* __restrict__ x2,
+                                           int n, int o, int w, int& flag) {
     const int lane = threadIdx.x & 31;
     T a = 0;
     for (int k = 0; k < w; ++k) {
         const int c = __ldg(col + o + k * 32 + lane);
-        if ((unsigned)c < (unsigned)n) a = fma(__ldg(val + o + k * 32 + lane), x[c], a);
+        if ((unsigned)c < (unsigned)n) a = fma(__ldg(val + o + k * 32 + lane), x2 ? x[c] * x2[c] : x[c], a);
         else if (c >= 0) flag = 1;
     }
     return a;
@@ -219,8 +221,24 @@ __device__ __forceinline__ T sell_row_loop(const int* __restrict__ col, const T*
 // Row results of a SELL product go through an epilogue: pre(row) loads the
 // row operands the epilogue needs (issued early), epi(row, (A x)_row, pre)
 // writes the results; kSlices > 0 overrides the slices per warp and
-// iteration (epilogues with many row operands take fewer).
+// iteration (epilogues with many row operands take fewer).  An epilogue with
+// a member x2 (and kProd = true) makes the product gather x[c] * x2[c]
+// instead of x[c]: A (x .* x2) without forming x .* x2.
 struct NoPre {};
+
+template <class E, class = void>
+struct GatherProd {
+    static constexpr bool value = false;
+};
+template <class E>
+struct GatherProd<E, decltype((void)E::kProd)> {
+    static constexpr bool value = E::kProd;
+};
+template <class E, typename T>
+__device__ __forceinline__ const T* gather_x2(const E& e) {
+    if constexpr (GatherProd<E>::value) return e.x2;
+    else return nullptr;
+}
 
 template <typename T>
 struct ScaleEpi {
@@ -291,6 +309,8 @@ __device__ __forceinline__ void sell_rows(const int* __restrict__ off,
 #pragma unroll
                 for (int k = 0; k < kSellW; ++k) {
                     xv[g][k] = (unsigned)c[g][k] < (unsigned)n ? x[c[g][k]] : (T)0;
+                    if constexpr (GatherProd<Epi>::value)
+                        xv[g][k] *= (unsigned)c[g][k] < (unsigned)n ? epi.x2[c[g][k]] : (T)0;
                     if (c[g][k] >= n) flag = 1;
                 }
 #pragma unroll
@@ -299,7 +319,9 @@ __device__ __forceinline__ void sell_rows(const int* __restrict__ off,
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 if (row_ok[g]) pre[g] = epi.pre(r[g]);
-                ax[g] = w[g] > 0 ? sell_row_loop<T>(col, val, x, n, o[g], w[g], flag) : (T)0;
+                ax[g] = w[g] > 0 ? sell_row_loop<T>(col, val, x, gather_x2<Epi, T>(epi), n, o[g],
+                                                    w[g], flag)
+                                 : (T)0;
             }
         }
 #pragma unroll
@@ -707,23 +729,38 @@ static const typename Sys::T* launch_precond(const DevArgs* a, KState* ks,
                                              const typename Sys::T* u, int sig_idx, int phase,
                                              int nblk, cudaStream_t st, cudaEvent_t* ev, int* k) {
     using T = typename Sys::T;
-    precond_scale_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, u, sig_idx, pc.dinv, pc.omega,
-                                                             pc.za, phase, pc.cheb, pc.tab,
-                                                             pc.dvec);
-    mark(ev, k, st);
+    if (pc.sweeps == 1) {
+        precond_scale_kernel<Sys><<<nblk, kStreamBlock, 0, st>>>(a, ks, u, sig_idx, pc.dinv,
+                                                                 pc.omega, pc.za, phase, pc.cheb,
+                                                                 pc.tab, pc.dvec);
+        mark(ev, k, st);
+        return pc.za;
+    }
+    // Sweep 1 forms z_1 from u itself (no scale kernel), then sweeps 2 .. d-1.
     T* cur = pc.za;
     T* nxt = pc.zb;
     for (int sw = 1; sw < pc.sweeps; ++sw) {
-        if (pc.cheb)
-            precond_sweep_kernel<Sys, 1><<<nblk, kSpmvBlock, 0, st>>>(
-                a, ks, u, sig_idx, pc.dinv, pc.omega, cur, nxt, phase, sw, pc.tab, pc.dvec);
+        const int last = sw == pc.sweeps - 1;
+        const T* zin = sw == 1 ? u : cur;
+        T* zout = sw == 1 ? cur : nxt;
+        if (pc.cheb && sw == 1)
+            precond_sweep_kernel<Sys, 1, 1><<<nblk, kSpmvBlock, 0, st>>>(
+                a, ks, u, sig_idx, pc.dinv, pc.omega, zin, zout, phase, sw, pc.tab, pc.dvec, last);
+        else if (pc.cheb)
+            precond_sweep_kernel<Sys, 1, 0><<<nblk, kSpmvBlock, 0, st>>>(
+                a, ks, u, sig_idx, pc.dinv, pc.omega, zin, zout, phase, sw, pc.tab, pc.dvec, last);
+        else if (sw == 1)
+            precond_sweep_kernel<Sys, 0, 1><<<nblk, kSpmvBlock, 0, st>>>(
+                a, ks, u, sig_idx, pc.dinv, pc.omega, zin, zout, phase, sw, pc.tab, pc.dvec, last);
         else
-            precond_sweep_kernel<Sys, 0><<<nblk, kSpmvBlock, 0, st>>>(
-                a, ks, u, sig_idx, pc.dinv, pc.omega, cur, nxt, phase, sw, pc.tab, pc.dvec);
+            precond_sweep_kernel<Sys, 0, 0><<<nblk, kSpmvBlock, 0, st>>>(
+                a, ks, u, sig_idx, pc.dinv, pc.omega, zin, zout, phase, sw, pc.tab, pc.dvec, last);
         mark(ev, k, st);
-        T* tmp = cur;
-        cur = nxt;
-        nxt = tmp;
+        if (sw > 1) {
+            T* tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
     }
     return cur;
 }

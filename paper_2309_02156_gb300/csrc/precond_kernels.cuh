@@ -142,13 +142,15 @@ struct SweepEpi {
     __device__ void operator()(int r, T ax) const { (*this)(r, ax, pre(r)); }
 };
 
-// Chebyshev step: d = c1 d + c2 dinv (s u - A z_in), z_out = z_in + d.
+// Chebyshev step: d = c1 d + c2 dinv (s u - A z_in), z_out = z_in + d (d is
+// not stored at the last step: dout = NULL).
 template <typename T>
 struct ChebEpi {
     const T* zin;
     const T* u;
     const T* dinv;
-    T* dvec;
+    const T* dvec;
+    T* dout;
     T sc, c1, c2;
     T* zout;
     static constexpr int kSlices = 2;
@@ -156,8 +158,40 @@ struct ChebEpi {
     __device__ Pre pre(int r) const { return {zin[r], u[r], dinv[r], dvec[r]}; }
     __device__ void operator()(int r, T ax, const Pre& o) const {
         const T dn = c1 * o.dv + c2 * (o.d * (sc * o.u - ax));
-        dvec[r] = dn;
+        if (dout) dout[r] = dn;
         zout[r] = o.z + dn;
+    }
+    __device__ void operator()(int r, T ax) const { (*this)(r, ax, pre(r)); }
+};
+
+// First sweep with the scale step folded in: z_1 = om (dinv (s u)) is a
+// pointwise function of u, so the product gathers u[c] dinv[c] (A z_1 = om s
+// A (dinv .* u)) and the row forms z_1 itself.  Jacobi: om = omega, z_out =
+// z_1 + om dinv (s u - A z_1).  Chebyshev: om = 1 / theta, d_0 = z_1, d_1 = c1
+// d_0 + c2 dinv (s u - A z_1), z_out = z_1 + d_1.
+template <typename T, int CHEB>
+struct FirstEpi {
+    const T* u;
+    const T* dinv;
+    const T* x2;                         // = dinv: the gather's second factor
+    T* dout;
+    T sc, om, c1, c2;
+    T* zout;
+    static constexpr int kSlices = CHEB ? 2 : 0;
+    static constexpr bool kProd = true;
+    struct Pre { T u, d; };
+    __device__ Pre pre(int r) const { return {u[r], dinv[r]}; }
+    __device__ void operator()(int r, T ax, const Pre& o) const {
+        const T su = sc * o.u;
+        const T z1 = (om * o.d) * su;
+        const T az = (om * sc) * ax;
+        if constexpr (CHEB != 0) {
+            const T dn = c1 * z1 + c2 * (o.d * (su - az));
+            if (dout) dout[r] = dn;
+            zout[r] = z1 + dn;
+        } else {
+            zout[r] = z1 + (om * o.d) * (su - az);
+        }
     }
     __device__ void operator()(int r, T ax) const { (*this)(r, ax, pre(r)); }
 };
@@ -171,16 +205,17 @@ __device__ __forceinline__ void precond_rows(const DevArgs* __restrict__ a, KSta
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
     if (a->sell_off) {
         sell_rows<T>(a->sell_off, a->sell_col, reinterpret_cast<const T*>(a->sell_val), zin, n, lo,
-                     hi, kSpmvWarps, a->sell_w, a->sell_keep, &ks->bad_index, epi);
+                     hi, (int)(blockDim.x >> 5), a->sell_w, a->sell_keep, &ks->bad_index, epi);
         return;
     }
     const T* val = Sys::val(a);
+    const T* x2 = gather_x2<Epi, T>(epi);
     int flag = 0;
     for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) {
         T ax = 0;
         for (int e = a->rowptr[r]; e < a->rowptr[r + 1]; ++e) {
             const int c = a->colind[e];
-            if ((unsigned)c < (unsigned)n) ax = fma(val[e], zin[c], ax);
+            if ((unsigned)c < (unsigned)n) ax = fma(val[e], x2 ? zin[c] * x2[c] : zin[c], ax);
             else flag = 1;
         }
         epi(r, ax);
@@ -189,22 +224,31 @@ __device__ __forceinline__ void precond_rows(const DevArgs* __restrict__ a, KSta
 }
 
 // Sweep k (k >= 1) of the preconditioner.  Jacobi: z_out = z_in + (omega
-// dinv) (s u - A z_in); Chebyshev: the recurrence step above.
-template <class Sys, int CHEB>
+// dinv) (s u - A z_in); Chebyshev: the recurrence step above.  FIRST: sweep 1
+// with the scale step folded in (z_in is not read; see FirstEpi).  last: the
+// final sweep of the application (Chebyshev does not store d there).
+template <class Sys, int CHEB, int FIRST>
 __global__ void __launch_bounds__(kSpmvBlock, 1)
 precond_sweep_kernel(const DevArgs* __restrict__ a, KState* ks, const typename Sys::T* __restrict__ u,
                      int sig_idx, const typename Sys::T* __restrict__ dinv, double omega,
                      const typename Sys::T* __restrict__ zin, typename Sys::T* __restrict__ zout,
                      int phase, int k, const double* __restrict__ tab,
-                     typename Sys::T* __restrict__ dvec) {
+                     typename Sys::T* __restrict__ dvec, int last) {
     using T = typename Sys::T;
     if (precond_skipped(ks, phase)) return;
     const T sc = sig_idx >= 0 ? (T)ks->sigma[sig_idx] : (T)1;
-    if constexpr (CHEB != 0) {
-        precond_rows<Sys>(a, ks, zin,
-                          ChebEpi<T>{zin, u, dinv, dvec, sc, (T)tab[2 * k], (T)tab[2 * k + 1], zout});
+    T* dout = last ? nullptr : dvec;
+    if constexpr (FIRST != 0) {
+        const T om = CHEB ? (T)tab[1] : (T)omega;
+        const T c1 = CHEB ? (T)tab[2] : (T)0, c2 = CHEB ? (T)tab[3] : (T)0;
+        const FirstEpi<T, CHEB> epi{u, dinv, dinv, dout, sc, om, c1, c2, zout};
+        precond_rows<Sys>(a, ks, u, epi);
+    } else if constexpr (CHEB != 0) {
+        const ChebEpi<T> epi{zin, u, dinv, dvec, dout, sc, (T)tab[2 * k], (T)tab[2 * k + 1], zout};
+        precond_rows<Sys>(a, ks, zin, epi);
     } else {
-        precond_rows<Sys>(a, ks, zin, SweepEpi<T>{zin, u, dinv, sc, (T)omega, zout});
+        const SweepEpi<T> epi{zin, u, dinv, sc, (T)omega, zout};
+        precond_rows<Sys>(a, ks, zin, epi);
     }
 }
 

@@ -61,6 +61,33 @@ def test_traffic_is_null_once_the_source_changes(tmp_path, monkeypatch):
     assert bench.profile_traffic("cgs_pass2", 1.0e6) is None
 
 
+def test_each_precision_reads_its_own_summary(tmp_path, monkeypatch):
+    """FP64 kernels, FP32 Arnoldi kernels and FP32 preconditioner sweeps each
+    take their ratio from their own summary, keyed to the hash of the sources
+    that summary names; a change in any one of those sources voids it."""
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    csrc = tmp_path / "paper_2309_02156_gb300" / "csrc"
+    os.makedirs(csrc)
+    os.makedirs(tmp_path / "profiles")
+    names = {n for _, srcs in bench.TRAFFIC_PROFILES.values() for n in srcs}
+    for n in names:
+        (csrc / n).write_text(f"// {n}\n")
+    ratio = {"f64": 0.91, "f32": 1.07, "f32_precond": 0.83}
+    for key, (name, srcs) in bench.TRAFFIC_PROFILES.items():
+        kind = "precond" if key == "f32_precond" else "spmv"
+        (tmp_path / "profiles" / name).write_text(
+            f"source_sha256_16: {bench.sources_digest(srcs)}\n"
+            f"traffic_ratio[{kind}]: {ratio[key]} (test)\n")
+    assert bench.profile_traffic("spmv", 1e6, "f64") == pytest.approx(0.91e6)
+    assert bench.profile_traffic("spmv", 1e6, "f32") == pytest.approx(1.07e6)
+    assert bench.profile_traffic("precond", 1e6, "f32") == pytest.approx(0.83e6)
+    assert bench.profile_traffic("precond", 1e6, "f64") is None
+    srcs = bench.TRAFFIC_PROFILES["f32_precond"][1]
+    with open(csrc / srcs[-1], "a") as f:
+        f.write("// edited\n")
+    assert bench.profile_traffic("precond", 1e6, "f32") is None
+
+
 def _run_reference(env_extra):
     import json
     import subprocess
