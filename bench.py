@@ -348,7 +348,7 @@ def profile_run(iters: int, precision: str = "f64", guess: str = "sketch", sweep
     seq.close()
 
 
-def batched_form(K, W, hbm_peak, count=512, plain_sample=16):
+def batched_form(K, W, hbm_peak, count=512, plain_sample=16, one_block_ref=False):
     """512 independent SPD sequences (grid side 48..384, M = 12, s = 48), FP32 CG
     inside FP64 refinement to 1e-8, one persistent launch per time step (CUDA
     graph).  Systems are assembled on the device between timed steps."""
@@ -405,6 +405,20 @@ def batched_form(K, W, hbm_peak, count=512, plain_sample=16):
         total_ms += e0.elapsed_time(e1)
         infos_all.append(infos)
         feed()
+    one_block = None
+    if one_block_ref and chosen["ctas_per_sequence"] > 1:
+        # the same step under the one-block schedule, for comparison
+        vs, bs, keep = inputs(M + W + K)
+        bt.set_schedule(1024, 1, 0)
+        bt.step(vs, bs, xs, TOL)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        vs, bs, keep = inputs(M + W + K + 1)
+        e0.record(stream)
+        bt.step(vs, bs, xs, TOL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        one_block = e0.elapsed_time(e1)
     bt.close()
     plain_out = None
     if plain:
@@ -454,7 +468,10 @@ def batched_form(K, W, hbm_peak, count=512, plain_sample=16):
         "final_relres_max": max(f["final_relres"] for f in flat),
         "all_converged": all(f["status"] == 0 for f in flat),
         "plain_fp64": plain_out,
-        "roofline": {"bound": "hbm", "kernel": "batched_step_kernel",
+        "one_block_ms_per_step": one_block,
+        "roofline": {"bound": "hbm",
+                     "kernel": ("batched_cluster_kernel" if chosen["ctas_per_sequence"] > 1
+                                else "batched_step_kernel"),
                      "achieved": byts / secs / 1e9, "peak": hbm_peak, "unit": "GB/s",
                      "frac": byts / secs / 1e9 / hbm_peak},
     }
@@ -1336,6 +1353,14 @@ def main():
     batched = None
     if not args.no_batched:
         batched = batched_form(args.batched_steps, 2, hbm_peak)
+        # fewer sequences than SMs: the autotuner's cluster schedules spread
+        # each sequence over several SMs
+        sb = batched_form(args.batched_steps, 2, hbm_peak, count=64, plain_sample=0,
+                          one_block_ref=True)
+        batched["batch_of_64"] = {k: sb[k] for k in ("form", "value", "unit", "ms_per_step",
+                                                      "schedule", "one_block_ms_per_step",
+                                                      "iters_mean", "all_converged")}
+        batched["batch_of_64"]["frac"] = sb["roofline"]["frac"]
 
     small = None
     if not args.no_chosen:

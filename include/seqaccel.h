@@ -374,8 +374,10 @@ int seq_batch_step(seq_batch* batch, const double* const* values, const double* 
 
 /* Autotuner: times one non-committing step (no history update) for every
  * schedule (threads per block 256/512/1024, one or two blocks per SM,
- * largest-first or given queue order) on these inputs and keeps the fastest;
- * chosen (3 ints, may be NULL) receives it. */
+ * largest-first or given queue order, one block or a cluster of 4 or 8 CTAs
+ * per sequence) on these inputs and keeps the fastest; chosen (3 ints, may be
+ * NULL) receives threads, blocks per SM and order (seq_batch_get_schedule
+ * also gives the cluster size). */
 int seq_batch_autotune(seq_batch* batch, const double* const* values, const double* const* b,
                        double* const* x, double tol, int32_t* chosen);
 
@@ -388,9 +390,23 @@ int seq_batch_push(seq_batch* batch, int32_t k, const double* x_dev);
  * with seq_batch_push); on = 1 (default): every step pushes its solutions. */
 int seq_batch_set_autopush(seq_batch* batch, int32_t on);
 
-/* Fix the schedule explicitly (e.g. one the autotuner picked earlier). */
+/* Fix the schedule explicitly (e.g. one the autotuner picked earlier); one
+ * block per sequence. */
 int seq_batch_set_schedule(seq_batch* batch, int32_t threads, int32_t blocks_per_sm,
                            int32_t order_kind);
+
+/* Cluster schedule: each sequence is taken by a thread-block cluster of ctas
+ * (1, 2, 4 or 8) CTAs, one per SM, each owning a contiguous range of the
+ * sequence's rows; block sums are combined over the cluster through
+ * distributed shared memory (same steps and arithmetic, rows split).  Fewer
+ * sequences are in flight at once, so their working sets stay in L2 between
+ * CG iterations.  ctas = 1 is the one-block schedule with `threads`.  The
+ * autotuner also tries clusters of 4 and 8 (512 and 1024 threads). */
+int seq_batch_set_cluster(seq_batch* batch, int32_t ctas, int32_t threads, int32_t order_kind);
+
+/* The schedule in use: out[0] threads per block, out[1] blocks per SM,
+ * out[2] order (0 largest first, 1 given), out[3] CTAs per sequence. */
+int seq_batch_get_schedule(const seq_batch* batch, int32_t* out);
 
 /* The sketched block W = S [A X | b] computed without allocating any device
  * memory.  The paper has no counterpart: this is a deployment variant of the

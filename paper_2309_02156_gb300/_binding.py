@@ -99,6 +99,9 @@ _SIGS = {
     "seq_batch_set_autopush": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "seq_batch_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_int32]),
+    "seq_batch_set_cluster": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_int32]),
+    "seq_batch_get_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "seq_mlp_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "seq_mlp_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -419,8 +422,16 @@ class Batch:
         rc = self._lib.seq_batch_autotune(self._h, va, ba, xa, ctypes.c_double(tol), chosen)
         if rc != 0:
             raise SeqError(rc, "seq_batch_autotune failed")
-        return {"threads": chosen[0], "blocks_per_sm": chosen[1],
-                "order": "largest first" if chosen[2] == 0 else "given"}
+        return self.schedule()
+
+    def schedule(self) -> dict:
+        """The schedule in use (seq_batch_get_schedule)."""
+        out = (ctypes.c_int32 * 4)()
+        rc = self._lib.seq_batch_get_schedule(self._h, out)
+        if rc != 0:
+            raise SeqError(rc, "seq_batch_get_schedule failed")
+        return {"threads": out[0], "blocks_per_sm": out[1],
+                "order": "largest first" if out[2] == 0 else "given", "ctas_per_sequence": out[3]}
 
     def set_autopush(self, on: bool) -> None:
         rc = self._lib.seq_batch_set_autopush(self._h, int(bool(on)))
@@ -436,6 +447,12 @@ class Batch:
         rc = self._lib.seq_batch_set_schedule(self._h, threads, blocks_per_sm, order)
         if rc != 0:
             raise SeqError(rc, "seq_batch_set_schedule failed")
+
+    def set_cluster(self, ctas: int, threads: int = 1024, order: int = 0) -> None:
+        """One thread-block cluster of `ctas` CTAs per sequence (seq_batch_set_cluster)."""
+        rc = self._lib.seq_batch_set_cluster(self._h, ctas, threads, order)
+        if rc != 0:
+            raise SeqError(rc, "seq_batch_set_cluster failed")
 
 
 class MLP:

@@ -120,12 +120,13 @@ __device__ void sketch_column_b(int j, int s, int zeta, uint64_t seed, uint16_t*
     }
 }
 
-// The sketched block W (s x (M+1), physical history slots, b last) of one
-// sequence, summed into Wsum (shared).  Warps 0..kSketchWarps-1 keep private
-// copies; rows are taken in batches of 32 per warp, lane l building the
-// sketch column of row base + l; the copies are added in warp order.
+// The sketched block W (s x (M+1), physical history slots, b last) of rows
+// [r_lo, r_hi) of one sequence, summed into Wsum (shared).  Warps
+// 0..kSketchWarps-1 keep private copies; rows are taken in batches of 32 per
+// warp, lane l building the sketch column of row base + l; the copies are
+// added in warp order.
 __device__ void block_sketch(const BatchSeq& q, double* Wpriv, uint16_t* sks, double* Wsum,
-                             int& bad) {
+                             int& bad, int r_lo, int r_hi) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ncol = q.M + 1, wsz = q.s * ncol;
     const int nsw = min(kSketchWarps, (int)(blockDim.x >> 5));
@@ -134,10 +135,10 @@ __device__ void block_sketch(const BatchSeq& q, double* Wpriv, uint16_t* sks, do
     if (warp < nsw) {
         double* Ww = Wpriv + warp * wsz;
         uint16_t* sk = sks + warp * 32 * kMaxZeta;
-        for (int base = warp * 32; base < q.n; base += nsw * 32) {
-            if (base + lane < q.n) sketch_column_b(base + lane, q.s, q.zeta, q.seed, sk + lane * kMaxZeta);
+        for (int base = r_lo + warp * 32; base < r_hi; base += nsw * 32) {
+            if (base + lane < r_hi) sketch_column_b(base + lane, q.s, q.zeta, q.seed, sk + lane * kMaxZeta);
             __syncwarp();
-            const int cnt = min(32, q.n - base);
+            const int cnt = min(32, r_hi - base);
             for (int u = 0; u < cnt; ++u) {
                 const int r = base + u;
                 double y = 0.0;
@@ -334,15 +335,18 @@ __device__ void block_lsq(const double* Wsum, int s, int M, int m, int oldest, d
 // column >= n is skipped and flagged.  Row results go to epi(row, value).
 constexpr int kBW = 5;      // 5-point stencils: every slice fits; wider rows take the loop
 
+// Slices [s_lo, s_hi); rows outside [r_lo, r_hi) were written by other
+// thread blocks of the launch and are read through L2 only.
 template <typename Epi>
 __device__ __forceinline__ void bsell_spmv(const BatchSeq& q, const float* __restrict__ x, int nw,
-                                           int* bad, Epi& epi) {
+                                           int* bad, Epi& epi, int s_lo, int s_hi, int r_lo,
+                                           int r_hi) {
     // Two slices per warp and iteration: both slices' index and value loads
     // and the epilogue's row operand are in flight together, then the gathers.
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n = q.n;
-    const int ns = (n + 31) >> 5;
+    const int ns = s_hi;
     int flag = 0;
-    for (int sl0 = warp; sl0 < ns; sl0 += 2 * nw) {
+    for (int sl0 = s_lo + warp; sl0 < ns; sl0 += 2 * nw) {
         int o[2], w[2], r[2];
         bool live[2];
 #pragma unroll
@@ -372,8 +376,11 @@ __device__ __forceinline__ void bsell_spmv(const BatchSeq& q, const float* __res
             for (int g = 0; g < 2; ++g)
 #pragma unroll
                 for (int k = 0; k < kBW; ++k) {
-                    xv[g][k] = (unsigned)c[g][k] < (unsigned)n ? x[c[g][k]] : 0.f;
-                    flag |= c[g][k] >= n;
+                    const int cc = c[g][k];
+                    xv[g][k] = (unsigned)cc < (unsigned)n
+                                   ? (cc >= r_lo && cc < r_hi ? x[cc] : __ldcg(x + cc))
+                                   : 0.f;
+                    flag |= cc >= n;
                 }
 #pragma unroll
             for (int g = 0; g < 2; ++g)
@@ -385,8 +392,11 @@ __device__ __forceinline__ void bsell_spmv(const BatchSeq& q, const float* __res
             for (int g = 0; g < 2; ++g)
                 for (int k = 0; k < w[g]; ++k) {
                     const int cc = q.scol[o[g] + k * 32 + lane];
-                    if ((unsigned)cc < (unsigned)n) a[g] = fmaf(q.sval[o[g] + k * 32 + lane], x[cc], a[g]);
-                    else flag |= cc >= n;
+                    if ((unsigned)cc < (unsigned)n)
+                        a[g] = fmaf(q.sval[o[g] + k * 32 + lane],
+                                    cc >= r_lo && cc < r_hi ? x[cc] : __ldcg(x + cc), a[g]);
+                    else
+                        flag |= cc >= n;
                 }
         }
 #pragma unroll
@@ -451,7 +461,7 @@ __device__ int block_cg32(const BatchSeq& q, double itol, int max_iters, float* 
         }
         __syncthreads();
         CgProductEpi epi{q.q, q.p, 0.f};
-        bsell_spmv(q, q.p, nw, sbad, epi);
+        bsell_spmv(q, q.p, nw, sbad, epi, 0, (n + 31) >> 5, 0, n);
         const float pq = btotal(epi.acc, sred);
         if (!(pq > 0.f)) {
             status = isfinite(pq) ? -4 : -5;
@@ -534,6 +544,170 @@ __device__ int block_cg32(const BatchSeq& q, double itol, int max_iters, float* 
     return it;
 }
 
+// ---------------------------------------------------------------------------
+// Cluster form: a thread-block cluster of C CTAs (one per SM) takes each
+// sequence, CTA k owning a contiguous range of its 32-row slices.  Fewer
+// sequences are in flight at once (one per cluster instead of one per SM), so
+// their working sets stay in L2 between CG iterations.  Block totals are
+// combined across the cluster through distributed shared memory: every CTA
+// reads the C partial sums in rank order, so all CTAs hold bitwise the same
+// total and take the same branches -- every cluster barrier below is reached
+// by all CTAs the same number of times.
+__device__ __forceinline__ unsigned cl_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cl_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// Cluster barrier; writes before it (shared and global) are visible after it.
+__device__ __forceinline__ void cl_sync() {
+    asm volatile("barrier.cluster.arrive.release;\n\t"
+                 "barrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cl_map(const void* p, unsigned rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(r)
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ double cl_ld(const double* p, unsigned rank) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(cl_map(p, rank)) : "memory");
+    return v;
+}
+__device__ __forceinline__ float cl_ld(const float* p, unsigned rank) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(cl_map(p, rank)) : "memory");
+    return v;
+}
+__device__ __forceinline__ int cl_ld(const int* p, unsigned rank) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(cl_map(p, rank)) : "memory");
+    return v;
+}
+
+// Sum over the cluster of one block total per CTA (every thread gets it).
+// slot: two shared words used alternately (par), bc: a shared word.
+template <typename T>
+__device__ __forceinline__ T cl_total(T blocktotal, T* slot, T* bc, int& par) {
+    if (threadIdx.x == 0) slot[par] = blocktotal;
+    cl_sync();
+    if (threadIdx.x < 32) {
+        const unsigned nr = cl_size();
+        const T v = threadIdx.x < nr ? cl_ld(&slot[par], threadIdx.x) : (T)0;
+        T t = 0;
+        for (unsigned r = 0; r < nr; ++r) t += __shfl_sync(0xffffffffu, v, r);
+        if (threadIdx.x == 0) *bc = t;
+    }
+    __syncthreads();
+    const T t = *bc;
+    par ^= 1;
+    return t;
+}
+
+struct ClRed {
+    double* dslot;
+    double* dbc;
+    float* fslot;
+    float* fbc;
+    int dpar, fpar;
+};
+
+// FP32 CG of block_cg32 on the rows [r_lo, r_hi) (slices [s_lo, s_hi)) of
+// this CTA, totals over the cluster.
+__device__ int cluster_cg32(const BatchSeq& q, double itol, int max_iters, float* sred, int* sbad,
+                            int s_lo, int s_hi, int r_lo, int r_hi, ClRed& red, int& status) {
+    const int i4lo = r_lo >> 2, i4hi = r_hi >> 2;
+    float4* r4 = reinterpret_cast<float4*>(q.r);
+    float4* p4 = reinterpret_cast<float4*>(q.p);
+    float4* q4 = reinterpret_cast<float4*>(q.q);
+    float4* d4 = reinterpret_cast<float4*>(q.d);
+    const int tid = threadIdx.x, bd = blockDim.x, nw = bd >> 5;
+    float rr_l = 0.f;
+    for (int i = i4lo + tid; i < i4hi; i += bd) {
+        const float4 ri = r4[i];
+        d4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        p4[i] = ri;
+        rr_l = fmaf(ri.x, ri.x, rr_l);
+        rr_l = fmaf(ri.y, ri.y, rr_l);
+        rr_l = fmaf(ri.z, ri.z, rr_l);
+        rr_l = fmaf(ri.w, ri.w, rr_l);
+    }
+    for (int i = max(r_lo, 4 * i4hi) + tid; i < r_hi; i += bd) {
+        const float ri = q.r[i];
+        q.d[i] = 0.f;
+        q.p[i] = ri;
+        rr_l = fmaf(ri, ri, rr_l);
+    }
+    float rr = cl_total(btotal(rr_l, sred), red.fslot, red.fbc, red.fpar);
+    const float target2 = (float)(itol * itol * (double)rr);
+    int it = 0;
+    status = kOk;
+    if (!(rr > 0.f)) return 0;
+    while (rr > target2) {
+        if (it >= max_iters) {
+            status = 1;
+            break;
+        }
+        __syncthreads();
+        CgProductEpi epi{q.q, q.p, 0.f};
+        bsell_spmv(q, q.p, nw, sbad, epi, s_lo, s_hi, r_lo, r_hi);
+        const float pq = cl_total(btotal(epi.acc, sred), red.fslot, red.fbc, red.fpar);
+        if (!(pq > 0.f)) {
+            status = isfinite(pq) ? -4 : -5;
+            break;
+        }
+        const float alpha = rr / pq;
+        float rn_l = 0.f;
+        for (int i = i4lo + tid; i < i4hi; i += bd) {
+            const float4 pv = p4[i], qv = q4[i];
+            float4 dv = d4[i], rv = r4[i];
+            dv.x = fmaf(alpha, pv.x, dv.x);
+            dv.y = fmaf(alpha, pv.y, dv.y);
+            dv.z = fmaf(alpha, pv.z, dv.z);
+            dv.w = fmaf(alpha, pv.w, dv.w);
+            rv.x = fmaf(-alpha, qv.x, rv.x);
+            rv.y = fmaf(-alpha, qv.y, rv.y);
+            rv.z = fmaf(-alpha, qv.z, rv.z);
+            rv.w = fmaf(-alpha, qv.w, rv.w);
+            d4[i] = dv;
+            r4[i] = rv;
+            rn_l = fmaf(rv.x, rv.x, rn_l);
+            rn_l = fmaf(rv.y, rv.y, rn_l);
+            rn_l = fmaf(rv.z, rv.z, rn_l);
+            rn_l = fmaf(rv.w, rv.w, rn_l);
+        }
+        for (int i = max(r_lo, 4 * i4hi) + tid; i < r_hi; i += bd) {
+            q.d[i] = fmaf(alpha, q.p[i], q.d[i]);
+            const float ri = fmaf(-alpha, q.q[i], q.r[i]);
+            q.r[i] = ri;
+            rn_l = fmaf(ri, ri, rn_l);
+        }
+        const float rr_new = cl_total(btotal(rn_l, sred), red.fslot, red.fbc, red.fpar);
+        ++it;
+        const float beta = rr_new / rr;
+        rr = rr_new;
+        for (int i = i4lo + tid; i < i4hi; i += bd) {
+            const float4 rv = r4[i];
+            float4 pv = p4[i];
+            pv.x = fmaf(beta, pv.x, rv.x);
+            pv.y = fmaf(beta, pv.y, rv.y);
+            pv.z = fmaf(beta, pv.z, rv.z);
+            pv.w = fmaf(beta, pv.w, rv.w);
+            p4[i] = pv;
+        }
+        for (int i = max(r_lo, 4 * i4hi) + tid; i < r_hi; i += bd) q.p[i] = fmaf(beta, q.p[i], q.r[i]);
+        cl_sync();    // the new direction is complete before the next product gathers it
+    }
+    __syncthreads();
+    return it;
+}
+
 // Shared-memory bytes of one block for sequences with at most s rows of
 // sketch and M history columns.
 size_t batch_smem_bytes(int s, int M) {
@@ -583,7 +757,7 @@ batched_step_kernel(BatchSeq* seqs, const int* __restrict__ order, int count, in
         if (m == 0) {
             for (int i = tid; i < n; i += bd) q.x[i] = 0.0;
         } else {
-            block_sketch(q, Wpriv, sks, Wsum, bad);
+            block_sketch(q, Wpriv, sks, Wsum, bad, 0, n);
             block_lsq(Wsum, s, M, m, (q.pushes - m) % M, 1e-12, ws, yphys, &rank, &rho);
             for (int i = tid; i < n; i += bd) {
                 const double* row = q.X + (size_t)i * q.ldx;
@@ -667,6 +841,159 @@ batched_step_kernel(BatchSeq* seqs, const int* __restrict__ order, int count, in
     }
 }
 
+// Shared-memory bytes of one CTA of the cluster form: the single-block layout
+// plus the cluster total of W.
+size_t batch_cluster_smem_bytes(int s, int M) {
+    const size_t base = batch_smem_bytes(s, M);
+    const int wsz = s * (M + 1);
+    const size_t d = (size_t)kSketchWarps * wsz + wsz + (2 * s * M + 3 * s + 5 * M) + kBatchMaxM;
+    const size_t guess = d * sizeof(double) + (size_t)kSketchWarps * 32 * kMaxZeta * sizeof(uint16_t);
+    const size_t need = guess + (size_t)wsz * sizeof(double);
+    return base > need ? base : need;
+}
+
+// One time step of every sequence, one cluster per sequence (see cl_sync and
+// cl_total above).  The steps and their arithmetic are those of
+// batched_step_kernel; rows are split over the cluster's CTAs and block
+// totals (the sketch W, norms, CG dot products) are summed over the cluster.
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
+batched_cluster_kernel(BatchSeq* seqs, const int* __restrict__ order, int count, int* queue,
+                       const BatchParams* __restrict__ prm) {
+    extern __shared__ double smem[];
+    __shared__ int s_take, s_idx;
+    __shared__ double dred[32];
+    __shared__ float fred[32];
+    __shared__ int sbad;
+    __shared__ double dslot[2], dbc;
+    __shared__ float fslot[2], fbc;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    const unsigned rk = cl_rank(), nr = cl_size();
+    const BatchParams P = *prm;
+    ClRed red{dslot, &dbc, fslot, &fbc, 0, 0};
+    for (;;) {
+        if (rk == 0 && tid == 0) s_take = atomicAdd(queue, 1);
+        if (tid == 0) sbad = 0;
+        cl_sync();
+        if (tid == 0) s_idx = cl_ld(&s_take, 0);
+        __syncthreads();
+        const int idx = s_idx;
+        if (idx >= count) break;
+        BatchSeq& gq = seqs[order[idx]];
+        const BatchSeq q = gq;
+        const int n = q.n, M = q.M, s = q.s;
+        const int m = min(q.pushes, M);
+        // This CTA's slices and rows.
+        const int ns = (n + 31) >> 5;
+        const int per = (ns + (int)nr - 1) / (int)nr;
+        const int s_lo = min(ns, (int)rk * per), s_hi = min(ns, s_lo + per);
+        const int r_lo = s_lo * 32, r_hi = min(n, s_hi * 32);
+        int bad = 0, rank = 0;
+        double rho = 0.0;
+        // 1. guess
+        const int ncol = M + 1, wsz = s * ncol;
+        double* Wpriv = smem;
+        double* Wsum = Wpriv + kSketchWarps * wsz;
+        double* ws = Wsum + wsz;
+        double* yphys = ws + (2 * s * M + 3 * s + 5 * M);
+        uint16_t* sks = reinterpret_cast<uint16_t*>(yphys + kBatchMaxM);
+        double* Wtot = reinterpret_cast<double*>(sks + kSketchWarps * 32 * kMaxZeta);
+        if (m == 0) {
+            for (int i = r_lo + tid; i < r_hi; i += bd) q.x[i] = 0.0;
+        } else {
+            block_sketch(q, Wpriv, sks, Wsum, bad, r_lo, r_hi);
+            cl_sync();
+            for (int i = tid; i < wsz; i += bd) {
+                double t = 0.0;
+                for (unsigned r = 0; r < nr; ++r) t += cl_ld(&Wsum[i], r);
+                Wtot[i] = t;
+            }
+            cl_sync();   // every CTA has read the partial sums before they are overwritten
+            block_lsq(Wtot, s, M, m, (q.pushes - m) % M, 1e-12, ws, yphys, &rank, &rho);
+            for (int i = r_lo + tid; i < r_hi; i += bd) {
+                const double* row = q.X + (size_t)i * q.ldx;
+                double acc = 0.0;
+                for (int k = 0; k < M; ++k) acc = fma(row[k], yphys[k], acc);
+                q.x[i] = acc;
+            }
+        }
+        // This step's values into the SELL copy (FP32), own rows.
+        for (int i = r_lo + tid; i < r_hi; i += bd) {
+            const int e0 = q.rowptr[i], e1 = q.rowptr[i + 1];
+            float* dst = q.sval + q.soff[i >> 5] + (i & 31);
+            for (int e = e0; e < e1; ++e) dst[(e - e0) * 32] = (float)q.val[e];
+        }
+        __syncthreads();
+        double* stage_d = smem;
+        const int lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+        // 2. FP64 refinement around FP32 CG (the x of other CTAs is complete
+        // after the cluster total below)
+        double bb_l = 0.0;
+        for (int i = r_lo + tid; i < r_hi; i += bd) bb_l = fma(q.b[i], q.b[i], bb_l);
+        const double bnorm = sqrt(cl_total(btotal(bb_l, dred), red.dslot, red.dbc, red.dpar));
+        const double target = P.tol * bnorm;
+        int total = 0, nref = 0, status = kOk;
+        double rn = 0.0, first = 0.0;
+        for (int pass = 0;; ++pass) {
+            double rr_l = 0.0;
+            for (int r0 = r_lo + warp * 32; r0 < r_hi; r0 += nw * 32) {
+                const double ax = warp_tile_spmv<double, double, double, true>(
+                    q.rowptr, q.colind, q.val, q.x, n, q.nnz, r0, stage_d + warp * kTileChunks * 32,
+                    &sbad);
+                const int i = r0 + lane;
+                if (i < r_hi) {
+                    const double ri = q.b[i] - ax;
+                    q.r[i] = (float)ri;
+                    rr_l = fma(ri, ri, rr_l);
+                }
+            }
+            rn = sqrt(cl_total(btotal(rr_l, dred), red.dslot, red.dbc, red.dpar));
+            if (pass == 0) first = bnorm > 0.0 ? rn / bnorm : rn;
+            if (!isfinite(rn)) {
+                status = -5;
+                break;
+            }
+            if (rn <= target) break;
+            if (total >= P.max_iters || nref >= 100) {
+                status = 1;
+                break;
+            }
+            const double itol = fmax(P.inner_tol, kTheta * target / rn);
+            int st = kOk;
+            total += cluster_cg32(q, itol, P.max_iters - total, fred, &sbad, s_lo, s_hi, r_lo, r_hi,
+                                  red, st);
+            ++nref;
+            if (st < 0) {
+                status = st;
+                break;
+            }
+            for (int i = r_lo + tid; i < r_hi; i += bd) q.x[i] += (double)q.d[i];
+            cl_sync();   // x complete before the next residual gathers it
+        }
+        // 3. push (own rows)
+        if (P.commit && status >= 0) {
+            const int slot = q.pushes % M;
+            for (int i = r_lo + tid; i < r_hi; i += bd) q.X[(size_t)i * q.ldx + slot] = q.x[i];
+        }
+        if (bad) atomicOr(&sbad, 1);
+        __syncthreads();
+        const double anybad = cl_total((double)(sbad != 0), red.dslot, red.dbc, red.dpar);
+        if (rk == 0 && tid == 0) {
+            if (P.commit && status >= 0) gq.pushes = q.pushes + 1;
+            gq.iters = total;
+            gq.refinements = nref;
+            gq.status = anybad > 0.0 ? -1 : status;
+            gq.history_cols = m;
+            gq.rank = rank;
+            gq.guess_relres = first;
+            gq.sketch_resid = rho;
+            gq.final_relres = bnorm > 0.0 ? rn / bnorm : rn;
+        }
+        __syncthreads();
+    }
+    cl_sync();   // no CTA leaves while another may still read its shared memory
+}
+
 // The instantiation whose register budget fits `threads` x `blocks_per_sm`
 // threads on one SM.
 using StepKernel = void (*)(BatchSeq*, const int*, int, int*, const BatchParams*);
@@ -674,6 +1001,11 @@ StepKernel step_kernel_for(int threads, int blocks_per_sm) {
     const int t = threads * blocks_per_sm;
     return t <= 256 ? batched_step_kernel<256> : t <= 512 ? batched_step_kernel<512>
                                                            : batched_step_kernel<1024>;
+}
+
+StepKernel cluster_kernel_for(int threads) {
+    return threads <= 256 ? batched_cluster_kernel<256> : threads <= 512 ? batched_cluster_kernel<512>
+                                                                        : batched_cluster_kernel<1024>;
 }
 
 __global__ void batch_push_kernel(const double* __restrict__ x, int n, double* X, int ldx, int slot) {
@@ -698,6 +1030,8 @@ struct seq_batch {
     int* d_queue = nullptr;
     std::vector<void*> allocs;
     int threads = 512, blocks_per_sm = 1, order_kind = 0;  // 0: largest first, 1: given order
+    int cluster = 1;                      // CTAs per sequence (1: one block per sequence)
+    size_t smem_cluster = 0;
     int autopush = 1;
     cudaGraphExec_t graph = nullptr;
     size_t smem = 0;
@@ -728,23 +1062,78 @@ int batch_order(seq_batch* bt) {
     return cudaStreamSynchronize(bt->stream) == cudaSuccess ? SEQ_OK : SEQ_ECUDA;
 }
 
+// Launch configuration of the cluster form: clusters of bt->cluster CTAs, one
+// CTA per SM, as many clusters as fit at once.  Returns the grid (0: none fits).
+int cluster_grid(seq_batch* bt, StepKernel kern) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = bt->cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(bt->cluster * bt->sms);
+    cfg.blockDim = dim3(bt->threads);
+    cfg.dynamicSmemBytes = bt->smem_cluster;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, (const void*)kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    // one CTA per SM
+    nc = std::min(nc, bt->sms / bt->cluster);
+    return nc * bt->cluster;
+}
+
 int batch_capture(seq_batch* bt) {
     if (bt->graph) {
         cudaGraphExecDestroy(bt->graph);
         bt->graph = nullptr;
     }
-    const StepKernel kern = step_kernel_for(bt->threads, bt->blocks_per_sm);
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bt->smem) != cudaSuccess) {
+    const bool cl = bt->cluster > 1;
+    const StepKernel kern = cl ? cluster_kernel_for(bt->threads)
+                               : step_kernel_for(bt->threads, bt->blocks_per_sm);
+    const size_t smem = cl ? bt->smem_cluster : bt->smem;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
         cudaGetLastError();
         return SEQ_ECUDA;
+    }
+    int grid = bt->sms * bt->blocks_per_sm;
+    if (cl) {
+        if (bt->cluster > 8 &&
+            cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return SEQ_ECUDA;
+        }
+        grid = cluster_grid(bt, kern);
+        if (grid <= 0) return SEQ_ECUDA;
     }
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return SEQ_ECUDA;
     cudaMemsetAsync(bt->d_queue, 0, sizeof(int), bt->cap);
-    kern<<<bt->sms * bt->blocks_per_sm, bt->threads, bt->smem, bt->cap>>>(
-        bt->d_seqs, bt->d_order, bt->count, bt->d_queue, bt->d_prm);
+    if (cl) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = bt->cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(bt->threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = bt->cap;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, kern, bt->d_seqs, (const int*)bt->d_order, bt->count, bt->d_queue,
+                           (const BatchParams*)bt->d_prm);
+    } else {
+        kern<<<grid, bt->threads, smem, bt->cap>>>(bt->d_seqs, bt->d_order, bt->count, bt->d_queue,
+                                                   bt->d_prm);
+    }
     if (cudaStreamEndCapture(bt->cap, &g) != cudaSuccess) {
         cudaGetLastError();
         return SEQ_ECUDA;
@@ -804,6 +1193,7 @@ int seq_batch_create(int32_t count, const seq_csr* patterns, int32_t M, int32_t 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&bt->sms, cudaDevAttrMultiProcessorCount, dev);
     bt->smem = batch_smem_bytes(s, M);
+    bt->smem_cluster = batch_cluster_smem_bytes(s, M);
     bt->host.resize(count);
     int rc = SEQ_OK;
     const int ldx = (M + 1) & ~1;
@@ -938,40 +1328,50 @@ int seq_batch_autotune(seq_batch* bt, const double* const* values, const double*
                        double* const* x, double tol, int32_t* chosen) {
     if (!bt || !values || !b || !x || !(tol > 0)) return SEQ_EINVAL;
     const int thr[3] = {256, 512, 1024};
+    const int cls[3] = {1, 4, 8};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
     int bt_thr = bt->threads, bt_bps = bt->blocks_per_sm, bt_ord = bt->order_kind;
-    for (int oi = 0; oi < 2; ++oi) {
-        for (int ti = 0; ti < 3; ++ti) {
-            for (int bps = 1; bps <= 2; ++bps) {
-                if ((size_t)bps * bt->smem > 220 * 1024) continue;
-                int nb = 0;
-                bt->threads = thr[ti];
-                bt->blocks_per_sm = bps;
-                bt->order_kind = oi;
-                const StepKernel kern = step_kernel_for(thr[ti], bps);
-                if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bt->smem) != cudaSuccess ||
-                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, thr[ti],
-                                                                  bt->smem) != cudaSuccess ||
-                    nb < bps) {
-                    cudaGetLastError();
-                    continue;
-                }
-                if (batch_order(bt) || batch_capture(bt)) continue;
-                cudaEventRecord(e0, bt->stream);
-                const int rc = batch_run(bt, values, b, x, tol, 0);
-                cudaEventRecord(e1, bt->stream);
-                cudaEventSynchronize(e1);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rc == SEQ_OK && ms < best) {
-                    best = ms;
-                    bt_thr = thr[ti];
-                    bt_bps = bps;
-                    bt_ord = oi;
+    int bt_cl = bt->cluster;
+    for (int ci = 0; ci < 3; ++ci) {
+        const int cl = cls[ci];
+        for (int oi = 0; oi < 2; ++oi) {
+            for (int ti = 0; ti < 3; ++ti) {
+                for (int bps = 1; bps <= 2; ++bps) {
+                    if (cl > 1 && (bps > 1 || thr[ti] < 512)) continue;
+                    const size_t smem = cl > 1 ? bt->smem_cluster : bt->smem;
+                    if ((size_t)bps * smem > 220 * 1024) continue;
+                    bt->threads = thr[ti];
+                    bt->blocks_per_sm = bps;
+                    bt->order_kind = oi;
+                    bt->cluster = cl;
+                    const StepKernel kern =
+                        cl > 1 ? cluster_kernel_for(thr[ti]) : step_kernel_for(thr[ti], bps);
+                    int nb = 0;
+                    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem) != cudaSuccess ||
+                        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, thr[ti], smem) !=
+                            cudaSuccess ||
+                        nb < bps || (cl > 1 && cluster_grid(bt, kern) <= 0)) {
+                        cudaGetLastError();
+                        continue;
+                    }
+                    if (batch_order(bt) || batch_capture(bt)) continue;
+                    cudaEventRecord(e0, bt->stream);
+                    const int rc = batch_run(bt, values, b, x, tol, 0);
+                    cudaEventRecord(e1, bt->stream);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rc == SEQ_OK && ms < best) {
+                        best = ms;
+                        bt_thr = thr[ti];
+                        bt_bps = bps;
+                        bt_ord = oi;
+                        bt_cl = cl;
+                    }
                 }
             }
         }
@@ -981,6 +1381,7 @@ int seq_batch_autotune(seq_batch* bt, const double* const* values, const double*
     bt->threads = bt_thr;
     bt->blocks_per_sm = bt_bps;
     bt->order_kind = bt_ord;
+    bt->cluster = bt_cl;
     int rc = batch_order(bt);
     if (!rc) rc = batch_capture(bt);
     if (chosen) {
@@ -1017,9 +1418,32 @@ int seq_batch_set_schedule(seq_batch* bt, int32_t threads, int32_t blocks_per_sm
     bt->threads = threads;
     bt->blocks_per_sm = blocks_per_sm;
     bt->order_kind = order_kind;
+    bt->cluster = 1;
     int rc = batch_order(bt);
     if (!rc) rc = batch_capture(bt);
     return rc;
+}
+
+int seq_batch_set_cluster(seq_batch* bt, int32_t ctas, int32_t threads, int32_t order_kind) {
+    if (!bt || (ctas != 1 && ctas != 2 && ctas != 4 && ctas != 8) ||
+        (threads != 256 && threads != 512 && threads != 1024) || order_kind < 0 || order_kind > 1)
+        return SEQ_EINVAL;
+    bt->cluster = ctas;
+    bt->threads = threads;
+    bt->blocks_per_sm = 1;
+    bt->order_kind = order_kind;
+    int rc = batch_order(bt);
+    if (!rc) rc = batch_capture(bt);
+    return rc;
+}
+
+int seq_batch_get_schedule(const seq_batch* bt, int32_t* out) {
+    if (!bt || !out) return SEQ_EINVAL;
+    out[0] = bt->threads;
+    out[1] = bt->blocks_per_sm;
+    out[2] = bt->order_kind;
+    out[3] = bt->cluster;
+    return SEQ_OK;
 }
 
 }  // extern "C"

@@ -195,7 +195,9 @@ __device__ __forceinline__ void block_rows(int n, int nblk, int blk, int& lo, in
 // otherwise chunk by chunk.  Products are staged in shared memory (sprod:
 // kTileChunks * 32 entries per warp) and each lane sums the entries of its own
 // row in CSR order.  Column indices outside [0, n) contribute 0 and raise *bad.
-template <typename Acc, typename VT, typename XT>
+// XL2: read x through L2 only (x is written by other thread blocks of the
+// same launch).
+template <typename Acc, typename VT, typename XT, bool XL2 = false>
 __device__ __forceinline__ Acc warp_tile_spmv(const int* __restrict__ rowptr,
                                               const int* __restrict__ colind,
                                               const VT* __restrict__ val,
@@ -234,7 +236,7 @@ __device__ __forceinline__ Acc warp_tile_spmv(const int* __restrict__ rowptr,
             Acc prod = 0;
             if (e < e1) {
                 if ((unsigned)cc[q] < (unsigned)n)
-                    prod = (Acc)vv[q] * (Acc)x[cc[q]];
+                    prod = (Acc)vv[q] * (Acc)(XL2 ? __ldcg(x + cc[q]) : x[cc[q]]);
                 else
                     flag = 1;
             }
@@ -251,7 +253,7 @@ __device__ __forceinline__ Acc warp_tile_spmv(const int* __restrict__ rowptr,
             if (e < e1) {
                 const int c = __ldg(colind + e);
                 if ((unsigned)c < (unsigned)n)
-                    prod = (Acc)__ldg(val + e) * (Acc)x[c];
+                    prod = (Acc)__ldg(val + e) * (Acc)(XL2 ? __ldcg(x + c) : x[c]);
                 else
                     flag = 1;
             }

@@ -49,10 +49,16 @@ def _inputs(ps, i):
     return vals, bs, As, bnp
 
 
-def test_batched_matches_oracle_with_shared_history():
+@pytest.mark.parametrize("ctas", [1, 2, 8])
+def test_batched_matches_oracle_with_shared_history(ctas):
+    """ctas > 1: each sequence taken by a cluster of that many CTAs (the
+    1 x 1 and 6 x 6 systems leave most CTAs of the cluster without rows)."""
     ps = _params()
     M, s, seed, tol = 6, 24, 77, 1e-8
     bt = _batch(ps, M, s, seed)
+    if ctas > 1:
+        bt.set_cluster(ctas)
+        assert bt.schedule()["ctas_per_sequence"] == ctas
     bt.set_autopush(False)
     S = [sketch.sparse_sign_matrix(p.n, s, 8, seed + k) for k, p in enumerate(ps)]
     hists = [method.History(p.n, M) for p in ps]
@@ -73,10 +79,13 @@ def test_batched_matches_oracle_with_shared_history():
     bt.close()
 
 
-def test_batched_primed_guess_parity():
+@pytest.mark.parametrize("ctas", [1, 8])
+def test_batched_primed_guess_parity(ctas):
     ps = _params()
     M, s, seed = 5, 20, 3
     bt = _batch(ps, M, s, seed)
+    if ctas > 1:
+        bt.set_cluster(ctas, threads=512)
     S = [sketch.sparse_sign_matrix(p.n, s, 8, seed + k) for k, p in enumerate(ps)]
     rng = np.random.default_rng(0)
     hists = []
@@ -106,16 +115,28 @@ def test_batched_autotune_and_schedules():
     xs = [torch.empty(p.n, dtype=torch.float64, device=DEV) for p in ps]
     chosen = bt.autotune(vals, bs, xs, 1e-8)
     assert chosen["threads"] in (256, 512, 1024) and chosen["blocks_per_sm"] in (1, 2)
+    assert chosen["ctas_per_sequence"] in (1, 4, 8)
     for sched in [(256, 1, 1), (256, 2, 0), (512, 1, 0)]:
         bt.set_schedule(*sched)
+        assert bt.schedule()["ctas_per_sequence"] == 1
         infos = bt.step(vals, bs, xs, 1e-8)
         for k in range(len(ps)):
             assert infos[k]["status"] == 0
             assert method.relres(As[k], bnp[k], xs[k].cpu().numpy()) <= 1e-8 * (1 + 1e-9)
+    for ctas, threads, order in [(4, 512, 1), (8, 1024, 0)]:
+        bt.set_cluster(ctas, threads, order)
+        infos = bt.step(vals, bs, xs, 1e-8)
+        for k in range(len(ps)):
+            assert infos[k]["status"] == 0
+            assert method.relres(As[k], bnp[k], xs[k].cpu().numpy()) <= 1e-8 * (1 + 1e-9)
+    import paper_2309_02156_gb300 as sa
+    with pytest.raises(sa.SeqError):
+        bt.set_cluster(3)
     bt.close()
 
 
-def test_batched_reports_bad_column_index():
+@pytest.mark.parametrize("ctas", [1, 4])
+def test_batched_reports_bad_column_index(ctas):
     import paper_2309_02156_gb300 as sa
     ps = _params()[:3]
     pats = []
@@ -126,6 +147,8 @@ def test_batched_reports_bad_column_index():
             colind[3] = p.n + 7
         pats.append((torch.from_numpy(rowptr).to(DEV), torch.from_numpy(colind).to(DEV)))
     bt = sa.Batch(pats, M=4, s=16)
+    if ctas > 1:
+        bt.set_cluster(ctas)
     vals, bs, As, bnp = _inputs(ps, 0)
     xs = [torch.empty(p.n, dtype=torch.float64, device=DEV) for p in ps]
     with pytest.raises(sa.SeqError):
@@ -163,7 +186,8 @@ def test_full_size_batch_sampled_residuals():
     bt.close()
 
 
-def test_full_size_batch_guess_parity():
+@pytest.mark.parametrize("ctas", [1, 8])
+def test_full_size_batch_guess_parity(ctas):
     """The 512-sequence workload at its real shape (grid sides 48..384, M = 12,
     s = 48, zeta = 8, sketch seed + k per sequence): every history is primed
     with 12 + 3 seeded Gaussian columns (the ring wraps), then one step.  For
@@ -179,6 +203,8 @@ def test_full_size_batch_guess_parity():
     pats = [(torch.from_numpy(rp).to(DEV), torch.from_numpy(ci).to(DEV)) for rp, ci in gen.patterns]
     M, s = 12, 48
     bt = sa.Batch(pats, M=M, s=s, zeta=8, seed=seed, max_iters=200000)
+    if ctas > 1:
+        bt.set_cluster(ctas)
     ns = np.array([p.n for p in ps])
     sample = sorted({int(np.argmax(ns)), int(np.argmin(ns))} | set(range(0, 512, 64)))
     hists = {}
