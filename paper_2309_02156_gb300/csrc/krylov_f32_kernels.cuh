@@ -40,10 +40,14 @@ template <> struct F32x<4> {
         *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
     }
 };
+// Per thread and iteration about 64 floats (256 bytes) in flight: one block
+// of 12 warps per SM (the partial sums of NK columns need the registers) has
+// to hide the memory latency with bytes per thread, not with warps.
 template <int NK> struct F32Shape {
-    static constexpr int VW = NK >= 32 ? 1 : (NK >= 12 ? 2 : 4);
+    static constexpr int VW = NK >= 32 ? 1 : (NK >= 20 ? 2 : 4);
     static constexpr int per = (NK + 1) * VW;                 // floats loaded per vector
-    static constexpr int U = per >= 32 ? 1 : (32 + per - 1) / per;
+    static constexpr int U0 = per >= 64 ? 1 : (64 + per - 1) / per;
+    static constexpr int U = (U0 > 1 && U0 * per > 96) ? U0 - 1 : U0;
 };
 
 // MODE 0: part[k] = sum v_k w (first CGS pass, h1).
