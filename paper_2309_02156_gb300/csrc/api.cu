@@ -515,7 +515,7 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
     ok = ok && cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) == cudaSuccess;
     ok = ok && cudaMalloc(&ctx->X, elh * (size_t)n * ctx->ldx) == cudaSuccess;
     ok = ok && cudaMemsetAsync(ctx->X, 0, elh * (size_t)n * ctx->ldx, ctx->stream) == cudaSuccess;
-    ctx->sk_nblk = sketch_grid(n);
+    ctx->sk_nblk = sketch_grid(n, s, M);
     ok = ok && cudaMalloc(&ctx->sk_partial, sizeof(double) * sketch_partial_doubles(n, s, M)) == cudaSuccess;
     ok = ok && cudaMalloc(&ctx->W, sizeof(double) * (s * (M + 1) + 1)) == cudaSuccess;
     ok = ok && cudaMalloc(&ctx->lsq, sizeof(LsqOut)) == cudaSuccess;

@@ -9,7 +9,7 @@
 namespace sa {
 
 // sketch.cu
-int sketch_grid(int n);
+int sketch_grid(int n, int s, int M);   // blocks of launch_sketch_* for up to M columns
 size_t sketch_partial_doubles(int n, int s, int M);   // partial buffer of launch_sketch_*
 void launch_sketch_columns(int n, int s, int zeta, uint64_t seed, uint16_t* packed,
                            int32_t* rows, int8_t* signs, cudaStream_t st);

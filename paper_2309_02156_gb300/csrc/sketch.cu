@@ -13,6 +13,8 @@
 // of row i at X[i * ldx + k]), so the M values a CSR neighbour contributes are
 // one contiguous read.  W is row-major s x (M + 1): W[q * (M+1) + k] for
 // history slot k < M and W[q * (M+1) + M] for b.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -69,16 +71,30 @@ void launch_sketch_columns(int n, int s, int zeta, uint64_t seed, uint16_t* pack
 
 namespace {
 
-constexpr int kSkWarps = 4;          // warps per block of the sketch kernel
-constexpr int kSkStage = 256;        // CSR entries of a 32-row tile staged in shared memory
+constexpr int kSkTeamWarps = 4;      // warps of a team (one 32-row tile at a time)
+constexpr int kSkTeamThreads = kSkTeamWarps * 32;
+constexpr int kSkMaxTeams = 8;       // teams per block (one block per SM)
+constexpr int kSkRowsPerWarp = 8;    // rows of a tile per warp
+constexpr int kSkWarpStage = 64;     // CSR entries of a warp's rows staged in shared memory
 constexpr int kSkFastRow = 5;        // rows up to this many entries take the unrolled path
+constexpr int kSkU = 2;              // product entries per lane in flight (32 warps per SM: 64 registers)
 constexpr int kSkValueBits = 52;     // |quantised value| < 2^52 (the bits of an FP64 mantissa)
+constexpr int kSkMaxTiles = 33;      // tiles per team: <= 33 * 32 terms per accumulator, < 2^63
+constexpr size_t kSkSmemCap = 220 * 1024;
 
-// Bytes of one warp's shared region: integer accumulator (s x ncol), the
-// tile's Y (32 x ncol doubles), staged CSR values and columns, sketch entries.
-__host__ __device__ inline size_t sketch_warp_bytes(int s, int ncol) {
-    return 8 * (size_t)s * ncol + 8 * 32 * (size_t)ncol + 12 * (size_t)kSkStage +
-           2 * 32 * (size_t)kMaxZeta;
+// Bytes of one team's shared region: integer accumulator (s x ncol), the
+// tile's Y (32 x ncol doubles, quantised in place), per warp the staged CSR
+// values (8 bytes each) and columns, the tile's sketch entries, and per
+// column the fixed-point exponent and status.
+__host__ __device__ inline size_t sketch_team_bytes(int s, int ncol) {
+    return 8 * (size_t)s * ncol + 8 * 32 * (size_t)ncol +
+           (size_t)kSkTeamWarps * kSkWarpStage * 12 + 2 * 32 * (size_t)kMaxZeta +
+           8 * (size_t)ncol;
+}
+
+int sketch_teams(int s, int ncol) {
+    const size_t t = kSkSmemCap / sketch_team_bytes(s, ncol);
+    return t < 1 ? 1 : (t > (size_t)kSkMaxTeams ? kSkMaxTeams : (int)t);
 }
 
 // y (finite) as a fixed-point integer with F fraction bits, rounded to
@@ -110,154 +126,137 @@ __device__ __forceinline__ long long shift_round(long long w, int d) {
     return (w + (1ll << (d - 1))) >> d;
 }
 
-}  // namespace
-
-// W += S[:, r] Yq[r, :] for the tile's rows (integers; Wi and Yq row-major
-// with ncol columns).  The zeta x ncol (sketch entry, column) pairs of a row
-// are spread over the warp's lanes, P per lane; the pairs of one row hit
-// distinct accumulators, so a lane reads all of its P, then writes them back,
-// and the warp moves to the next row together.
-template <int P>
-__device__ __forceinline__ void scatter_rows(long long* Wi, const long long* Yq,
-                                             const uint16_t* skS, int ncol, int zeta, int cnt) {
-    const int lane = threadIdx.x & 31;
-    int zz[P], kk[P];
-    bool ok[P];
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-        const int p = lane + 32 * i;
-        ok[i] = p < zeta * ncol;
-        zz[i] = ok[i] ? p / ncol : 0;
-        kk[i] = ok[i] ? p - zz[i] * ncol : 0;
-    }
-    for (int r = 0; r < cnt; ++r) {
-        int off[P];
-        long long cur[P];
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-            if (ok[i]) {
-                const unsigned e = skS[r * kMaxZeta + zz[i]];
-                const long long v = Yq[r * ncol + kk[i]];
-                off[i] = (int)(e & 0x7fff) * ncol + kk[i];
-                cur[i] = Wi[off[i]] + ((e & 0x8000) ? -v : v);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < P; ++i)
-            if (ok[i]) Wi[off[i]] = cur[i];
-        __syncwarp();
-    }
+__device__ __forceinline__ void team_sync(int team) {
+    asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(kSkTeamThreads) : "memory");
 }
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+}  // namespace
 
 // W = S [A X | b] in one pass over A and X, with S generated on the fly.
 //
-// The grid's warps take 32-row tiles in turn.  For a tile it stages the rows' CSR entries,
-// generates the rows' sketch columns (zeta entries each), and forms
-// Y = [A X | b] with the 32 x M products spread over all 32 lanes (lane l
-// computes entries l, l + 32, ... in row-major order, several at once).  The
-// scatter W += S[:, r] Y_r then runs in exact integer arithmetic: lane k turns
-// column k of the tile into fixed-point integers (a per-column scale with
-// values below 2^52, chosen from the running maximum of the column; when a
-// larger value arrives the accumulated column is shifted to the new scale),
-// and the warp adds +-v into its private 64-bit accumulator at the zeta
-// sketch rows of each row.  Integer sums do not depend on their order, so the result is
-// deterministic, and the sketch's zeta (M+1) additions per row leave the
-// FP64 pipe (the limiting unit of this GPU for FP64 work) to the products;
-// the additions of one row are spread over all lanes (scatter_rows).
-// At the end the block's warps are converted back to FP64 and summed in warp
+// A block (one per SM) runs up to eight teams of four warps; each team takes
+// 32-row tiles in turn (tiles are dealt to the grid's teams cyclically, so
+// that at any time the whole GPU works on one window of consecutive rows and
+// the X rows a stencil shares between rows far apart, r and r +- the grid
+// side, are still in L2 when their second reader comes).  For a tile:
+//  (a) warp w takes rows 8w .. 8w+7: their CSR entries (staged in shared
+//      memory) and sketch columns (zeta entries each, generated from the
+//      counters), and b;
+//  (b) it forms Y = A X on those rows, the 8 x M products spread over its
+//      lanes, four at a time;
+//  (c) the warps split the M + 1 columns: for each, the tile's largest
+//      magnitude sets a fixed-point scale (values below 2^52, chosen from the
+//      running maximum of the column; when a larger value arrives the
+//      accumulated column is shifted to the new scale) and the column is
+//      turned into integers;
+//  (d) the team adds +-v into its 64-bit accumulator at the zeta sketch rows
+//      of each row (shared-memory atomics: integer sums do not depend on
+//      their order, so the result is deterministic), leaving the FP64 pipe
+//      (the limiting unit of this GPU for FP64 work) to the products.
+// At the end the block's teams are converted back to FP64 and summed in team
 // order into partial[blk] (s (M+1) values); a column with a non-finite value
-// becomes NaN.  A warp takes at most 33 tiles (grid sizing), so an
+// becomes NaN.  A team takes at most kSkMaxTiles tiles (grid sizing), so an
 // accumulator holds at most 1056 terms below 2^52 and stays below 2^63.
-template <typename T, typename XT, int P>
-__global__ void __launch_bounds__(kSkWarps * 32)
+template <typename T, typename XT>
+__global__ void __launch_bounds__(kSkMaxTeams * kSkTeamThreads, 1)
 sketch_block_kernel(const int* __restrict__ rowptr, const int* __restrict__ colind,
                     const T* __restrict__ val, const XT* __restrict__ X, int ldx,
                     const double* __restrict__ b, int n, int nnz, int M, int s, int zeta,
                     uint64_t seed, double* __restrict__ partial, int* bad) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int Fsh[kSkWarps][32];
-    __shared__ int stat[kSkWarps][32];      // bit 0: column has values, bit 1: non-finite
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nteams = blockDim.x / kSkTeamThreads;
+    const int team = threadIdx.x / kSkTeamThreads, tt = threadIdx.x % kSkTeamThreads;
+    const int tw = tt >> 5, lane = threadIdx.x & 31;
     const int ncol = M + 1, wsz = s * ncol;
-    unsigned char* base_ptr = smem_raw + (size_t)warp * sketch_warp_bytes(s, ncol);
+    const size_t tb = sketch_team_bytes(s, ncol);
+    unsigned char* base_ptr = smem_raw + (size_t)team * tb;
     long long* Wi = reinterpret_cast<long long*>(base_ptr);
     double* Ys = reinterpret_cast<double*>(Wi + wsz);
-    T* valS = reinterpret_cast<T*>(Ys + 32 * ncol);
-    int* colS = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(valS) + 8 * kSkStage);
-    uint16_t* skS = reinterpret_cast<uint16_t*>(colS + kSkStage);
-    for (int i = lane; i < wsz; i += 32) Wi[i] = 0;
-    int F = 0, has = 0, nonfinite = 0, flag = 0;
-    // This lane's first product entry in the row-major 32 x M tile, and the
-    // step to the next one (32 entries further).
-    const int r_first = lane / M, k_first = lane - (lane / M) * M;
-    const int dr = 32 / M, dk = 32 - (32 / M) * M;
-    // Tiles are dealt to the grid's warps cyclically, so that at any time the
-    // whole GPU works on one window of consecutive rows and the X rows a
-    // stencil shares between rows far apart (r and r +- the grid side) are
-    // still in L2 when their second reader comes.
-    const int hi = n;
+    unsigned char* stg = reinterpret_cast<unsigned char*>(Ys + 32 * ncol);
+    T* valW = reinterpret_cast<T*>(stg + (size_t)tw * kSkWarpStage * 8);
+    int* colW = reinterpret_cast<int*>(stg + (size_t)kSkTeamWarps * kSkWarpStage * 8) +
+                tw * kSkWarpStage;
+    uint16_t* skS = reinterpret_cast<uint16_t*>(stg + (size_t)kSkTeamWarps * kSkWarpStage * 12);
+    int* Fk = reinterpret_cast<int*>(skS + 32 * kMaxZeta);
+    int* stk = Fk + ncol;                    // bit 0: column has values, bit 1: non-finite
+    for (int i = tt; i < wsz; i += kSkTeamThreads) Wi[i] = 0;
+    for (int k = tt; k < ncol; k += kSkTeamThreads) {
+        Fk[k] = 0;
+        stk[k] = 0;
+    }
+    team_sync(team);
+    int flag = 0;
+    const int nent = kSkRowsPerWarp * M;
     const long long ntiles = ((long long)n + 31) / 32;
-    for (long long tile = (long long)blockIdx.x * kSkWarps + warp; tile < ntiles;
-         tile += (long long)gridDim.x * kSkWarps) {
-        const int base = (int)(tile * 32);
-        const int cnt = min(32, hi - base);
+    for (long long tile = (long long)blockIdx.x * nteams + team; tile < ntiles;
+         tile += (long long)gridDim.x * nteams) {
+        const int row0 = (int)(tile * 32);
+        const int cnt = min(32, n - row0);
+        const int r0 = row0 + tw * kSkRowsPerWarp;
+        const int wcnt = max(0, min(kSkRowsPerWarp, n - r0));
+        // (a) this warp's rows
         int rs = 0, re = 0;
-        if (lane < cnt) {
-            rs = max(0, min(__ldg(rowptr + base + lane), nnz));
-            re = max(rs, min(__ldg(rowptr + base + lane + 1), nnz));
-            sketch_column_packed(base + lane, s, zeta, seed, skS + lane * kMaxZeta);
+        if (lane < wcnt) {
+            rs = max(0, min(__ldg(rowptr + r0 + lane), nnz));
+            re = max(rs, min(__ldg(rowptr + r0 + lane + 1), nnz));
+            sketch_column_packed(r0 + lane, s, zeta, seed,
+                                 skS + (tw * kSkRowsPerWarp + lane) * kMaxZeta);
         }
         const int e0 = __shfl_sync(0xffffffffu, rs, 0);
-        const int e1 = max(e0, __shfl_sync(0xffffffffu, re, cnt - 1));
-        const bool staged = e1 - e0 <= kSkStage;
+        const int e1 = max(e0, __shfl_sync(0xffffffffu, re, max(wcnt - 1, 0)));
+        const bool staged = e1 - e0 <= kSkWarpStage;
         if (staged) {
             for (int e = e0 + lane; e < e1; e += 32) {
-                colS[e - e0] = __ldg(colind + e);
-                valS[e - e0] = __ldg(val + e);
+                colW[e - e0] = __ldg(colind + e);
+                valW[e - e0] = __ldg(val + e);
             }
         }
-        if (lane < 32) Ys[lane * ncol + M] = lane < cnt ? __ldg(b + base + lane) : 0.0;
+        if (lane < kSkRowsPerWarp)
+            Ys[(tw * kSkRowsPerWarp + lane) * ncol + M] = lane < wcnt ? __ldg(b + r0 + lane) : 0.0;
         __syncwarp();
-        // Y[:, 0:M] = A X for the tile's rows, four entries per lane at a time.
-        int r = r_first, k = k_first;
-        for (int j = 0; j < M; j += 4) {
-            int rr[4], kk[4], st[4], ln[4];
-            T acc[4];
+        // (b) Y[:, 0:M] = A X on the warp's rows, kSkU entries per lane at a time
+        // (the loop is uniform over the warp: the shuffles need every lane)
+        for (int eb0 = 0; eb0 < nent; eb0 += kSkU * 32) {
+            const int eb = eb0 + lane;
+            int rr[kSkU], kk[kSkU], st[kSkU], ln[kSkU];
+            T acc[kSkU];
             int maxlen = 0;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kSkU; ++u) {
+                const int e = eb + 32 * u;
+                const bool in = e < nent;
+                const int r = in ? e / M : 0;
                 rr[u] = r;
-                kk[u] = k;
-                const int srow = min(r, 31);
-                const int a = __shfl_sync(0xffffffffu, rs, srow);
-                const int z = __shfl_sync(0xffffffffu, re, srow);
-                const bool live = (j + u < M) && r < cnt;
+                kk[u] = in ? e - r * M : 0;
+                const int a = __shfl_sync(0xffffffffu, rs, r);
+                const int z = __shfl_sync(0xffffffffu, re, r);
                 st[u] = a;
-                ln[u] = live ? z - a : 0;
+                ln[u] = (in && r < wcnt) ? z - a : 0;
                 maxlen = max(maxlen, ln[u]);
                 acc[u] = 0;
-                k += dk;
-                r += dr;
-                if (k >= M) {
-                    k -= M;
-                    r += 1;
-                }
             }
             if (maxlen <= kSkFastRow) {
-                // Rows of at most kSkFastRow entries: every load of the four
-                // entries is issued before the first product.
-                T xv[4][kSkFastRow], vv[4][kSkFastRow];
+                T xv[kSkU][kSkFastRow], vv[kSkU][kSkFastRow];
 #pragma unroll
                 for (int t = 0; t < kSkFastRow; ++t) {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
+                    for (int u = 0; u < kSkU; ++u) {
                         xv[u][t] = 0;
                         vv[u][t] = 0;
                         if (t < ln[u]) {
                             const int e = st[u] + t;
-                            const int c = staged ? colS[e - e0] : __ldg(colind + e);
+                            const int c = staged ? colW[e - e0] : __ldg(colind + e);
                             if ((unsigned)c < (unsigned)n) {
-                                vv[u][t] = staged ? valS[e - e0] : __ldg(val + e);
+                                vv[u][t] = staged ? valW[e - e0] : __ldg(val + e);
                                 xv[u][t] = (T)__ldg(X + (size_t)c * ldx + kk[u]);
                             } else {
                                 flag = 1;
@@ -268,17 +267,17 @@ sketch_block_kernel(const int* __restrict__ rowptr, const int* __restrict__ coli
 #pragma unroll
                 for (int t = 0; t < kSkFastRow; ++t) {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
+                    for (int u = 0; u < kSkU; ++u)
                         if (t < ln[u]) acc[u] = fma(vv[u][t], xv[u][t], acc[u]);
                 }
             } else {
                 for (int t = 0; t < maxlen; ++t) {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
+                    for (int u = 0; u < kSkU; ++u) {
                         if (t < ln[u]) {
                             const int e = st[u] + t;
-                            const int c = staged ? colS[e - e0] : __ldg(colind + e);
-                            const T v = staged ? valS[e - e0] : __ldg(val + e);
+                            const int c = staged ? colW[e - e0] : __ldg(colind + e);
+                            const T v = staged ? valW[e - e0] : __ldg(val + e);
                             if ((unsigned)c < (unsigned)n)
                                 acc[u] = fma(v, (T)__ldg(X + (size_t)c * ldx + kk[u]), acc[u]);
                             else
@@ -288,58 +287,76 @@ sketch_block_kernel(const int* __restrict__ rowptr, const int* __restrict__ coli
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (j + u < M && rr[u] < 32) Ys[rr[u] * ncol + kk[u]] = rr[u] < cnt ? (double)acc[u] : 0.0;
+            for (int u = 0; u < kSkU; ++u)
+                if (eb + 32 * u < nent)
+                    Ys[(tw * kSkRowsPerWarp + rr[u]) * ncol + kk[u]] =
+                        rr[u] < wcnt ? (double)acc[u] : 0.0;
         }
-        __syncwarp();
-        long long* Yq = reinterpret_cast<long long*>(Ys);     // quantised in place
-        if (lane < ncol) {
-            // Column scale from the tile's largest magnitude, then the column
-            // as fixed-point integers (zeros for a column with no finite scale).
-            unsigned long long mx = 0;
-            for (int q = 0; q < cnt; ++q) {
-                const unsigned long long a =
-                    (unsigned long long)__double_as_longlong(Ys[q * ncol + lane]) & 0x7fffffffffffffffull;
-                mx = a > mx ? a : mx;
-            }
-            if (mx >= 0x7ff0000000000000ull) nonfinite = 1;
+        team_sync(team);
+        // (c) column scales and fixed-point values; warp tw owns columns tw, tw + 4, ...
+        long long* Yq = reinterpret_cast<long long*>(Ys);
+        for (int k = tw; k < ncol; k += kSkTeamWarps) {
+            const double y = Ys[lane * ncol + k];
+            const unsigned long long mx = warp_max_u64(
+                lane < cnt ? ((unsigned long long)__double_as_longlong(y) & 0x7fffffffffffffffull)
+                           : 0ull);
+            const bool nonfinite = mx >= 0x7ff0000000000000ull;
             const bool use = mx != 0 && !nonfinite;
+            const int has = stk[k] & 1;
+            int F = Fk[k];
             if (use) {
                 const int emax = (int)(mx >> 52) - 1023;          // mx < 2^(emax + 1)
                 const int Fn = (kSkValueBits - 1) - emax;
                 if (!has) {
                     F = Fn;
-                    has = 1;
                 } else if (Fn < F) {
                     const int d = F - Fn;
-                    for (int q = 0; q < s; ++q) Wi[q * ncol + lane] = shift_round(Wi[q * ncol + lane], d);
+                    for (int q = lane; q < s; q += 32)
+                        Wi[q * ncol + k] = shift_round(Wi[q * ncol + k], d);
                     F = Fn;
                 }
             }
-            for (int q = 0; q < 32; ++q)
-                Yq[q * ncol + lane] = (use && q < cnt) ? quantize(Ys[q * ncol + lane], F) : 0;
+            Yq[lane * ncol + k] = (use && lane < cnt) ? quantize(y, F) : 0;
+            __syncwarp();
+            if (lane == 0) {
+                Fk[k] = F;
+                stk[k] |= (use ? 1 : 0) | (nonfinite ? 2 : 0);
+            }
         }
-        __syncwarp();
-        scatter_rows<P>(Wi, Yq, skS, ncol, zeta, cnt);
-        __syncwarp();
+        team_sync(team);
+        // (d) W += S[:, r] Yq[r, :] for the tile's rows (integer atomics)
+        const int per_row = zeta * ncol;
+        const int pairs = cnt * per_row;
+        for (int p = tt; p < pairs; p += kSkTeamThreads) {
+            const int r = p / per_row;
+            const int rem = p - r * per_row;
+            const int z = rem / ncol;
+            const int k = rem - z * ncol;
+            const long long v = Yq[r * ncol + k];
+            if (v != 0) {
+                const unsigned e = skS[r * kMaxZeta + z];
+                atomicAdd(reinterpret_cast<unsigned long long*>(&Wi[(int)(e & 0x7fff) * ncol + k]),
+                          (unsigned long long)((e & 0x8000) ? -v : v));
+            }
+        }
+        team_sync(team);
     }
     if (flag) atomicOr(bad, 1);
-    Fsh[warp][lane] = F;
-    stat[warp][lane] = has | (nonfinite << 1);
     __syncthreads();
     double* out = partial + (size_t)blockIdx.x * wsz;
     for (int i = threadIdx.x; i < wsz; i += blockDim.x) {
         const int k = i % ncol;
         double acc = 0.0;
         bool nan = false;
-        for (int w = 0; w < kSkWarps; ++w) {
-            const int sw = stat[w][k];
-            nan |= (sw & 2) != 0;
-            if (sw & 1) {
-                const long long* Ww = reinterpret_cast<const long long*>(
-                    smem_raw + (size_t)w * sketch_warp_bytes(s, ncol));
-                acc += scalbn((double)Ww[i], -Fsh[w][k]);
-            }
+        for (int t = 0; t < nteams; ++t) {
+            const unsigned char* tp = smem_raw + (size_t)t * tb;
+            const long long* Wt = reinterpret_cast<const long long*>(tp);
+            const int* Ft = reinterpret_cast<const int*>(tp + 8 * (size_t)wsz + 8 * 32 * (size_t)ncol +
+                                                         (size_t)kSkTeamWarps * kSkWarpStage * 12 +
+                                                         2 * 32 * (size_t)kMaxZeta);
+            const int st = Ft[ncol + k];
+            nan |= (st & 2) != 0;
+            if (st & 1) acc += scalbn((double)Wt[i], -Ft[k]);
         }
         out[i] = nan ? __longlong_as_double(0x7ff8000000000000ll) : acc;
     }
@@ -353,35 +370,23 @@ __global__ void sketch_reduce_kernel(const double* __restrict__ partial, int nbl
     W[i] = sum_over_blocks(partial, nblk, wsz, i) * inv_sqrt_zeta;
 }
 
-// Blocks of the sketch kernel: two per SM, more when needed so that no warp
-// takes more than 33 tiles of 32 rows (so its accumulators stay below 2^63),
-// never more than one per 128 rows.
-int sketch_grid(int n) {
+// Blocks of the sketch kernel: one per SM, more when needed so that no team
+// takes more than kSkMaxTiles tiles of 32 rows (its accumulators stay below
+// 2^63), never more than the tiles need.
+int sketch_grid(int n, int s, int M) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int nblk = sms * 2;
-    const int by_rows = (int)(((long long)n + 4095) / 4096);
-    if (by_rows > nblk) nblk = by_rows;
-    const int need = (n + 127) / 128;
-    return nblk < need ? nblk : (need > 0 ? need : 1);
+    const int teams = sketch_teams(s, M + 1);
+    const long long ntiles = ((long long)n + 31) / 32;
+    long long nblk = std::min<long long>(sms, (ntiles + teams - 1) / teams);
+    const long long need = (ntiles + (long long)kSkMaxTiles * teams - 1) / ((long long)kSkMaxTiles * teams);
+    if (need > nblk) nblk = need;
+    return nblk > 0 ? (int)nblk : 1;
 }
 
 size_t sketch_partial_doubles(int n, int s, int M) {
-    return (size_t)sketch_grid(n) * s * (M + 1);
-}
-
-// Kernel for P = ceil(zeta (M+1) / 32) scatter pairs per lane.
-template <typename T, typename XT, int P>
-static void launch_sketch_p(const int* rowptr, const int* colind, const T* val, const XT* X,
-                            int ldx, const double* b, int n, int nnz, int M, int s, int zeta,
-                            uint64_t seed, double* partial, int nblk, int* bad, cudaStream_t st) {
-    const size_t smem = kSkWarps * sketch_warp_bytes(s, M + 1);
-    // The attribute is per device: set it on every call (cheap, host only).
-    cudaFuncSetAttribute(sketch_block_kernel<T, XT, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    sketch_block_kernel<T, XT, P><<<nblk, kSkWarps * 32, smem, st>>>(
-        rowptr, colind, val, X, ldx, b, n, nnz, M, s, zeta, seed, partial, bad);
+    return (size_t)sketch_grid(n, s, M) * s * (M + 1);
 }
 
 template <typename T, typename XT>
@@ -390,23 +395,15 @@ static void launch_sketch_impl(const int* rowptr, const int* colind, const T* va
                                uint64_t seed, double* partial, int nblk, double* W, int* bad,
                                cudaStream_t st) {
     const int wsz = s * (M + 1);
-#define SA_SK(PP)                                                                           \
-    launch_sketch_p<T, XT, PP>(rowptr, colind, val, X, ldx, b, n, nnz, M, s, zeta, seed, \
-                               partial, nblk, bad, st)
-    switch ((zeta * (M + 1) + 31) / 32) {
-        case 1: SA_SK(1); break;
-        case 2: SA_SK(2); break;
-        case 3: SA_SK(3); break;
-        case 4: SA_SK(4); break;
-        case 5: SA_SK(5); break;
-        case 6: SA_SK(6); break;
-        case 7: SA_SK(7); break;
-        case 8: SA_SK(8); break;
-        case 9: case 10: SA_SK(10); break;
-        case 11: case 12: SA_SK(12); break;
-        default: SA_SK(16); break;
-    }
-#undef SA_SK
+    // Teams for these columns (at least as many as the grid was sized for,
+    // so that no team takes more than kSkMaxTiles tiles).
+    const int teams = sketch_teams(s, M + 1);
+    const size_t smem = (size_t)teams * sketch_team_bytes(s, M + 1);
+    // The attribute is per device: set it on every call (cheap, host only).
+    cudaFuncSetAttribute(sketch_block_kernel<T, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    sketch_block_kernel<T, XT><<<nblk, teams * kSkTeamThreads, smem, st>>>(
+        rowptr, colind, val, X, ldx, b, n, nnz, M, s, zeta, seed, partial, bad);
     const double inv = 1.0 / sqrt((double)zeta);
     sketch_reduce_kernel<<<(wsz + 127) / 128, 128, 0, st>>>(partial, nblk, wsz, inv, W);
 }
