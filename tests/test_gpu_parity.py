@@ -73,7 +73,7 @@ def _run_guess(seq, p, i, hist_cols):
 
 
 @pytest.mark.parametrize("N,M,s,extra", [(40, 10, 40, 3), (37, 20, 80, 0), (23, 7, 48, 11),
-                                         (64, 1, 40, 0), (9, 5, 16, 2)])
+                                         (64, 1, 40, 0), (9, 5, 16, 2), (33, 3, 24, 1)])
 def test_guess_parity_well_conditioned(N, M, s, extra):
     """Random history (ring wrapped `extra` times): W, y and x0 agree tightly."""
     p = workloads.plain_nonsym(N)
