@@ -375,7 +375,8 @@ def batched_form(K, W, hbm_peak, count=512, plain_sample=16, one_block_ref=False
     # The plain FP64 GPU method (single-sequence API: sketched guess, FP64 CG,
     # push) on a sample of the sequences, fed the batch's solutions so that it
     # sees the same histories; timed on the step after the batched timing.
-    sample = list(range(0, count, max(1, count // plain_sample)))[:plain_sample]
+    sample = (list(range(0, count, max(1, count // plain_sample)))[:plain_sample]
+              if plain_sample else [])
     plain = {k: sa.Sequence(ps[k].n, M, S, zeta=ZETA, seed=SEED, krylov="cg", max_iters=200000)
              for k in sample} if plain_sample else {}
 
