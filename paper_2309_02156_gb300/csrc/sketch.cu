@@ -188,12 +188,16 @@ sketch_block_kernel(const int* __restrict__ rowptr, const int* __restrict__ coli
     uint16_t* skS = reinterpret_cast<uint16_t*>(stg + (size_t)kSkTeamWarps * kSkWarpStage * 12);
     int* Fk = reinterpret_cast<int*>(skS + 32 * kMaxZeta);
     int* stk = Fk + ncol;                    // bit 0: column has values, bit 1: non-finite
+    // (entry, column) of the flat index q = z (M + 1) + k of a row's scatter pairs
+    __shared__ int zk[kMaxZeta * (kMaxM + 1)];
+    const int per_row = zeta * ncol;
+    for (int q = threadIdx.x; q < per_row; q += blockDim.x) zk[q] = ((q / ncol) << 8) | (q % ncol);
     for (int i = tt; i < wsz; i += kSkTeamThreads) Wi[i] = 0;
     for (int k = tt; k < ncol; k += kSkTeamThreads) {
         Fk[k] = 0;
         stk[k] = 0;
     }
-    team_sync(team);
+    __syncthreads();
     int flag = 0;
     const int nent = kSkRowsPerWarp * M;
     const long long ntiles = ((long long)n + 31) / 32;
@@ -324,19 +328,29 @@ sketch_block_kernel(const int* __restrict__ rowptr, const int* __restrict__ coli
             }
         }
         team_sync(team);
-        // (d) W += S[:, r] Yq[r, :] for the tile's rows (integer atomics)
-        const int per_row = zeta * ncol;
-        const int pairs = cnt * per_row;
-        for (int p = tt; p < pairs; p += kSkTeamThreads) {
-            const int r = p / per_row;
-            const int rem = p - r * per_row;
-            const int z = rem / ncol;
-            const int k = rem - z * ncol;
-            const long long v = Yq[r * ncol + k];
-            if (v != 0) {
-                const unsigned e = skS[r * kMaxZeta + z];
-                atomicAdd(reinterpret_cast<unsigned long long*>(&Wi[(int)(e & 0x7fff) * ncol + k]),
-                          (unsigned long long)((e & 0x8000) ? -v : v));
+        // (d) W += S[:, r] Yq[r, :] for the tile's rows (integer atomics); the
+        // (row, sketch entry, column) triples are walked with the (entry,
+        // column) of each flat index taken from the block's table zk.
+        {
+            int r = 0, q = tt;
+            while (q >= per_row) {
+                q -= per_row;
+                ++r;
+            }
+            for (; r < cnt;) {
+                const int t = zk[q];
+                const int z = t >> 8, k = t & 0xff;
+                const long long v = Yq[r * ncol + k];
+                if (v != 0) {
+                    const unsigned e = skS[r * kMaxZeta + z];
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&Wi[(int)(e & 0x7fff) * ncol + k]),
+                              (unsigned long long)((e & 0x8000) ? -v : v));
+                }
+                q += kSkTeamThreads;
+                while (q >= per_row) {
+                    q -= per_row;
+                    ++r;
+                }
             }
         }
         team_sync(team);
