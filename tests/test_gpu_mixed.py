@@ -4,8 +4,8 @@ SEQ_MIXED_KRYLOV: FP64 history, sketch and guess; FP32 inner Krylov inside
 FP64 iterative refinement.  SEQ_MIXED: also the history and the sketch in
 FP32 (the least squares stays FP64).  Both must reach the FP64 tolerance on
 the true residual; inner iteration counts follow the oracle's float32
-emulation loosely (float32 rounding order differs between the two), and the
-number of refinement steps agrees within one.
+emulation within a few percent (float32 rounding order differs between the
+two), and the number of refinement steps agrees within one.
 """
 import numpy as np
 import pytest
@@ -59,9 +59,16 @@ def test_mixed_krylov_from_oracle_history(kind, N, tol):
         info = seq.solve(Ad, bd, tol, x)
         assert info["status"] == 0 and st_ref == 0
         assert method.relres(A, b, x.cpu().numpy()) <= tol * (1 + 1e-9)
-        # GMRES: one refinement per inner restart cycle, so the counts move together
-        assert abs(info["refinements"] - nref_ref) <= (1 if kind == "cg" else max(1, 0.5 * nref_ref))
-        assert info["iters"] <= 1.5 * it_ref + 10 and it_ref <= 1.5 * info["iters"] + 10
+        # The inner solves run in FP32 on both sides with different summation
+        # orders.  Measured over these 39 systems: GMRES counts within 0.7% (at
+        # most 1 iteration) with equal refinement counts; CG within 5.1% (10
+        # iterations, where one refinement more or less shifts the count).
+        # The bounds below are about twice those.
+        assert abs(info["refinements"] - nref_ref) <= 1
+        if kind == "gmres":
+            assert abs(info["iters"] - it_ref) <= max(3, 0.03 * it_ref)
+        else:
+            assert abs(info["iters"] - it_ref) <= max(3, 0.10 * it_ref)
         hist.push(x_ref)
         seq.push(_t(x_ref))
     seq.close()
