@@ -348,7 +348,8 @@ def profile_run(iters: int, precision: str = "f64", guess: str = "sketch", sweep
     seq.close()
 
 
-def batched_form(K, W, hbm_peak, count=512, plain_sample=16, one_block_ref=False):
+def batched_form(K, W, hbm_peak, count=512, plain_sample=16, one_block_ref=False,
+                 schedule="auto"):
     """512 independent SPD sequences (grid side 48..384, M = 12, s = 48), FP32 CG
     inside FP64 refinement to 1e-8, one persistent launch per time step (CUDA
     graph).  Systems are assembled on the device between timed steps."""
@@ -389,7 +390,11 @@ def batched_form(K, W, hbm_peak, count=512, plain_sample=16, one_block_ref=False
         bt.step(vs, bs, xs, TOL)
         feed()
     vs, bs, keep = inputs(M)
-    chosen = bt.autotune(vs, bs, xs, TOL)
+    if schedule == "one_block":                # fixed: 1,024 threads, one block per sequence
+        bt.set_schedule(1024, 1, 0)
+        chosen = bt.schedule()
+    else:
+        chosen = bt.autotune(vs, bs, xs, TOL)
     for i in range(M, M + W):
         vs, bs, keep = inputs(i)
         bt.step(vs, bs, xs, TOL)
@@ -1053,6 +1058,7 @@ def main():
     ap.add_argument("--profile-sweeps", type=int, default=0)
     ap.add_argument("--profile-precond", default="jacobi", choices=["jacobi", "chebyshev"])
     ap.add_argument("--batched-only", action="store_true")
+    ap.add_argument("--batched-schedule", default="auto", choices=["auto", "one_block"])
     ap.add_argument("--batched-count", type=int, default=512)
     ap.add_argument("--precond-form", action="store_true")
     ap.add_argument("--precond-sweeps", type=int, default=4)
@@ -1105,7 +1111,8 @@ def main():
         import torch
         hbm_peak, _ = peaks()
         torch.cuda.set_device(0)
-        print(json.dumps(batched_form(args.batched_steps, args.warmup, hbm_peak, args.batched_count)))
+        print(json.dumps(batched_form(args.batched_steps, args.warmup, hbm_peak, args.batched_count,
+                                      schedule=args.batched_schedule)))
         return
     if args.cpu_baseline_worker:
         cpu_baseline_worker(args.iters_per_system, args.gmres_iters)
