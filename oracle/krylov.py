@@ -265,7 +265,12 @@ def mixed_refine(A64, A32, b, x, tol: float, inner: str, restart: int,
             return x, total, refinements, rn / bnorm, CONVERGED
         if (max_refinements is not None and refinements >= max_refinements) or total >= max_iters:
             return x, total, refinements, rn / bnorm, NOT_CONVERGED
-        rhs32 = r.astype(np.float32)
+        # The inner equation A d = r / ||r|| (the correction is ||r|| d): the
+        # Krylov iterates scale with the right-hand side and the inner
+        # tolerance is relative, so this is the same solve in exact
+        # arithmetic, and the float32 right-hand side stays in range whatever
+        # the scale of b.
+        rhs32 = (r / rn).astype(np.float32)
         itol = max(inner_tol, theta * target / rn)
         d0 = np.zeros_like(rhs32)
         budget = max_iters - total
@@ -279,7 +284,7 @@ def mixed_refine(A64, A32, b, x, tol: float, inner: str, restart: int,
         refinements += 1
         if st == BREAKDOWN:
             return x, total, refinements, rn / bnorm, BREAKDOWN
-        x = x + d.astype(np.float64)
+        x = x + rn * d.astype(np.float64)
 
 
 def direct_solve(A, b, refinements: int = 2):

@@ -144,3 +144,25 @@ def test_full_size_precision_form_first_systems():
         assert abs(info["final_relres"] - r) <= 3e-11
         seq.push(x)
     seq.close()
+
+
+@pytest.mark.parametrize("scale", [1e-36, 1e30])
+def test_mixed_solve_is_scale_invariant(scale):
+    """b scaled by 1e-36 (float32 r . r would underflow) or 1e30: the FP32
+    inner solves see r / ||r||, so the solve converges with the same
+    refinements and inner iterations as for b itself."""
+    import paper_2309_02156_gb300 as sa
+    p = workloads.plain_nonsym(33)
+    rowptr, colind, vals, b = workloads.csr_system(p, 2)
+    A = krylov.csr(rowptr, colind, vals, p.n)
+    out = []
+    for bb in (b, b * scale):
+        seq = sa.Sequence(p.n, 4, 16, precision="mixed_krylov", krylov="gmres", max_iters=60000)
+        Ad, bd = _dev(rowptr, colind, vals, bb)
+        x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+        info = seq.solve(Ad, bd, 1e-10, x)
+        assert info["status"] == 0
+        assert method.relres(A, bb, x.cpu().numpy()) <= 1e-10 * (1 + 1e-9)
+        out.append((info["refinements"], info["iters"]))
+        seq.close()
+    assert out[1][0] == out[0][0] and abs(out[1][1] - out[0][1]) <= 1

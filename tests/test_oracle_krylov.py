@@ -156,6 +156,23 @@ def test_mixed_refinement_inner_tolerance_and_count(tol, theta, inner_tol, iters
         assert rel == 2.0 ** -refs
 
 
+@pytest.mark.parametrize("scale", [1e-36, 1e30])
+def test_mixed_refinement_is_scale_invariant(scale):
+    """b scaled by 1e-36 (its float32 image would be subnormal or zero) or
+    1e30: the inner float32 solves see r / ||r||, so refinements, inner
+    iterations and the relative residual history do not change, and x scales
+    with b."""
+    A64, A32, b = _two_level_diagonal()
+    ref = krylov.mixed_refine(A64, A32, b, np.zeros_like(b), 1.5 * 2.0 ** -10, "cg", 30, 1000,
+                              inner_tol=0.55, max_refinements=50)
+    got = krylov.mixed_refine(A64, A32, b * scale, np.zeros_like(b), 1.5 * 2.0 ** -10, "cg", 30,
+                              1000, inner_tol=0.55, max_refinements=50)
+    assert got[4] == krylov.CONVERGED and ref[4] == krylov.CONVERGED
+    assert got[1:3] == ref[1:3] == (10, 10)
+    assert got[3] == pytest.approx(ref[3], rel=1e-12)
+    assert np.allclose(got[0], ref[0] * scale, rtol=1e-12, atol=0)
+
+
 def test_mixed_refinement_refinement_cap():
     """max_refinements stops the loop with NOT_CONVERGED and the residual
     reached: 2^-3 after three halving refinements."""
