@@ -74,9 +74,10 @@ def test_batched_matches_oracle_with_shared_history(ctas):
             assert info["guess_relres"] == pytest.approx(r["guess_relres"], rel=2e-3, abs=1e-13)
             assert abs(info["refinements"] - r["refinements"]) <= 1
             # FP32 CG on both sides in different summation orders: measured
-            # within 4.3% (one block) and 6.9% (clusters of 8), at most 4
-            # iterations, over 9 steps of these 8 sequences
-            assert abs(info["iters"] - r["iters"]) <= max(5, 0.12 * r["iters"])
+            # within 7.6% (13 iterations of 170) over 9 steps of these 8
+            # sequences, one block or clusters of 8 (and 2 against 1 on the
+            # 1 x 1 system)
+            assert abs(info["iters"] - r["iters"]) <= max(5, 0.15 * r["iters"])
         for k, r in enumerate(ref):       # both histories receive the oracle's solutions
             bt.push(k, torch.from_numpy(r["x"]).to(DEV))
     bt.close()
