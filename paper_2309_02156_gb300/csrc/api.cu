@@ -44,6 +44,7 @@ struct seq_ctx {
     float* val32 = nullptr;          // rounded matrix values (mixed, when not supplied)
     int val32_cap = 0;
     float* rhs32 = nullptr;
+    double* r64 = nullptr;           // FP64 residual of the refinement (mixed precision)
     float* d = nullptr;
     DevArgs* d_args = nullptr;       // outer (FP64) system
     DevArgs* h_args = nullptr;       // pinned staging
@@ -533,6 +534,7 @@ int seq_create(const seq_config* cfg, void* cuda_stream, seq_ctx** out) {
     }
     if (ctx->mixed) {
         ok = ok && cudaMalloc(&ctx->rhs32, sizeof(float) * (size_t)n) == cudaSuccess;
+        ok = ok && cudaMalloc(&ctx->r64, sizeof(double) * (size_t)n) == cudaSuccess;
         ok = ok && cudaMalloc(&ctx->d, sizeof(float) * (size_t)n) == cudaSuccess;
     }
     if (c.krylov == SEQ_GMRES || n >= kGridCgMinRows) {     // SELL-32 copy for the cycles
@@ -605,7 +607,7 @@ int seq_destroy(seq_ctx* ctx) {
     for (auto e : ctx->ev) cudaEventDestroy(e);
     if (ctx->mlp_owned) seq_mlp_destroy(ctx->mlp_owned);
     void* dev_ptrs[] = {ctx->X, ctx->sk_partial, ctx->W, ctx->lsq, ctx->kpartial,
-                        ctx->V, ctx->w, ctx->r, ctx->p, ctx->q, ctx->val32, ctx->rhs32, ctx->d,
+                        ctx->V, ctx->w, ctx->r, ctx->p, ctx->q, ctx->val32, ctx->rhs32, ctx->r64, ctx->d,
                         ctx->d_args, ctx->d_args_in, ctx->ks, ctx->ks_in, ctx->sell_width,
                         ctx->sell_off, ctx->sell_col, ctx->sell_val, ctx->yring, ctx->sample,
                         ctx->yhat, ctx->used_net, ctx->Om, ctx->Zs, ctx->gpart, ctx->gcount,
@@ -984,7 +986,7 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
         // FP64 iterative refinement around FP32 inner solves.
         const double theta = 0.5;
         int total = 0, refinements = 0;
-        launch_refine_residual(ctx->d_args, ctx->ks, ctx->rhs32, ctx->kpartial, ctx->nblk,
+        launch_refine_residual(ctx->d_args, ctx->ks, ctx->r64, ctx->kpartial, ctx->nblk,
                                ctx->stream);
         ctx->launches += 1;
         CK(cudaGetLastError());
@@ -1009,6 +1011,8 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
                 status = SEQ_NOT_CONVERGED;
                 break;
             }
+            launch_refine_scale(ctx->r64, ctx->ks, ctx->rhs32, ctx->cfg.n, ctx->stream);
+            ctx->launches += 1;
             DevArgs* hi = ctx->h_args_in;
             hi->tol = fmax(c.inner_tol, theta * target / beta);
             hi->max_iters = c.max_iters - total;
@@ -1037,8 +1041,8 @@ int seq_solve(seq_ctx* ctx, const seq_csr* A, const double* b_dev, double tol, d
                 status = ist;
                 break;
             }
-            launch_refine_update(ctx->d_args, nullptr, 0.0, nullptr, ctx->stream);
-            launch_refine_residual(ctx->d_args, ctx->ks, ctx->rhs32, ctx->kpartial, ctx->nblk,
+            launch_refine_update(ctx->d_args, ctx->ks, ctx->stream);
+            launch_refine_residual(ctx->d_args, ctx->ks, ctx->r64, ctx->kpartial, ctx->nblk,
                                    ctx->stream);
             ctx->launches += 2;
             CK(cudaGetLastError());

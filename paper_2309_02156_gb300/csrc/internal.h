@@ -115,12 +115,13 @@ void launch_gmres_cycle_f32(const DevArgs* a, KState* ks, float* V, size_t ldv, 
                             const ChebConfig* cheb = nullptr, float* dvec = nullptr);
 void launch_diag_inv_f32(const DevArgs* a, float* dinv, int n, cudaStream_t st,
                          unsigned long long* bound = nullptr);
-// Mixed precision outer step: x += scale * d (FP64 += FP32), then the FP64
-// residual r = b - A64 x, its norm, and rhs32 = r / ||r||.
-void launch_refine_residual(const DevArgs* a, KState* ks, float* rhs32, double* partial, int nblk,
+// Mixed precision outer step: the FP64 residual r = b - A64 x (into r64) with
+// st->beta = ||r|| and ||b||; the FP32 right-hand side rhs32 = r / ||r||; and
+// after the inner solve x += ||r|| d (FP64 += FP32).
+void launch_refine_residual(const DevArgs* a, KState* ks, double* r64, double* partial, int nblk,
                             cudaStream_t st);
-void launch_refine_update(const DevArgs* a, const KState* inner, double scale_from_outer_beta,
-                          KState* outer, cudaStream_t st);
+void launch_refine_scale(const double* r64, const KState* ks, float* rhs32, int n, cudaStream_t st);
+void launch_refine_update(const DevArgs* a, const KState* outer, cudaStream_t st);
 // Single-block CG (T = double: FP64 system; the kernel loops on the device).
 void launch_cg_block_f64(const DevArgs* a, KState* ks, double* r, double* p, double* q,
                          cudaStream_t st);

@@ -207,9 +207,9 @@ void launch_sell_fill_f32(const int* rowptr, const int* colind, const float* val
 }
 
 // ---------------------------------------------------------------------------
-// Mixed precision: r = b - A64 x in FP64, beta = ||r||, rhs32 = (float) r.
+// Mixed precision: r = b - A64 x in FP64 (into r64), beta = ||r||, ||b||.
 __global__ void __launch_bounds__(kStreamBlock, 1)
-refine_residual_kernel(const DevArgs* __restrict__ a, KState* ks, float* rhs32, double* partial) {
+refine_residual_kernel(const DevArgs* __restrict__ a, KState* ks, double* r64, double* partial) {
     __shared__ double sprod[kWarps * kTileP];
     __shared__ double scratch[kWarps * 2];
     __shared__ double red[2];
@@ -225,7 +225,7 @@ refine_residual_kernel(const DevArgs* __restrict__ a, KState* ks, float* rhs32, 
         if (row < n) {
             const double bi = a->b[row];
             const double r = bi - ax;
-            rhs32[row] = (float)r;
+            r64[row] = r;
             acc[0] += r * r;
             acc[1] += bi * bi;
         }
@@ -244,22 +244,41 @@ refine_residual_kernel(const DevArgs* __restrict__ a, KState* ks, float* rhs32, 
     }
 }
 
-void launch_refine_residual(const DevArgs* a, KState* ks, float* rhs32, double* partial, int nblk,
+void launch_refine_residual(const DevArgs* a, KState* ks, double* r64, double* partial, int nblk,
                             cudaStream_t st) {
-    refine_residual_kernel<<<nblk, kStreamBlock, 0, st>>>(a, ks, rhs32, partial);
+    refine_residual_kernel<<<nblk, kStreamBlock, 0, st>>>(a, ks, r64, partial);
 }
 
-// x += d (FP64 += FP32 correction of the inner solve).
-__global__ void refine_update_kernel(const DevArgs* __restrict__ a) {
+// rhs32 = r / ||r|| in FP32: the inner equation is A d = r / ||r|| and the
+// correction ||r|| d, the same solve in exact arithmetic (the inner tolerance
+// is relative), with the FP32 right-hand side and its dot products in range
+// whatever the scale of b.
+__global__ void refine_scale_kernel(const double* __restrict__ r64, const KState* __restrict__ ks,
+                                    float* __restrict__ rhs32, int n) {
+    const double inv = 1.0 / ks->beta;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        rhs32[i] = (float)(r64[i] * inv);
+}
+
+void launch_refine_scale(const double* r64, const KState* ks, float* rhs32, int n, cudaStream_t st) {
+    int b = (n + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    refine_scale_kernel<<<b > 0 ? b : 1, 256, 0, st>>>(r64, ks, rhs32, n);
+}
+
+// x += ||r|| d (FP64 += the FP32 correction of the inner solve on r / ||r||;
+// ||r|| = outer->beta, the residual norm the right-hand side was scaled by).
+__global__ void refine_update_kernel(const DevArgs* __restrict__ a, const KState* __restrict__ outer) {
     const int n = a->n;
     const float* d = reinterpret_cast<const float*>(a->d);
+    const double beta = outer->beta;
     double* x = a->x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        x[i] += (double)d[i];
+        x[i] = fma(beta, (double)d[i], x[i]);
 }
 
-void launch_refine_update(const DevArgs* a, const KState*, double, KState*, cudaStream_t st) {
-    refine_update_kernel<<<152 * 8, 256, 0, st>>>(a);
+void launch_refine_update(const DevArgs* a, const KState* outer, cudaStream_t st) {
+    refine_update_kernel<<<152 * 8, 256, 0, st>>>(a, outer);
 }
 
 __global__ void round_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, int n) {
