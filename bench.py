@@ -1274,6 +1274,17 @@ def main():
     x_h = torch.empty(n, dtype=torch.float64).pin_memory()
     h2d = rp_h.numel() * 4 + ci_h.numel() * 4 + v_d.numel() * 8 + b_d.numel() * 8
     d2h = n * 8
+    # One untimed guess and solve of the first system without a push: the
+    # fresh context builds its restart-cycle graph and SELL buffers here, as
+    # the timed context did in its warm-up steps; the history is unchanged.
+    i0 = steps_e2e[0]
+    rp_d.copy_(rp_h, non_blocking=True)
+    ci_d.copy_(ci_h, non_blocking=True)
+    v_d.copy_(pin[i0][0], non_blocking=True)
+    b_d.copy_(pin[i0][1], non_blocking=True)
+    A = sa.CSR(rp_d, ci_d, v_d)
+    seq.guess(A, b_d, x)
+    seq.solve(A, b_d, TOL, x)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
