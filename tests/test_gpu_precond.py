@@ -192,6 +192,43 @@ def test_preconditioned_gmres_on_irregular_rows(N, far):
     seq.close()
 
 
+@pytest.mark.parametrize("kind", ["jacobi", "chebyshev"])
+def test_preconditioned_gmres_without_a_sell_copy(kind):
+    """One row holding 1,000 entries (0.1% of the diagonal each) pads its
+    32-row slice so far that the SELL copy is not built: the products, the
+    folded first sweep included, run on the CSR arrays.  Same parity as above
+    against the oracle's preconditioner."""
+    import scipy.sparse as sp
+    p = workloads.plain_nonsym(40)
+    rowptr, colind, vals, b = workloads.csr_system(p, 3)
+    A = krylov.csr(rowptr, colind, vals, p.n).tolil()
+    d = A.diagonal()
+    r0 = 17
+    for c in range(0, p.n, max(1, p.n // 1000))[:1000]:
+        if c != r0:
+            A[r0, c] = A[r0, c] + 0.01 * d[r0] / 10
+    A_ref = sp.csr_matrix(A)
+    A_ref.sort_indices()
+    ns = (p.n + 31) // 32
+    assert 32 * np.diff(A_ref.indptr).max() > 2 * A_ref.nnz + 64 * ns     # no SELL copy
+    if kind == "jacobi":
+        minv = krylov.jacobi_sweeps(A_ref, 4, 0.8)
+    else:
+        lmax = krylov.gershgorin_bound(A_ref)
+        minv = krylov.chebyshev_sweeps(A_ref, 4, lmax / 30, lmax)
+    x_ref, it_ref, rel_ref, st_ref = krylov.gmres(A_ref, b, np.zeros(p.n), 1e-9, 30, 50000, minv=minv)
+    A = _sa().CSR(_t(A_ref.indptr.astype(np.int32), torch.int32),
+                  _t(A_ref.indices.astype(np.int32), torch.int32), _t(A_ref.data))
+    seq = _sa().Sequence(p.n, 4, 16, krylov="gmres", restart=30, max_iters=50000,
+                         precond_sweeps=4, precond_kind=kind)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    info = seq.solve(A, _t(b), 1e-9, x)
+    assert info["status"] == 0 and st_ref == 0
+    assert abs(info["iters"] - it_ref) <= max(2, 0.03 * it_ref)
+    assert method.relres(A_ref, b, x.cpu().numpy()) <= 1e-9 * (1 + 1e-9)
+    seq.close()
+
+
 @pytest.mark.parametrize("N,d,ratio,lfix", [(32, 2, 0.0, 0.0), (45, 4, 0.0, 0.0), (40, 8, 10.0, 0.0),
                                             (24, 6, 0.0, 1.9)])
 def test_chebyshev_preconditioned_gmres_matches_oracle(N, d, ratio, lfix):
