@@ -1214,7 +1214,8 @@ def main():
         roof["algorithmic_flops_per_launch"] = flops_l
         roof["launch_us"] = t_launch * 1e6
         roof["timing"] = ("CUDA events on the context's stream between the kernels of the "
-                          "restart-cycle graph, averaged over every launch of a separate "
+                          "restart-cycle graph (the sweeps of one preconditioner application "
+                          "between one pair), averaged over every launch of a separate "
                           "profiled pass (systems %d..%d)" % (label_steps[0], label_steps[-1]))
         total_ms = sum(v["ms"] for v in stats.values())
         kernels = {k: {"launches": v["launches"],

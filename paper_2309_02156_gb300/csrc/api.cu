@@ -257,7 +257,7 @@ int capture_cycle(seq_ctx* ctx, bool prof) {
     const double om = ctx->cfg.precond_omega;
     if (prof) {
         if (ctx->ev.empty()) {
-            ctx->ev.resize(cycle_kernels(R, sw, ctx->mixed) + 1);
+            ctx->ev.resize(cycle_marks(R, sw, ctx->mixed) + 1);
             for (auto& e : ctx->ev) CK(cudaEventCreate(&e));
         }
         ev = ctx->ev.data();
@@ -286,14 +286,15 @@ int capture_cycle(seq_ctx* ctx, bool prof) {
     return SEQ_OK;
 }
 
-void add_stat(seq_ctx* ctx, int kind, int ev0, double bytes, double flops) {
+// launches kernels of one kind between events ev0 and ev0 + 1.
+void add_stat(seq_ctx* ctx, int kind, int ev0, double bytes, double flops, int launches = 1) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ctx->ev[ev0], ctx->ev[ev0 + 1]) != cudaSuccess) {
         cudaGetLastError();
         return;
     }
     seq_kernel_stat& st = ctx->stats[kind];
-    st.launches += 1;
+    st.launches += launches;
     st.ms += ms;
     st.bytes += bytes;
     st.flops += flops;
@@ -310,29 +311,31 @@ void account_cycle(seq_ctx* ctx, bool f32, int jd, bool updated, int nnz) {
     const double spmv_mat = ctx->sell_ok ? 4.0 * (ns + 1) + (4.0 + E) * (double)*ctx->h_int : csr;
     const int sw = ctx->cfg.precond_sweeps;
     const int pk = precond_kernels(sw);
-    const int S = step_kernels(f32) + pk;
+    const int pm = sw > 0 ? 1 : 0;                   // one mark per preconditioner application
+    const int S = step_kernels(f32) + pm;
     // Preconditioner of degree d > 1: the first sweep reads the matrix, u
     // (gathered; the same array as its row operand) and dinv and writes z;
     // each later sweep reads the matrix, z (gathered), u, dinv and writes the
     // next z.  Chebyshev also writes d at every sweep but the last and reads
     // it at every sweep but the first.  Degree 1: the scale reads u, dinv and
-    // writes z (and d).
+    // writes z (and d).  The application's sweeps share one pair of events.
     const double cv = ctx->cfg.precond_kind == 1 ? 1.0 : 0.0;
     auto precond = [&](int ev0) {
         if (sw == 1) {
             add_stat(ctx, SEQ_K_PRECOND, ev0, (3.0 + cv) * E * n, 2.0 * n);
             return;
         }
+        double bytes = 0.0, flops = 0.0;
         for (int k = 1; k < sw; ++k) {
             const double dv = cv * ((k > 1 ? 1.0 : 0.0) + (k < sw - 1 ? 1.0 : 0.0));
-            add_stat(ctx, SEQ_K_PRECOND, ev0 + k - 1,
-                     spmv_mat + ((k == 1 ? 3.0 : 4.0) + dv) * E * n,
-                     2.0 * nnz + (k == 1 ? 6.0 + 2.0 * cv : 4.0 + 3.0 * cv) * n);
+            bytes += spmv_mat + ((k == 1 ? 3.0 : 4.0) + dv) * E * n;
+            flops += 2.0 * nnz + (k == 1 ? 6.0 + 2.0 * cv : 4.0 + 3.0 * cv) * n;
         }
+        add_stat(ctx, SEQ_K_PRECOND, ev0, bytes, flops, pk);
     };
     for (int j = 0; j < jd; ++j) {
         const double nk = j + 1;
-        int e = S * j + pk;
+        int e = S * j + pm;
         if (sw > 0) precond(S * j);
         if (f32) {
             // fused SpMV + first-pass dots: matrix, gathered vector, w written
@@ -351,9 +354,9 @@ void account_cycle(seq_ctx* ctx, bool f32, int jd, bool updated, int nnz) {
         if (updated) {
             add_stat(ctx, SEQ_K_UPDATE, u, E * n * (jd + 1), 2.0 * n * jd);
             precond(u + 1);
-            add_stat(ctx, SEQ_K_UPDATE, u + 1 + pk, 3.0 * E * n, n);
+            add_stat(ctx, SEQ_K_UPDATE, u + 2, 3.0 * E * n, n);
         }
-        u += pk + 2;
+        u += 3;
     } else {
         if (updated) add_stat(ctx, SEQ_K_UPDATE, u, E * n * (jd + 2), 2.0 * n * jd);
         u += 1;

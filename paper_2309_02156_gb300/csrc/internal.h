@@ -75,6 +75,12 @@ inline int cycle_kernels(int R, int sweeps, bool f32) {
     const int pk = precond_kernels(sweeps);
     return (step_kernels(f32) + pk) * R + (sweeps > 0 ? pk + 2 : 1) + 1;
 }
+// Timing marks of a profiled cycle: one per kernel, one per preconditioner
+// application (its sweeps run back to back between two events).
+inline int cycle_marks(int R, int sweeps, bool f32) {
+    const int pm = sweeps > 0 ? 1 : 0;
+    return (step_kernels(f32) + pm) * R + (sweeps > 0 ? 3 : 1) + 1;
+}
 // ||b - A x|| and ||b|| of FP64 vectors; results in st->beta, st->bnorm and
 // st->first_relres = beta / bnorm.
 void launch_residual_norm(const DevArgs* a, KState* ks, double* partial, int nblk,

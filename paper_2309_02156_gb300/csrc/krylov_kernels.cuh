@@ -755,7 +755,7 @@ static const typename Sys::T* launch_precond(const DevArgs* a, KState* ks,
         else
             precond_sweep_kernel<Sys, 0, 0><<<nblk, kSpmvBlock, 0, st>>>(
                 a, ks, u, sig_idx, pc.dinv, pc.omega, zin, zout, phase, sw, pc.tab, pc.dvec, last);
-        mark(ev, k, st);
+        if (last) mark(ev, k, st);     // one event pair around the application's sweeps
         if (sw > 1) {
             T* tmp = cur;
             cur = nxt;
@@ -811,13 +811,13 @@ struct StepTable<Sys, kMaxRestart + 1> {
                        const PrecondArgs<typename Sys::T>&) {}
 };
 
-// One restart cycle.  With `ev` (cycle_kernels + 1 timing events) an event is
-// recorded before the first kernel and after every kernel: kernel i of the
-// cycle lies between ev[i] and ev[i + 1].  With S = step_kernels + sweeps
-// kernels per Arnoldi step j: S j .. S j + sweeps - 1 the preconditioner, then
-// SpMV, first-pass dots, pass 2, pass 3 (FP32: SpMV with the dots, pass 2,
-// pass 3); from S R the update kernels (one, or combine + sweeps + axpy), then
-// the restart residual.
+// One restart cycle.  With `ev` (cycle_marks + 1 timing events) an event is
+// recorded before the first kernel and after every kernel, except that a
+// preconditioner application's consecutive sweeps share one pair of events:
+// with S = step_kernels + (1 with a preconditioner) marks per Arnoldi step j,
+// S j is the preconditioner, then SpMV, first-pass dots, pass 2, pass 3
+// (FP32: SpMV with the dots, pass 2, pass 3); from S R the update (one
+// kernel, or combine + preconditioner + axpy), then the restart residual.
 template <class Sys>
 static void launch_cycle(const DevArgs* a, KState* ks, typename Sys::T* V, size_t ldv,
                          typename Sys::T* w, typename Sys::T* partial, int nblk, int R,
