@@ -1210,6 +1210,12 @@ def main():
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["traffic"] = profile_traffic(dom, bytes_l, "f64" if fp64 else "f32")
         roof["kernel"] = dom
+        if dom == "precond":
+            roof["note"] = ("the sweeps of one preconditioner application re-read the same matrix, "
+                            "which stays in L2 between them; the algorithmic bytes count it at "
+                            "every sweep, so the fraction of the HBM copy rate can exceed 1 "
+                            "(profiles/precond_sweeps_nonsym1024.txt: DRAM reads per sweep with "
+                            "a cold and a warm L2)")
         roof["algorithmic_bytes_per_launch"] = bytes_l
         roof["algorithmic_flops_per_launch"] = flops_l
         roof["launch_us"] = t_launch * 1e6
