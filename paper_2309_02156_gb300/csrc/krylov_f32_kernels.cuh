@@ -13,17 +13,25 @@
 // layout replaces the column-segment dot kernel of FP64.  Rows past the last
 // full vector of the block's range are handled one per thread.  Reductions:
 // per-thread partials over its rows, warp reduce-scatter, warps in order,
-// blocks in order in the last block (deterministic).
+// blocks in order in the last block (deterministic).  The basis columns are
+// read with streaming loads (ld.global.cs, evict-first in L2): each pass
+// reads them once, so they leave L2 before the matrix does and the product
+// of the next Arnoldi step finds the matrix there.
 template <int VW> struct F32x;
 template <> struct F32x<1> {
     using type = float;
     __device__ static void get(const float* p, float (&o)[1]) { o[0] = *p; }
+    __device__ static void stream(const float* p, float (&o)[1]) { o[0] = __ldcs(p); }
     __device__ static void put(float* p, const float (&o)[1]) { *p = o[0]; }
 };
 template <> struct F32x<2> {
     using type = float2;
     __device__ static void get(const float* p, float (&o)[2]) {
         const float2 v = *reinterpret_cast<const float2*>(p);
+        o[0] = v.x; o[1] = v.y;
+    }
+    __device__ static void stream(const float* p, float (&o)[2]) {
+        const float2 v = __ldcs(reinterpret_cast<const float2*>(p));
         o[0] = v.x; o[1] = v.y;
     }
     __device__ static void put(float* p, const float (&o)[2]) {
@@ -34,6 +42,10 @@ template <> struct F32x<4> {
     using type = float4;
     __device__ static void get(const float* p, float (&o)[4]) {
         const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+    __device__ static void stream(const float* p, float (&o)[4]) {
+        const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
         o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
     }
     __device__ static void put(float* p, const float (&o)[4]) {
@@ -68,7 +80,7 @@ __device__ __forceinline__ void f32_rows(const float* __restrict__ V, size_t ldv
         for (int u = 0; u < U; ++u) {
             const int i = min(i0 + u * bd * VW, hv - VW);
 #pragma unroll
-            for (int k = 0; k < NK; ++k) X::get(V + (size_t)k * ldv + i, vv[u][k]);
+            for (int k = 0; k < NK; ++k) X::stream(V + (size_t)k * ldv + i, vv[u][k]);
             X::get(w + i, r[u]);
         }
 #pragma unroll

@@ -390,7 +390,9 @@ arnoldi_spmv_kernel(const DevArgs* __restrict__ a, const KState* __restrict__ ks
 // segment g) spread over all warps (nseg segments per column so that small
 // bases still use every warp); each lane keeps eight accumulators, combined
 // in a fixed order, then the warp butterfly; segments are summed in segment
-// order.
+// order.  Here and in K7a/K7b the basis columns are read with streaming
+// loads (evict-first in L2), which keeps the matrix in L2 for the product of
+// the next Arnoldi step.
 constexpr int kDotBlock = 768;
 constexpr int kDotWarps = kDotBlock / 32;
 
@@ -420,9 +422,9 @@ arnoldi_dot_kernel(const DevArgs* __restrict__ a, KState* ks,
         int i = s0 + lane;
         for (; i + 7 * 32 < s1; i += 8 * 32) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) acc[u] = fma(vk[i + u * 32], w[i + u * 32], acc[u]);
+            for (int u = 0; u < 8; ++u) acc[u] = fma(__ldcs(vk + i + u * 32), w[i + u * 32], acc[u]);
         }
-        for (; i < s1; i += 32) acc[0] = fma(vk[i], w[i], acc[0]);
+        for (; i < s1; i += 32) acc[0] = fma(__ldcs(vk + i), w[i], acc[0]);
         const T t = warp_sum(((acc[0] + acc[1]) + (acc[2] + acc[3])) +
                              ((acc[4] + acc[5]) + (acc[6] + acc[7])));
         if (lane == 0) segsum[k * kDotWarps + g] = t;
@@ -481,7 +483,7 @@ arnoldi_pass2_kernel(const DevArgs* __restrict__ a, KState* ks,
         for (int u = 0; u < ROWS; ++u) {
             const int i = min(i0 + u * bd, hi - 1);
 #pragma unroll
-            for (int k = 0; k < NK; ++k) vv[u][k] = V[(size_t)k * ldv + i];
+            for (int k = 0; k < NK; ++k) vv[u][k] = __ldcs(V + (size_t)k * ldv + i);
             r[u] = w[i];
         }
 #pragma unroll
@@ -647,7 +649,7 @@ arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T*
         for (int u = 0; u < ROWS; ++u) {
             const int i = min(i0 + u * bd, hi - 1);
 #pragma unroll
-            for (int k = 0; k < NK; ++k) vv[u][k] = V[(size_t)k * ldv + i];
+            for (int k = 0; k < NK; ++k) vv[u][k] = __ldcs(V + (size_t)k * ldv + i);
             r[u] = w[i];
         }
 #pragma unroll
@@ -707,12 +709,9 @@ template <class Sys>
 static size_t spmv_smem() {
     using T = typename Sys::T;
     const size_t bytes = sizeof(T) * (size_t)kSpmvWarps * kTile;
-    static bool set = false;
-    if (!set) {
-        cudaFuncSetAttribute(arnoldi_spmv_kernel<Sys>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bytes);
-        set = true;
-    }
+    // The attribute is per device: set it on every call (cheap, host only).
+    cudaFuncSetAttribute(arnoldi_spmv_kernel<Sys>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bytes);
     return bytes;
 }
 

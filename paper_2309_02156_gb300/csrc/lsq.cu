@@ -178,11 +178,8 @@ lsq_kernel(const double* __restrict__ W, int s, int M, int m, int oldest, double
 void launch_lsq(const double* W, int s, int M, int m, int oldest_slot, double tau, LsqOut* out,
                 cudaStream_t st) {
     const size_t smem = sizeof(double) * (2 * (size_t)s * m + 3 * (size_t)s + 5 * (size_t)m + 32);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(lsq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-        attr = true;
-    }
+    // The attribute is per device: set it on every call (cheap, host only).
+    cudaFuncSetAttribute(lsq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     lsq_kernel<<<1, 256, smem, st>>>(W, s, M, m, oldest_slot, tau, out);
 }
 
