@@ -129,7 +129,8 @@ gmres_start_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* V
 
 // Lane l of every warp holds, for K <= 32, the warp partial of column l % K
 // after warp_reduce_scatter; the block partial of column k (k < nk) is the
-// sum over warps in warp order.  K = 64 is handled as two halves of 32.
+// sum over warps in warp order.  32 < K <= 64 is handled as two halves of 32,
+// the upper one padded with zeros past column K - 1.
 template <typename T, int K>
 __device__ __forceinline__ void block_columns(T (&part)[K], int nk, T* wsum /* kWarps * K */,
                                               T* out /* global, K */) {
@@ -145,16 +146,17 @@ __device__ __forceinline__ void block_columns(T (&part)[K], int nk, T* wsum /* k
         const T c = warp_reduce_scatter<T, P>(v);
         if (lane < K) wsum[warp * K + lane] = c;
     } else {
+        static_assert(K <= 64, "at most 64 columns");
         T lo[32], hi[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
             lo[i] = part[i];
-            hi[i] = part[32 + i];
+            hi[i] = 32 + i < K ? part[32 + i] : (T)0;
         }
         const T cl = warp_reduce_scatter<T, 32>(lo);
         const T ch = warp_reduce_scatter<T, 32>(hi);
         wsum[warp * K + lane] = cl;
-        wsum[warp * K + 32 + lane] = ch;
+        if (32 + lane < K) wsum[warp * K + 32 + lane] = ch;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < nk; k += blockDim.x) {
@@ -390,11 +392,13 @@ arnoldi_spmv_kernel(const DevArgs* __restrict__ a, const KState* __restrict__ ks
 // segment g) spread over all warps (nseg segments per column so that small
 // bases still use every warp); each lane keeps eight accumulators, combined
 // in a fixed order, then the warp butterfly; segments are summed in segment
-// order.  Here and in K7a/K7b the basis columns are read with streaming
-// loads (evict-first in L2), which keeps the matrix in L2 for the product of
-// the next Arnoldi step.
+// order.  With more columns than warps the row-parallel K5b' below takes
+// over.  Here and in K5b', K7a and K7b the basis columns are read with
+// streaming loads (evict-first in L2), which keeps the matrix in L2 for the
+// product of the next Arnoldi step.
 constexpr int kDotBlock = 768;
 constexpr int kDotWarps = kDotBlock / 32;
+constexpr int kDotRowsMin = kDotWarps + 1;   // first nk taken by K5b' (measured: slower below)
 
 template <class Sys>
 __global__ void __launch_bounds__(kDotBlock, 1)
@@ -514,6 +518,49 @@ arnoldi_pass2_kernel(const DevArgs* __restrict__ a, KState* ks,
     }
 }
 
+// K5b' (nk > kDotWarps): the same h1 = sigma_k (V_stored^T w)_k, row-parallel
+// like K7a: each thread reads a row of all NK columns and w once and keeps NK
+// partial sums; the warp reduce-scatter and the block's warps in order, then
+// the blocks in order in the last block.  With one column per warp item, K5b
+// would leave a warp with a whole extra column after the others finish, and
+// on this GPU a warp-wide FP64 add holds a sub-partition's FP64 pipe for tens
+// of cycles, so splitting columns into more segments costs as much in
+// per-item reductions as it saves.
+template <class Sys, int NK>
+__global__ void __launch_bounds__(kStreamBlock, 1)
+arnoldi_dot_rows_kernel(const DevArgs* __restrict__ a, KState* ks,
+                        const typename Sys::T* __restrict__ V, size_t ldv,
+                        const typename Sys::T* __restrict__ w, typename Sys::T* partial, int j) {
+    using T = typename Sys::T;
+    if (ks->cycle_over) return;
+    __shared__ T wsum[kWarps * NK];
+    const int n = a->n;
+    int lo, hi;
+    block_rows(n, gridDim.x, blockIdx.x, lo, hi);
+    T part[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) part[k] = 0;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        T vv[NK];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) vv[k] = __ldcs(V + (size_t)k * ldv + i);
+        const T wi = w[i];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) part[k] = fma(vv[k], wi, part[k]);
+    }
+    block_columns<T, NK>(part, NK, wsum, partial + (size_t)blockIdx.x * kMaxBasis);
+    if (last_block_arrive(&ks->counter[CNT_DOT])) {
+        __shared__ double tot[NK];
+        reduce_blocks(partial, gridDim.x, kMaxBasis, NK, tot);
+        for (int k = threadIdx.x; k < NK; k += blockDim.x) {
+            const double hk = ks->sigma[k] * tot[k];
+            ks->h1[k] = hk;
+            ks->c1[k] = ks->sigma[k] * hk;
+        }
+        if (threadIdx.x == 0) ks->counter[CNT_DOT] = 0;
+    }
+}
+
 // Last block of K7b, all threads: Hessenberg column j = h1 + h2 with
 // h_{j+1,j} = ||w||, the previous Givens rotations applied to it, the new
 // rotation, the residual estimate |g_{j+1}| and the end-of-cycle decision;
@@ -621,8 +668,10 @@ __device__ inline void arnoldi_finish(KState* ks, const DevArgs* a, int j, int R
 }
 
 // K7b: w -= V_stored c2, stored as basis column j+1; ||w||^2; then K8.
-// NK is a compile-time constant: all column loads of ROWS rows are issued
-// before the nk + 1 FP64 fused multiply-adds per row.
+// NK is a compile-time constant: all column loads of two rows per thread are
+// issued before the nk + 1 FP64 fused multiply-adds per row (measured faster
+// than four or eight rows per thread for nk >= 2; four rows spilled registers
+// at nk = 18..23).
 template <class Sys, int NK>
 __global__ void __launch_bounds__(kStreamBlock, 1)
 arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T* __restrict__ V,
@@ -641,7 +690,7 @@ arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T*
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
     T part[1] = {0};
     const int bd = blockDim.x;
-    constexpr int ROWS = NK >= 24 ? 2 : (NK >= 8 ? 4 : 8);
+    constexpr int ROWS = 2;
     for (int i0 = lo + threadIdx.x; i0 < hi; i0 += ROWS * bd) {
         T vv[ROWS][NK];
         T r[ROWS];
@@ -782,7 +831,10 @@ static void launch_step(const DevArgs* a, KState* ks, typename Sys::T* V, size_t
     } else {
         arnoldi_spmv_kernel<Sys><<<nblk, kSpmvBlock, spmv_smem<Sys>(), st>>>(a, ks, V, ldv, w, j, src);
         mark(ev, k, st);
-        arnoldi_dot_kernel<Sys><<<nblk, kDotBlock, 0, st>>>(a, ks, V, ldv, w, partial, j, kMaxBasis);
+        if constexpr (NK >= kDotRowsMin)
+            arnoldi_dot_rows_kernel<Sys, NK><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j);
+        else
+            arnoldi_dot_kernel<Sys><<<nblk, kDotBlock, 0, st>>>(a, ks, V, ldv, w, partial, j, kMaxBasis);
         mark(ev, k, st);
         arnoldi_pass2_kernel<Sys, NK><<<nblk, kStreamBlock, 0, st>>>(a, ks, V, ldv, w, partial, j);
         mark(ev, k, st);

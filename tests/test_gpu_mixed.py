@@ -74,6 +74,31 @@ def test_mixed_krylov_from_oracle_history(kind, N, tol):
     seq.close()
 
 
+@pytest.mark.parametrize("m", [40, 64])
+def test_mixed_long_restart_reaches_tolerance(m):
+    """FP32 inner GMRES(m) with m above 32 (the FP32 CGS passes then reduce
+    more basis columns than a warp has lanes) inside FP64 refinement to 1e-10
+    from x0 = 0 on a 64 x 64 grid (inner solves of 38-52 iterations, so the
+    cycles pass 32 columns): converges, and the inner iterations stay within
+    9% of the oracle's float32 emulation."""
+    import paper_2309_02156_gb300 as sa
+    p = workloads.plain_nonsym(64)
+    rowptr, colind, vals, b = workloads.csr_system(p, 1)
+    A = krylov.csr(rowptr, colind, vals, p.n)
+    _, it_ref, nref_ref, rel_ref, st_ref = krylov.mixed_refine(
+        A, A.astype(np.float32), b, np.zeros(p.n), 1e-10, "gmres", m, 60000)
+    Ad, bd = _dev(rowptr, colind, vals, b)
+    seq = sa.Sequence(p.n, 4, 16, seed=3, precision="mixed_krylov", krylov="gmres", restart=m,
+                      max_iters=60000)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    info = seq.solve(Ad, bd, 1e-10, x)
+    assert info["status"] == 0 and st_ref == 0
+    assert method.relres(A, b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-9)
+    assert abs(info["refinements"] - nref_ref) <= 1
+    assert abs(info["iters"] - it_ref) <= max(3, 0.09 * it_ref)
+    seq.close()
+
+
 def test_mixed_fp32_history_sketch_and_refinement():
     import paper_2309_02156_gb300 as sa
     p = workloads.plain_nonsym(40)

@@ -262,6 +262,26 @@ def test_gmres_cycles_match_oracle_residual_by_residual(N):
     seq.close()
 
 
+@pytest.mark.parametrize("m", [33, 40, 64])
+def test_gmres_long_restart_cycle_matches_oracle(m):
+    """One GMRES(m) cycle from x0 = 0 with m above 32, where the CGS passes
+    reduce more basis columns than a warp has lanes: the true residual after
+    the cycle equals the oracle's to 5% (the oracle's own residual moves by
+    less than 1% here when b is perturbed by 1e-15)."""
+    p = workloads.plain_nonsym(20)
+    rowptr, colind, vals, b = workloads.csr_system(p, 0)
+    A = krylov.csr(rowptr, colind, vals, p.n)
+    Ad, bd = _dev_system(rowptr, colind, vals, b)
+    seq = _sa().Sequence(p.n, 20, 80, seed=3, krylov="gmres", restart=m, max_iters=m)
+    x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+    info = seq.solve(Ad, bd, 1e-30, x, allow=(1,))
+    _, it, rel, st = krylov.gmres(A, b, np.zeros(p.n), 1e-30, m, m)
+    assert info["iters"] == it == m
+    assert method.relres(A, b, x.cpu().numpy()) == pytest.approx(rel, rel=0.05)
+    assert info["final_relres"] == pytest.approx(rel, rel=0.05)
+    seq.close()
+
+
 def test_gmres30_count_within_the_oracles_rounding_spread():
     """GMRES(30) to 1e-8 on a 40 x 40 system: the oracle is run on b and on
     seven copies of b perturbed by 1e-15 relative (a rounding-level change);
