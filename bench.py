@@ -1336,6 +1336,7 @@ def main():
             "ms_per_step": cms / K,
             "dtype": "f32 inner + f64 refinement" if precision != "f64" else "f64",
             "iters_per_system": float(np.mean([inf["iters"] for _, inf in cinfos])),
+            "ms_per_krylov_iteration": cms / K / float(np.mean([inf["iters"] for _, inf in cinfos])),
             "refinements_per_system": float(np.mean([inf["refinements"] for _, inf in cinfos])),
             "final_relres_max": max(inf["final_relres"] for _, inf in cinfos),
             "roofline": croof, "kernels": ckern,
@@ -1418,6 +1419,9 @@ def main():
                        "roofline and kernel shares: a separate profiled pass of %d further "
                        "steps" % KP),
             "iters_per_system": float(np.mean(iters)),
+            # ms_per_step / iters_per_system: restarted GMRES(30) counts move at the
+            # rounding level with the order of FP64 sums, the time per iteration does not
+            "ms_per_krylov_iteration": ms / K / float(np.mean(iters)),
             "iters_per_system_prev_steps": [inf["iters"] for _, inf in prime[-3:]],
             "guess_relres_mean": float(np.mean([g["guess_relres"] for g, _ in infos])),
             "final_relres_max": worst,

@@ -580,22 +580,44 @@ __device__ inline void arnoldi_finish(KState* ks, const DevArgs* a, int j, int R
         sn_s[i] = ks->sn[i];
     }
     __syncthreads();
-    if (tid == 0) {
-        const double hn = sqrt(hn2);
-        double hh = 0.0;
-        for (int i = 0; i < nk; ++i) hh += hc[i] * hc[i];
-        hc[j + 1] = hn;
-        for (int i = 0; i < j; ++i) {
-            const double t = cs_s[i] * hc[i] + sn_s[i] * hc[i + 1];
-            hc[i + 1] = -sn_s[i] * hc[i] + cs_s[i] * hc[i + 1];
-            hc[i] = t;
+    // The serial part (the previous rotations applied to the new column) is
+    // one dependent FP64 chain; everything that does not depend on it runs
+    // beside it: ||h||^2 over warp 0 before lane 0 starts the chain, and
+    // h_{j+1,j} = ||w|| with its reciprocal in warp 1 (FP64 square roots and
+    // divisions are long sequences of FP64 operations on this GPU).
+    __shared__ double hh_s, hn_s, hninv_s;
+    if (tid < 32) {
+        double v = 0.0;
+        for (int i = tid; i < nk; i += 32) v += hc[i] * hc[i];
+        v = warp_sum(v);
+        if (tid == 0) {
+            hh_s = v;
+            // The rotated entry i + 1 is carried in a register: the chain is
+            // one FP64 multiply-add per rotation, no shared-memory round trip.
+            double carry = hc[0];
+            for (int i = 0; i < j; ++i) {
+                const double hi1 = hc[i + 1];
+                hc[i] = cs_s[i] * carry + sn_s[i] * hi1;
+                carry = -sn_s[i] * carry + cs_s[i] * hi1;
+            }
+            hc[j] = carry;
         }
-        const double av = hc[j], bv = hc[j + 1];
+    } else if (tid == 32) {
+        const double hn = sqrt(hn2);
+        hn_s = hn;
+        hninv_s = hn > 0.0 ? 1.0 / hn : 0.0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double hn = hn_s, hh = hh_s;
+        hc[j + 1] = hn;
+        const double av = hc[j], bv = hn;
         const double rr = hypot(av, bv);
         double c = 1.0, sv = 0.0;
         if (rr != 0.0) {
-            c = av / rr;
-            sv = bv / rr;
+            const double rinv = 1.0 / rr;
+            c = av * rinv;
+            sv = bv * rinv;
         }
         ks->cs[j] = c;
         ks->sn[j] = sv;
@@ -606,9 +628,10 @@ __device__ inline void arnoldi_finish(KState* ks, const DevArgs* a, int j, int R
         ks->g[j + 1] = gj1;
         ks->g[j] = c * gj;
         ks->iters += 1;
-        ks->sigma[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+        ks->sigma[j + 1] = hninv_s;
         const bool nonfinite = !isfinite(hn) || !isfinite(gj1);
-        const bool happy = hn <= 1e-14 * sqrt(hh + hn * hn);
+        // Breakdown: ||w|| <= 1e-14 ||(h, ||w||)||, compared in squares.
+        const bool happy = hn * hn <= 1e-28 * (hh + hn * hn);
         const bool conv = fabs(gj1) <= ks->target;
         const int e = nonfinite || happy || conv || ks->iters >= a->max_iters || j == R - 1;
         end_cycle = e;
@@ -650,12 +673,17 @@ __device__ inline void arnoldi_finish(KState* ks, const DevArgs* a, int j, int R
             return;
         }
         // Lane l owns rows l and l + 32; acc starts at g and loses H[row][i] y_i.
+        // The diagonal's reciprocals are formed lane-parallel first, so the
+        // dependent chain holds a multiplication per row, not a division.
+        __shared__ double rdiag[kMaxRestart + 1];
+        for (int i = lane; i < k; i += 32) rdiag[i] = 1.0 / Hs[i * kMaxBasis + i];
+        __syncwarp();
         double acc0 = lane < k ? ks->g[lane] : 0.0;
         double acc1 = lane + 32 < k ? ks->g[lane + 32] : 0.0;
         double y0 = 0.0, y1 = 0.0;
         for (int i = k - 1; i >= 0; --i) {
             const double own = (i < 32) ? acc0 : acc1;
-            double yi = __shfl_sync(0xffffffffu, own, i & 31) / Hs[i * kMaxBasis + i];
+            double yi = __shfl_sync(0xffffffffu, own, i & 31) * rdiag[i];
             if (lane == (i & 31)) {
                 if (i < 32) y0 = yi; else y1 = yi;
             }
