@@ -238,9 +238,7 @@ f32_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, float* __restrict__ 
     block_sum<float, 1>(p1, 1, red, scratch);
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
     if (last_block_arrive(&ks->counter[CNT_PASS3])) {
-        __shared__ double tot[1];
-        reduce_blocks(partial, gridDim.x, 1, 1, tot);
         if (threadIdx.x == 0) ks->counter[CNT_PASS3] = 0;
-        arnoldi_finish(ks, a, j, R, tot[0]);
+        arnoldi_finish(ks, a, j, R, partial, (int)gridDim.x);
     }
 }

@@ -568,18 +568,34 @@ arnoldi_dot_rows_kernel(const DevArgs* __restrict__ a, KState* ks,
 // (column-oriented back substitution from shared memory) and sigma_k y_k
 // stored for the basis update.  Everything is staged in shared memory, so
 // thread 0's serial part touches no global memory.
-__device__ inline void arnoldi_finish(KState* ks, const DevArgs* a, int j, int R, double hn2) {
+template <typename T>
+__device__ inline void arnoldi_finish(KState* ks, const DevArgs* a, int j, int R,
+                                     const T* __restrict__ partial, int nblk) {
     __shared__ double hc[kMaxBasis + 1];
     __shared__ double cs_s[kMaxRestart], sn_s[kMaxRestart];
     __shared__ double Hs[kMaxBasis * kMaxRestart];
+    __shared__ double hn2_s;
     __shared__ int end_cycle, k_s, ok_s;
     const int tid = threadIdx.x, nk = j + 1;
-    for (int i = tid; i < nk; i += blockDim.x) hc[i] = ks->h1[i] + ks->h2[i];
-    for (int i = tid; i < j; i += blockDim.x) {
-        cs_s[i] = ks->cs[i];
-        sn_s[i] = ks->sn[i];
+    if (tid < 32) {
+        // ||w||^2: the block partials summed by warp 0 in block order (as
+        // reduce_blocks does) ...
+        T v = 0;
+        for (int b = tid; b < nblk; b += 32) v += __ldcg(partial + b);
+        v = warp_sum(v);
+        if (tid == 0) hn2_s = (double)v;
+    } else {
+        // ... while the other warps load the new column and the previous
+        // rotations (one L2 round trip overlapped with the other).
+        const int t = tid - 32, nt = blockDim.x - 32;
+        for (int i = t; i < nk; i += nt) hc[i] = ks->h1[i] + ks->h2[i];
+        for (int i = t; i < j; i += nt) {
+            cs_s[i] = ks->cs[i];
+            sn_s[i] = ks->sn[i];
+        }
     }
     __syncthreads();
+    const double hn2 = hn2_s;
     // The serial part (the previous rotations applied to the new column) is
     // one dependent FP64 chain; everything that does not depend on it runs
     // beside it: ||h||^2 over warp 0 before lane 0 starts the chain, and
@@ -743,10 +759,8 @@ arnoldi_pass3_kernel(const DevArgs* __restrict__ a, KState* ks, typename Sys::T*
     block_sum<T, 1>(part, 1, red, scratch);
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
     if (last_block_arrive(&ks->counter[CNT_PASS3])) {
-        __shared__ double tot[1];
-        reduce_blocks(partial, gridDim.x, 1, 1, tot);
         if (threadIdx.x == 0) ks->counter[CNT_PASS3] = 0;
-        arnoldi_finish(ks, a, j, R, tot[0]);
+        arnoldi_finish(ks, a, j, R, partial, (int)gridDim.x);
     }
 }
 
@@ -768,8 +782,18 @@ gmres_update_kernel(const DevArgs* __restrict__ a, const KState* ks,
     int lo, hi;
     block_rows(n, gridDim.x, blockIdx.x, lo, hi);
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        // Eight independent column loads in flight per thread (streaming
+        // loads); the multiply-adds keep the column order.
         T acc = 0;
-        for (int l = 0; l < k; ++l) acc = fma(V[(size_t)l * ldv + i], cy[l], acc);
+        int l = 0;
+        for (; l + 8 <= k; l += 8) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcs(V + (size_t)(l + u) * ldv + i);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc = fma(v[u], cy[l + u], acc);
+        }
+        for (; l < k; ++l) acc = fma(__ldcs(V + (size_t)l * ldv + i), cy[l], acc);
         x[i] += acc;
     }
 }
